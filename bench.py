@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Benchmark: candidate pairs verified per second on one GB300.
+
+Workload (default "short_sets"): the prefix-filter self-join over 200,000
+short sets (sizes lognormal mean 20, sigma 0.6, clipped 2..200; Zipf(1.0)
+tokens over a 1,000,000 vocabulary), at Jaccard t in {0.9, 0.8, 0.7, 0.6}.
+The CPU feeder produces the four candidate batches once (untimed); one
+step verifies all four on the GPU.  Synthetic, seeded data.
+
+value   pairs/s with inputs resident in HBM; L2 is flushed (512 MiB write)
+        before every timed step because the inputs fit in L2; CUDA events on
+        the launching stream; max over ranks.
+e2e     the same metric through the public synchronous call with pinned
+        host buffers: host->device copies, kernels and the result readback
+        in the timed region.
+roofline  algorithmic bytes of the verify kernel (candidate stream, set
+        descriptors, the tokens the positional filter lets the merge read,
+        results) over its own event-timed duration, against the measured HBM
+        copy bandwidth.
+cpu_baseline / --impl reference  the CPU oracle as it stands, on host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "candidate pairs verified/sec and GB/s vs HBM peak; p50/p99 batch latency"
+UNIT = "pairs/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+# --------------------------------------------------------------------------- workloads
+
+def workload(name: str):
+    """Returns (label, config dict, collection, [(p, q), ...])."""
+    import synth
+    if name == "short_sets":
+        spec = synth.short_sets()
+        ts = [(9, 10), (4, 5), (7, 10), (3, 5)]
+        label = "prefix-filter self-join, 200k short sets, t in {0.9,0.8,0.7,0.6}"
+    elif name == "long_sets":
+        spec = synth.long_sets()
+        ts = [(3, 5)]
+        label = "prefix-filter self-join, 50k long sets, t=0.6"
+    elif name == "serving_collection":
+        spec = synth.serving_collection()
+        ts = [(7, 10), (4, 5), (9, 10)]
+        label = "prefix-filter self-join, 1M sets mean 12, t in {0.7,0.8,0.9}"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    c = synth.collection(spec)
+    cfg = {"workload": name, "description": label, "n_sets": c.n, "n_tokens": int(len(c.tokens)),
+           "size_law": f"{'lognormal' if spec.size_kind else 'uniform'}({spec.a},{spec.b}) clip [{spec.lo},{spec.hi}]",
+           "zipf_s": spec.zipf_s, "vocab": spec.vocab, "seed": spec.seed,
+           "thresholds": [f"{p}/{q}" for p, q in ts]}
+    return label, cfg, c, ts
+
+
+def make_batches(c, ts):
+    import paper_1812_09141_gb300 as ssj
+    threads = max(1, min(16, os.cpu_count() or 1))
+    out = []
+    for p, q in ts:
+        pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=threads)
+        out.append((p, q, pr, co, ci))
+    return out
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+
+def oracle_accounting(c, batches):
+    """Algorithmic bytes of each batch from the oracle's sequential stop points:
+    12 B per probe (id + offset), 4 B per candidate id, 8 B per touched set
+    descriptor (probe and candidate), 4 B per token the merge must read (the
+    probe's tokens once per probe, the candidate's up to the stop point), 12 B
+    per result triple and 8 B for the count."""
+    import oracle
+    acc = []
+    for p, q, pr, co, ci in batches:
+        tr, cr, cs = oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci,
+                                         consumed=True)
+        counts = np.diff(co.astype(np.int64))
+        pr_max = np.zeros(len(pr), dtype=np.int64)
+        if len(ci):
+            nz = counts > 0
+            starts = co[:-1].astype(np.int64)[nz]
+            pr_max[nz] = np.maximum.reduceat(cr.astype(np.int64), starts)
+        a = (12 * len(pr) + 4 * len(ci) + 8 * (len(pr) + len(ci)) + 4 * int(pr_max.sum())
+             + 4 * int(cs.astype(np.int64).sum()) + 12 * len(tr) + 8)
+        acc.append({"bytes": int(a), "survivors": int(len(tr)), "pairs": int(len(ci))})
+    return acc
+
+
+def cpu_baseline(c, batches, min_seconds=10.0, max_seconds=30.0):
+    """The oracle (single-threaded C) timed on the host over whole steps of the workload."""
+    import oracle
+    pairs_step = sum(len(b[4]) for b in batches)
+    reps, total_t = 0, 0.0
+    while total_t < min_seconds and reps < 1000:
+        t0 = time.perf_counter()
+        for p, q, pr, co, ci in batches:
+            oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci)
+        total_t += time.perf_counter() - t0
+        reps += 1
+        if total_t > max_seconds:
+            break
+    return {"value": pairs_step * reps / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full step(s) of the workload ({pairs_step} pairs each), "
+                      f"{total_t:.1f} s of single-threaded CPU work"}
+
+
+# --------------------------------------------------------------------------- measurement helpers
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(workload_name: str):
+    """DRAM bytes per verify launch from the committed ncu summary, if it was taken on the
+    current kernel source (the summary records the sha256 of verify.cu)."""
+    path = os.path.join(ROOT, "profiles", f"verify_kernel_{workload_name}.md")
+    src = os.path.join(ROOT, "paper_1812_09141_gb300", "csrc", "verify.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        m_sha = re.search(r"verify\.cu sha256:\s*([0-9a-f]{64})", text)
+        m_tr = re.search(r"dram bytes per verify launch:\s*([0-9.eE+]+)", text)
+        if m_sha and m_tr and m_sha.group(1) == sha:
+            return float(m_tr.group(1))
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the GPU works."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.perf_counter(), ln.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for _, ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_1812_09141_gb300 as ssj
+    from paper_1812_09141_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    label, cfg, c, ts = workload(args.workload)
+    batches = make_batches(c, ts)
+    pairs_step = sum(len(b[4]) for b in batches)
+
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ssj.ssj_create(local_rank, flags=ssj.SSJ_CTX_PROFILE, stream=stream.cuda_stream)
+    h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
+    dev_batches = []
+    max_probes, max_cands = 0, 0
+    for p, q, pr, co, ci in batches:
+        t_pr = torch.from_numpy(pr.astype(np.int32)).to(dev)
+        t_co = torch.from_numpy(co.astype(np.int64)).to(dev)
+        t_ci = torch.from_numpy(ci.astype(np.int32)).to(dev)
+        cap = max(len(ci), 1)
+        out = torch.empty(cap * 3, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        dev_batches.append((p, q, t_pr, t_co, t_ci, len(pr), len(ci), out, cap, cnt))
+        max_probes, max_cands = max(max_probes, len(pr)), max(max_cands, len(ci))
+    ssj.ssj_reserve(ctx, max_probes, max_cands)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize(dev)
+
+    def step(events=None):
+        for k, (p, q, t_pr, t_co, t_ci, npr, nci, out, cap, cnt) in enumerate(dev_batches):
+            if events is not None:
+                events[k].record(stream)
+            ssj.ssj_verify_batch_async(ctx, h, h, p, q, t_pr, t_co, t_ci, nci, out, cap, cnt,
+                                       stream=stream.cuda_stream, n_probes=npr)
+        if events is not None:
+            events[len(dev_batches)].record(stream)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            step()
+        stream.synchronize()
+        if ssj.ssj_device_error(ctx):
+            raise RuntimeError("device-side batch check fired")
+        ssj.ssj_profile_read(ctx)  # drop warm-up launches
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        all_events = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(dev_batches) + 1)]
+            step(evs)
+            all_events.append(evs)
+        stream.synchronize()
+        torch.cuda.synchronize(dev)
+    batch_ms, step_ms = [], []
+    for evs in all_events:
+        per = [evs[k].elapsed_time(evs[k + 1]) for k in range(len(dev_batches))]
+        batch_ms.extend(per)
+        step_ms.append(sum(per))
+    launches, plan_ms, verify_ms = ssj.ssj_profile_read(ctx)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    counts = [int(b[9].item()) for b in dev_batches]
+
+    # ---------------- end to end through the public synchronous call, host buffers
+    pinned = []
+    for p, q, pr, co, ci in batches:
+        tp = torch.from_numpy(pr.astype(np.uint32).view(np.int32)).pin_memory()
+        tc = torch.from_numpy(co.astype(np.uint64).view(np.int64)).pin_memory()
+        ti = torch.from_numpy(ci.astype(np.uint32).view(np.int32)).pin_memory()
+        pinned.append((p, q, tp.numpy().view(np.uint32), tc.numpy().view(np.uint64), ti.numpy().view(np.uint32),
+                       (tp, tc, ti)))
+    e2e_steps = max(3, min(args.steps, 20))
+    e2e_t = 0.0
+    h2d = sum(4 * len(b[2]) + 8 * (len(b[2]) + 1) + 4 * len(b[4]) for b in pinned)
+    d2h = 0
+    with torch.cuda.stream(stream):
+        for it in range(e2e_steps + 1):
+            flush.fill_(1)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            res_total = 0
+            for p, q, pr, co, ci, _keep in pinned:
+                res = ssj.ssj_verify_batch(ctx, h, h, p, q, pr, co, ci)
+                res_total += len(res)
+            dt = time.perf_counter() - t0
+            if it > 0:  # the first pass sizes the staging buffers
+                e2e_t += dt
+                d2h = 12 * res_total + (8 + 4) * len(pinned)
+    clocks.stop()
+    ssj.ssj_profile_read(ctx)
+    ssj.ssj_destroy(ctx)
+
+    result = {"total_ms": total_ms, "step_ms": step_ms, "batch_ms": batch_ms, "verify_ms": verify_ms,
+              "plan_ms": plan_ms, "launches": launches, "counts": counts, "pairs_step": pairs_step,
+              "e2e_value": pairs_step * e2e_steps / e2e_t * world, "h2d": h2d, "d2h": d2h,
+              "clocks": clocks.summary(), "cfg": cfg}
+    return result, c, batches
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="short_sets")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        label, cfg, c, ts = workload(args.workload)
+        batches = make_batches(c, ts)
+        import oracle
+        pairs_step = sum(len(b[4]) for b in batches)
+        for _ in range(args.warmup if args.warmup < 2 else 1):
+            for p, q, pr, co, ci in batches:
+                oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for p, q, pr, co, ci in batches:
+                oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci)
+        dt = time.perf_counter() - t0
+        v = pairs_step * args.steps / dt
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{args.steps} full steps of the workload ({pairs_step} pairs each)"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res, c, batches = run_ours(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    pairs_step = res["pairs_step"]
+    total_s = res["total_ms"] / 1e3
+    value = pairs_step * args.steps * world / total_s
+    peak, peak_kind = measured_hbm_peak()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(res["cfg"], pairs_per_step=pairs_step, batches_per_step=len(batches),
+                           l2="flushed before every timed step (512 MiB write); inputs fit in L2",
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU")}
+    bm = sorted(res["batch_ms"])
+    line["latency_ms"] = {"p50": float(np.percentile(bm, 50)), "p99": float(np.percentile(bm, 99)),
+                          "per": "one candidate batch (one threshold), device time"}
+    line["gpu_launches"] = 2 * res["launches"]
+    line["kernel_ms_per_step"] = {"verify": res["verify_ms"] / args.steps, "plan": res["plan_ms"] / args.steps}
+    line["survivors_per_step"] = sum(res["counts"])
+    line["e2e"] = {"value": res["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
+                   "d2h_bytes_per_step": res["d2h"], "call": "ssj_verify_batch (host pointers, pinned)"}
+    line["clocks"] = res["clocks"]
+
+    if world == 1 and not args.no_cpu_baseline:
+        acc = oracle_accounting(c, batches)
+        bytes_step = sum(a["bytes"] for a in acc)
+        if [a["survivors"] for a in acc] != res["counts"]:
+            line["count_mismatch"] = {"oracle": [a["survivors"] for a in acc], "gpu": res["counts"]}
+        verify_s_step = res["verify_ms"] / 1e3 / args.steps
+        achieved = bytes_step / verify_s_step / 1e9
+        traffic = recorded_traffic(args.workload)
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": traffic,
+                            "kernel": "verify_kernel", "peak_source": f"{peak_kind} copy bandwidth",
+                            "algorithmic_bytes_per_launch": bytes_step / len(batches)}
+        line["gbs_vs_hbm_peak"] = {"achieved_gbs": achieved, "frac": achieved / peak}
+        line["cpu_baseline"] = cpu_baseline(c, batches)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * ssj.h - C ABI of the GB300 verification library for exact set similarity
+ * joins (Bellas & Gounaris, "Speeding-up the Verification Phase of Set
+ * Similarity Joins in the GPGPU paradigm").
+ *
+ * Problem (Section 3, Definition): given collections R and S of token sets
+ * and a threshold t, find every (r, s) in R x S with Jaccard(r, s) >= t.
+ * A CPU filter (Section 2.2.3-2.2.4) emits candidate pairs; this library
+ * performs the verification phase (Section 3.3) on the GPU: for each
+ * candidate it intersects the two sorted token arrays by merging, stops as
+ * soon as the threshold can no longer be reached (positional filter,
+ * Section 2.2.3), and keeps the pair iff o*(p+q) >= p*(|r|+|s|), the exact
+ * integer form of the Jaccard equivalent overlap of Table "Similarity
+ * Functions" with t = p/q.
+ *
+ * Conventions for every call:
+ *   - Every call returns an ssj_status and never aborts the process.
+ *   - Unless a flag says otherwise, pointers are HOST pointers and are only
+ *     read during the call.
+ *   - Set ids are 0-based indices into the collection as loaded.
+ *   - Tokens are uint32; each set must be strictly increasing.
+ *   - The library owns every device buffer it allocates (collections,
+ *     batch slots, work queues); the caller owns everything it passes in.
+ *   - A context is bound to one CUDA device and is not thread-safe except
+ *     where a function says so (ssj_submit / ssj_poll / ssj_results may be
+ *     called from different threads).
+ */
+#ifndef SSJ_H
+#define SSJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssj_ctx ssj_ctx;   /* opaque, owned by the library */
+typedef uint32_t ssj_coll;        /* handle of a loaded collection */
+
+/* One result pair: set ids and their exact overlap |r n s|.  For a self-join
+ * r < s (the smaller id first); for R != S, r is in R and s is in S. */
+typedef struct {
+    uint32_t r, s, overlap;
+} ssj_triple;
+
+typedef enum {
+    SSJ_OK = 0,
+    SSJ_EINVAL = 1,    /* malformed argument or batch (ids, offsets, threshold, order) */
+    SSJ_ENOMEM = 2,    /* device/host allocation failed, or a caller buffer is too small */
+    SSJ_EAGAIN = 3,    /* no free slot or memory budget right now: retry later */
+    SSJ_ETIMEDOUT = 4, /* ssj_poll: the batch did not finish within the timeout */
+    SSJ_EBUSY = 5,     /* the object is in use by an in-flight batch */
+    SSJ_ENOTFOUND = 6, /* unknown collection handle or ticket */
+    SSJ_EDEVICE = 7    /* a CUDA call failed or a device-side check fired */
+} ssj_status;
+
+/* ------------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    int device;                 /* CUDA device ordinal */
+    uint64_t mem_budget_bytes;  /* M_c of Table "Notation": device bytes that in-flight
+                                   candidate batches (inputs, work queue, outputs) may
+                                   occupy at once; 0 selects 4 GiB, the paper's default
+                                   (Section 5.2) */
+    uint32_t max_inflight;      /* batch slots for ssj_submit; 0 selects 4 */
+    void* stream;               /* cudaStream_t used by the synchronous calls; NULL
+                                   makes the library create its own */
+    uint32_t flags;             /* SSJ_CTX_PROFILE or 0 */
+} ssj_config;
+
+#define SSJ_CTX_PROFILE 0x1u    /* record CUDA events around the kernels of every synchronous
+                                   or stream-ordered verification (see ssj_profile_read) */
+
+/* Create a context on config->device.  *out receives the handle.
+ * Errors: SSJ_EINVAL (NULL arguments, unknown flags, bad device),
+ * SSJ_EDEVICE (CUDA initialisation failed). */
+ssj_status ssj_create(const ssj_config* config, ssj_ctx** out);
+
+/* Wait for in-flight batches, free every device buffer and the context.
+ * NULL is accepted and ignored. */
+void ssj_destroy(ssj_ctx* ctx);
+
+/* Text of the last error raised on this context (never NULL, "" when
+ * there was none).  The string stays valid until the next failing call on
+ * the context. */
+const char* ssj_last_error(ssj_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Collections (Section 3.3.1, Fig. datasetslayout: all tokens linearised in
+ * one array plus an offsets array delimiting the sets, copied to the device
+ * once).
+ * ------------------------------------------------------------------------ */
+
+#define SSJ_RENUMBER_BY_FREQ 0x1u  /* replace tokens by their rank in ascending global
+                                      frequency, ties by token value (Section 2.2.1), and
+                                      re-sort each set; results are unchanged, only the
+                                      device layout is.  Self-joins only: a batch whose R
+                                      and S differ rejects renumbered collections. */
+#define SSJ_VALIDATE 0x2u          /* check that every set is strictly increasing */
+#define SSJ_PIN_L2 0x4u            /* keep the token array L2-resident through an access
+                                      policy window on the library's streams when it fits
+                                      the persisting L2 set-aside of this context */
+
+/* Load a collection of n_sets sets.  offsets (n_sets+1 entries, host) are
+ * nondecreasing with offsets[0] = 0; set i is tokens[offsets[i] ..
+ * offsets[i+1]) (host).  Each set must hold fewer than 2^31 tokens.
+ * The data are copied; the caller may free them on return.
+ * Device layout: tokens padded so that every set starts on a 16-byte
+ * boundary (pad value 0xFFFFFFFF), plus one 8-byte (start, length)
+ * descriptor per set.  Empty sets are allowed and never match.
+ * Errors: SSJ_EINVAL (NULL pointers, decreasing offsets, unsorted set with
+ * SSJ_VALIDATE, unknown flag), SSJ_ENOMEM, SSJ_EDEVICE. */
+ssj_status ssj_load_collection(ssj_ctx* ctx, const uint64_t* offsets, const uint32_t* tokens,
+                               uint32_t n_sets, uint32_t flags, ssj_coll* out);
+
+/* Free a collection.  SSJ_EBUSY if a submitted batch that uses it has not
+ * been collected with ssj_results; SSJ_ENOTFOUND for an unknown handle. */
+ssj_status ssj_unload_collection(ssj_ctx* ctx, ssj_coll coll);
+
+/* Number of sets and of (unpadded) tokens of a loaded collection. */
+ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, uint64_t* n_tokens);
+
+/* ------------------------------------------------------------------------
+ * Candidate batches (Section 3.3.1, Fig. candidatesoutputlayout: the ids of
+ * candidate sets C, delimited per probe set by offsets C_O).
+ * ------------------------------------------------------------------------ */
+
+#define SSJ_COUNT_ONLY 0x1u     /* only count result pairs (aggregation on top of the join,
+                                   Section 3.2, "output count") */
+#define SSJ_SORTED 0x2u         /* return triples sorted by (r, s) */
+#define SSJ_DEVICE_PTRS 0x4u    /* probe_ids, cand_offsets, cand_ids and the output array are
+                                   DEVICE pointers (same device as the context) */
+#define SSJ_EMIT_ALL 0x8u       /* diagnostic: emit every listed pair (except self pairs of a
+                                   self-join) with its exact overlap, no threshold test and no
+                                   early termination */
+#define SSJ_FORCE_THREAD 0x10u  /* verify every pair with one thread (Alternative A/B style) */
+#define SSJ_FORCE_WARP 0x20u    /* verify every pair with one warp (merge path over 32 lanes) */
+#define SSJ_FORCE_BLOCK 0x40u   /* verify every pair with one thread block (Alternative C) */
+
+typedef struct {
+    ssj_coll R, S;                /* R == S: self-join */
+    uint32_t p, q;                /* Jaccard threshold t = p/q, 0 < p <= q < 2^31 */
+    uint32_t n_probes;
+    const uint32_t* probe_ids;    /* n_probes ids into R */
+    const uint64_t* cand_offsets; /* n_probes+1 nondecreasing offsets, cand_offsets[0] = 0 */
+    const uint32_t* cand_ids;     /* cand_offsets[n_probes] ids into S; probe k is paired with
+                                     cand_ids[cand_offsets[k] .. cand_offsets[k+1]) */
+    uint64_t n_cands;             /* cand_offsets[n_probes].  Required with SSJ_DEVICE_PTRS (the
+                                     host does not read device offsets; the device checks it);
+                                     with host pointers 0 means "take it from cand_offsets" */
+    uint32_t flags;               /* SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | ... */
+} ssj_batch;
+
+/*
+ * Verify one batch synchronously.
+ * Semantics: every listed pair is verified; a self-join skips pairs whose
+ * two ids are equal and reports (min id, max id).  Pairs are not
+ * deduplicated: each listed pair yields at most one triple.  Without
+ * SSJ_SORTED the triple order is unspecified.
+ * out / cap: room for cap triples (host memory, or device memory with
+ * SSJ_DEVICE_PTRS); may be NULL with cap = 0 to query the count.
+ * *n_out receives the number of result pairs.  If it exceeds cap, only the
+ * first cap are written (which ones is unspecified unless SSJ_SORTED) and
+ * SSJ_ENOMEM is returned.  With SSJ_COUNT_ONLY nothing is written to out.
+ * Errors: SSJ_EINVAL (bad threshold, id out of range, decreasing offsets,
+ * renumbered collections in an R != S batch), SSJ_ENOTFOUND, SSJ_ENOMEM,
+ * SSJ_EDEVICE.
+ */
+ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* out, uint64_t cap,
+                            uint64_t* n_out);
+
+/*
+ * Enqueue the verification of a batch on `stream` (a cudaStream_t, or NULL
+ * for the context's stream) and return without waiting.  All batch arrays,
+ * d_out (cap triples) and d_count (one uint64, receives the number of
+ * result pairs, which may exceed cap) are DEVICE pointers that must stay
+ * valid until the stream reaches this work; SSJ_DEVICE_PTRS is implied.
+ * The work queue is taken from the context's workspace, which grows (with
+ * a device allocation) only when a batch is larger than any before; call
+ * ssj_reserve first to keep allocations out of a timed or captured region.
+ * Calls on the same context must not overlap on different streams, since
+ * they share the workspace.  Invalid ids or offsets are detected on the
+ * device: the affected pairs are skipped and ssj_device_error reports it.
+ */
+ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* d_out,
+                                  uint64_t cap, uint64_t* d_count, void* stream);
+
+/* Size the workspace for batches of up to n_probes probes and n_cands
+ * candidates (device allocation happens here, not in later calls). */
+ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands);
+
+/* Read and clear the device-side error word of the last stream-ordered or
+ * synchronous verification (synchronises the context's stream; call it
+ * only after that stream has seen the work).  *code = 0 when no check fired;
+ * bit 0: probe id out of range, bit 1: candidate id out of range, bit 2:
+ * offsets decreasing or past the candidate array. */
+ssj_status ssj_device_error(ssj_ctx* ctx, uint32_t* code);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching (Section 3.2, Fig. executionoverlap: the
+ * filtering thread keeps producing chunks while the device verifies earlier
+ * ones; a chunk is admitted when device memory M_c allows).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Admit a batch.  Host inputs are copied into a library slot before the
+ * call returns, so the caller may reuse its arrays at once (with
+ * SSJ_DEVICE_PTRS the caller keeps them alive until ssj_poll reports done).
+ * The batch runs on its own stream, overlapping with other admitted
+ * batches.  Returns SSJ_EAGAIN when every slot is busy or the batch does not
+ * fit the remaining memory budget; SSJ_EINVAL when it could never fit.
+ * *ticket identifies the batch for ssj_poll / ssj_results.
+ * Thread-safe with respect to ssj_poll and ssj_results.
+ */
+ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t* ticket);
+
+/* Wait up to timeout_ms (0: just test, <0: forever) for a ticket.  *done is
+ * 1 when its results are ready.  SSJ_ETIMEDOUT when the wait ran out,
+ * SSJ_ENOTFOUND for an unknown or collected ticket. */
+ssj_status ssj_poll(ssj_ctx* ctx, uint64_t ticket, int timeout_ms, int* done);
+
+/* Collect a finished ticket.  out == NULL: only report the count in *n_out
+ * and keep the ticket.  Otherwise copy min(count, cap) triples to out
+ * (host), set *n_out to the count and release the ticket and its slot;
+ * SSJ_ENOMEM (ticket kept) if cap < count.  SSJ_EAGAIN if not finished. */
+ssj_status ssj_results(ssj_ctx* ctx, uint64_t ticket, ssj_triple* out, uint64_t cap,
+                       uint64_t* n_out);
+
+/* ------------------------------------------------------------------------
+ * Tuning and measurement
+ * ------------------------------------------------------------------------ */
+
+/* For a context created with SSJ_CTX_PROFILE: wait for the verifications
+ * launched since the last read and return how many there were and the
+ * summed device time of their plan kernels and of their verify kernels
+ * (milliseconds, CUDA events recorded on each launch's stream).  Batches
+ * run through ssj_submit are not recorded.  SSJ_EINVAL without the flag. */
+ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double* plan_ms, double* verify_ms);
+
+/* Granularity bins keyed by |r|+|s| (estimated per probe as 2|r|): a probe
+ * whose key is <= thread_max_key is verified one pair per thread, <=
+ * warp_max_key one pair per warp, otherwise one pair per thread block
+ * (the rule of Section 5.4: per-thread work for small sets, cooperative
+ * Intersect Path for large ones).  thread_max_key is capped at 256.
+ * block_threads is 128, 256 or 512.  Zero leaves a value unchanged. */
+ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t warp_max_key,
+                               uint32_t block_threads);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSJ_H */

@@ -1,0 +1,62 @@
+/*
+ * ssj_feeder.h - CPU candidate generation for a Jaccard self-join, the
+ * filtering half of the paper's filter-verification framework (thread H0 of
+ * Section 3.2) that feeds the GPU verification in include/ssj.h.
+ *
+ * Algorithm ALL (AllPairs, Section 3.1) as an index nested loop
+ * (Section 2.2.4): tokens are renumbered by ascending frequency and sets
+ * ordered by (size, lexicographic) (Section 2.2.1); each probe looks up its
+ * prefix tokens in the inverted index of the sets before it (prefix filter,
+ * Section 2.2.3), keeps those that pass the length filter, deduplicates
+ * them, and is then added to the index.  The prefix of a set x is its first
+ * |x| - ceil(t|x|) + 1 tokens; every set s that reaches Jaccard t with a
+ * probe r (|s| <= |r|) shares a token with r inside both prefixes, so no
+ * result pair is lost.
+ *
+ * Output is the grouped batch layout of ssj_batch (Section 3.3.1): probe ids,
+ * candidate offsets, candidate ids, all in the caller's original set ids.
+ * Candidates of one probe are contiguous; a probe whose list does not fit
+ * the remaining room of a chunk continues in the next chunk (its id then
+ * appears in both).
+ */
+#ifndef SSJ_FEEDER_H
+#define SSJ_FEEDER_H
+
+#include <stdint.h>
+
+#include "ssj.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssj_feeder ssj_feeder;
+
+/* Prepare a self-join of n_sets sets (host offsets / tokens as for
+ * ssj_load_collection; copied) at Jaccard t = p/q, 0 < p <= q < 2^31.
+ * n_threads > 1 generates candidates of consecutive probe ranges in
+ * parallel (results identical to one thread).
+ * Errors: SSJ_EINVAL (bad threshold or offsets, unsorted set),
+ * SSJ_ENOMEM. */
+ssj_status ssj_feeder_create(const uint64_t* offsets, const uint32_t* tokens, uint32_t n_sets, uint32_t p,
+                             uint32_t q, uint32_t n_threads, ssj_feeder** out);
+
+/* Fill the next chunk: at most max_probes entries in probe_ids (and
+ * max_probes+1 in cand_offsets) and at most max_cands candidate ids
+ * (max_probes >= 1, max_cands >= 1).  *n_probes and *n_cands receive the
+ * chunk's size; *done becomes 1 once every probe has been emitted (the
+ * chunk may still hold data).  SSJ_EINVAL for NULL arrays or zero limits. */
+ssj_status ssj_feeder_next(ssj_feeder* f, uint32_t max_probes, uint64_t max_cands, uint32_t* probe_ids,
+                           uint64_t* cand_offsets, uint32_t* cand_ids, uint32_t* n_probes, uint64_t* n_cands,
+                           int* done);
+
+/* Total candidates emitted so far, and probes processed out of n_sets. */
+ssj_status ssj_feeder_progress(ssj_feeder* f, uint64_t* n_cands, uint32_t* probed, uint32_t* n_sets);
+
+void ssj_feeder_destroy(ssj_feeder* f);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSJ_FEEDER_H */

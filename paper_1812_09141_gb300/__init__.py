@@ -1,0 +1,347 @@
+"""Python binding of libssj: GPU verification for exact set similarity joins.
+
+Thin ctypes layer over the C ABI in ``include/ssj.h`` and
+``include/ssj_feeder.h``: the functions below carry the C names and only
+marshal arguments (numpy arrays for host memory, torch CUDA tensors or raw
+integers for device memory).  Every step of the verification runs in the
+library's CUDA kernels; there is no Python or CPU fallback, and importing
+this package fails loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libssj.so")
+
+# status codes
+SSJ_OK, SSJ_EINVAL, SSJ_ENOMEM, SSJ_EAGAIN, SSJ_ETIMEDOUT, SSJ_EBUSY, SSJ_ENOTFOUND, SSJ_EDEVICE = range(8)
+STATUS_NAMES = ["SSJ_OK", "SSJ_EINVAL", "SSJ_ENOMEM", "SSJ_EAGAIN", "SSJ_ETIMEDOUT", "SSJ_EBUSY",
+                "SSJ_ENOTFOUND", "SSJ_EDEVICE"]
+
+# load flags
+SSJ_RENUMBER_BY_FREQ = 0x1
+SSJ_VALIDATE = 0x2
+SSJ_PIN_L2 = 0x4
+# batch flags
+SSJ_COUNT_ONLY = 0x1
+SSJ_SORTED = 0x2
+SSJ_DEVICE_PTRS = 0x4
+SSJ_EMIT_ALL = 0x8
+SSJ_FORCE_THREAD = 0x10
+SSJ_FORCE_WARP = 0x20
+SSJ_FORCE_BLOCK = 0x40
+# context flags
+SSJ_CTX_PROFILE = 0x1
+
+TRIPLE_DTYPE = np.dtype([("r", np.uint32), ("s", np.uint32), ("overlap", np.uint32)])
+
+
+class SsjError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+class ssj_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_uint32), ("stream", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class ssj_batch(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_uint32), ("S", ctypes.c_uint32), ("p", ctypes.c_uint32), ("q", ctypes.c_uint32),
+                ("n_probes", ctypes.c_uint32), ("probe_ids", ctypes.c_void_p), ("cand_offsets", ctypes.c_void_p),
+                ("cand_ids", ctypes.c_void_p), ("n_cands", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+
+
+class ssj_triple(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_uint32), ("s", ctypes.c_uint32), ("overlap", ctypes.c_uint32)]
+
+
+# every exported symbol with (restype, argtypes); the tests check this list against include/*.h
+_VP, _U32, _U64, _INT = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_P = ctypes.POINTER
+SIGNATURES = {
+    "ssj_create": (_INT, [_P(ssj_config), _P(_VP)]),
+    "ssj_destroy": (None, [_VP]),
+    "ssj_last_error": (ctypes.c_char_p, [_VP]),
+    "ssj_load_collection": (_INT, [_VP, _VP, _VP, _U32, _U32, _P(_U32)]),
+    "ssj_unload_collection": (_INT, [_VP, _U32]),
+    "ssj_collection_info": (_INT, [_VP, _U32, _P(_U32), _P(_U64)]),
+    "ssj_verify_batch": (_INT, [_VP, _P(ssj_batch), _VP, _U64, _P(_U64)]),
+    "ssj_verify_batch_async": (_INT, [_VP, _P(ssj_batch), _VP, _U64, _VP, _VP]),
+    "ssj_reserve": (_INT, [_VP, _U32, _U64]),
+    "ssj_device_error": (_INT, [_VP, _P(_U32)]),
+    "ssj_submit": (_INT, [_VP, _P(ssj_batch), _P(_U64)]),
+    "ssj_poll": (_INT, [_VP, _U64, _INT, _P(_INT)]),
+    "ssj_results": (_INT, [_VP, _U64, _VP, _U64, _P(_U64)]),
+    "ssj_set_granularity": (_INT, [_VP, _U32, _U32, _U32]),
+    "ssj_profile_read": (_INT, [_VP, _P(_U32), _P(ctypes.c_double), _P(ctypes.c_double)]),
+    "ssj_feeder_create": (_INT, [_VP, _VP, _U32, _U32, _U32, _U32, _P(_VP)]),
+    "ssj_feeder_next": (_INT, [_VP, _U32, _U64, _VP, _VP, _VP, _P(_U32), _P(_U64), _P(_INT)]),
+    "ssj_feeder_progress": (_INT, [_VP, _P(_U64), _P(_U32), _P(_U32)]),
+    "ssj_feeder_destroy": (None, [_VP]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libssj.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              f"or python paper_1812_09141_gb300/_build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------
+# pointer marshalling
+# --------------------------------------------------------------------------
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, (a.ctypes.data if a.size else None)
+
+
+def _devptr(x) -> int | None:
+    """Device address of a torch CUDA tensor, or an integer address."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor for a device pointer")
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _check(ctx, status: int):
+    if status != SSJ_OK:
+        msg = lib().ssj_last_error(ctx).decode() if ctx else ""
+        raise SsjError(status, msg)
+
+
+# --------------------------------------------------------------------------
+# C functions with their C names (argument marshalling only)
+# --------------------------------------------------------------------------
+
+def ssj_create(device: int = 0, mem_budget_bytes: int = 0, max_inflight: int = 0, stream: int | None = None,
+               flags: int = 0) -> int:
+    cfg = ssj_config(device, mem_budget_bytes, max_inflight, stream, flags)
+    out = ctypes.c_void_p()
+    _check(None, lib().ssj_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def ssj_destroy(ctx: int) -> None:
+    lib().ssj_destroy(ctx)
+
+
+def ssj_last_error(ctx: int) -> str:
+    return lib().ssj_last_error(ctx).decode()
+
+
+def ssj_load_collection(ctx: int, offsets, tokens, flags: int = 0) -> int:
+    offs, po = _host(offsets, np.uint64)
+    toks, pt = _host(tokens, np.uint32)
+    out = ctypes.c_uint32()
+    _check(ctx, lib().ssj_load_collection(ctx, po, pt, len(offs) - 1, flags, ctypes.byref(out)))
+    return out.value
+
+
+def ssj_unload_collection(ctx: int, coll: int) -> None:
+    _check(ctx, lib().ssj_unload_collection(ctx, coll))
+
+
+def ssj_collection_info(ctx: int, coll: int) -> tuple[int, int]:
+    n, t = ctypes.c_uint32(), ctypes.c_uint64()
+    _check(ctx, lib().ssj_collection_info(ctx, coll, ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
+
+
+@dataclass
+class _HostBatch:
+    batch: ssj_batch
+    keep: tuple
+
+
+def _make_batch(R, S, p, q, probe_ids, cand_offsets, cand_ids, flags, n_cands=None, n_probes=None) -> _HostBatch:
+    if flags & SSJ_DEVICE_PTRS:
+        if n_probes is None:
+            if not hasattr(probe_ids, "numel"):
+                raise ValueError("n_probes is required with raw device pointers")
+            n_probes = int(probe_ids.numel())
+        if n_cands is None:
+            raise ValueError("n_cands is required with device pointers")
+        b = ssj_batch(R, S, p, q, n_probes, _devptr(probe_ids), _devptr(cand_offsets), _devptr(cand_ids),
+                      int(n_cands), flags)
+        return _HostBatch(b, (probe_ids, cand_offsets, cand_ids))
+    pr, pp = _host(probe_ids, np.uint32)
+    co, pc = _host(cand_offsets, np.uint64)
+    ci, pi = _host(cand_ids, np.uint32)
+    b = ssj_batch(R, S, p, q, len(pr), pp, pc, pi, 0 if n_cands is None else int(n_cands), flags)
+    return _HostBatch(b, (pr, co, ci))
+
+
+def ssj_verify_batch(ctx: int, R: int, S: int, p: int, q: int, probe_ids, cand_offsets, cand_ids,
+                     flags: int = 0, out=None, cap: int | None = None, n_cands: int | None = None,
+                     n_probes: int | None = None):
+    """Synchronous verification.  Host mode returns a structured array of triples (or the
+    count with SSJ_COUNT_ONLY).  With SSJ_DEVICE_PTRS, `out` is a device tensor/pointer of
+    `cap` triples and the count is returned."""
+    hb = _make_batch(R, S, p, q, probe_ids, cand_offsets, cand_ids, flags, n_cands, n_probes)
+    n_out = ctypes.c_uint64()
+    if flags & SSJ_DEVICE_PTRS:
+        _check(ctx, lib().ssj_verify_batch(ctx, ctypes.byref(hb.batch), _devptr(out), int(cap or 0),
+                                           ctypes.byref(n_out)))
+        return n_out.value
+    if flags & SSJ_COUNT_ONLY:
+        _check(ctx, lib().ssj_verify_batch(ctx, ctypes.byref(hb.batch), None, 0, ctypes.byref(n_out)))
+        return n_out.value
+    if cap is None:
+        cap = int(hb.batch.n_cands) if hb.batch.n_cands else int(hb.keep[1][-1]) if len(hb.keep[1]) else 0
+    res = np.empty(max(cap, 1), dtype=TRIPLE_DTYPE)
+    st = lib().ssj_verify_batch(ctx, ctypes.byref(hb.batch), res.ctypes.data, cap, ctypes.byref(n_out))
+    _check(ctx, st)
+    return res[:n_out.value]
+
+
+def ssj_verify_batch_async(ctx: int, R: int, S: int, p: int, q: int, probe_ids, cand_offsets, cand_ids, n_cands: int,
+                           d_out, cap: int, d_count, stream: int | None = None, flags: int = 0,
+                           n_probes: int | None = None) -> None:
+    """Enqueue verification of device-resident inputs on `stream` (device pointers only)."""
+    hb = _make_batch(R, S, p, q, probe_ids, cand_offsets, cand_ids, flags | SSJ_DEVICE_PTRS, n_cands, n_probes)
+    _check(ctx, lib().ssj_verify_batch_async(ctx, ctypes.byref(hb.batch), _devptr(d_out), int(cap),
+                                             _devptr(d_count), stream))
+
+
+def ssj_reserve(ctx: int, n_probes: int, n_cands: int) -> None:
+    _check(ctx, lib().ssj_reserve(ctx, n_probes, n_cands))
+
+
+def ssj_device_error(ctx: int) -> int:
+    code = ctypes.c_uint32()
+    _check(ctx, lib().ssj_device_error(ctx, ctypes.byref(code)))
+    return code.value
+
+
+def ssj_submit(ctx: int, R: int, S: int, p: int, q: int, probe_ids, cand_offsets, cand_ids, flags: int = 0,
+               n_cands: int | None = None, n_probes: int | None = None) -> int | None:
+    """Admit a batch; returns its ticket, or None when the call answered SSJ_EAGAIN."""
+    hb = _make_batch(R, S, p, q, probe_ids, cand_offsets, cand_ids, flags, n_cands, n_probes)
+    t = ctypes.c_uint64()
+    st = lib().ssj_submit(ctx, ctypes.byref(hb.batch), ctypes.byref(t))
+    if st == SSJ_EAGAIN:
+        return None
+    _check(ctx, st)
+    return t.value
+
+
+def ssj_poll(ctx: int, ticket: int, timeout_ms: int = 0) -> bool:
+    done = ctypes.c_int()
+    st = lib().ssj_poll(ctx, ticket, timeout_ms, ctypes.byref(done))
+    if st == SSJ_ETIMEDOUT:
+        return False
+    _check(ctx, st)
+    return bool(done.value)
+
+
+def ssj_results(ctx: int, ticket: int, count_only: bool = False):
+    """Collect a finished ticket: structured triples (or the count if count_only)."""
+    n = ctypes.c_uint64()
+    _check(ctx, lib().ssj_results(ctx, ticket, None, 0, ctypes.byref(n)))
+    if count_only:
+        dummy = np.empty(1, dtype=TRIPLE_DTYPE)
+        _check(ctx, lib().ssj_results(ctx, ticket, dummy.ctypes.data, 0, ctypes.byref(n)))
+        return n.value
+    res = np.empty(max(n.value, 1), dtype=TRIPLE_DTYPE)
+    _check(ctx, lib().ssj_results(ctx, ticket, res.ctypes.data, n.value, ctypes.byref(n)))
+    return res[:n.value]
+
+
+def ssj_set_granularity(ctx: int, thread_max_key: int = 0, warp_max_key: int = 0, block_threads: int = 0) -> None:
+    _check(ctx, lib().ssj_set_granularity(ctx, thread_max_key, warp_max_key, block_threads))
+
+
+def ssj_profile_read(ctx: int) -> tuple[int, float, float]:
+    """(launches, plan kernel ms, verify kernel ms) since the last read (SSJ_CTX_PROFILE contexts)."""
+    n, a, b = ctypes.c_uint32(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().ssj_profile_read(ctx, ctypes.byref(n), ctypes.byref(a), ctypes.byref(b)))
+    return n.value, a.value, b.value
+
+
+# feeder --------------------------------------------------------------------
+
+def ssj_feeder_create(offsets, tokens, p: int, q: int, n_threads: int = 1) -> int:
+    offs, po = _host(offsets, np.uint64)
+    toks, pt = _host(tokens, np.uint32)
+    out = ctypes.c_void_p()
+    _check(None, lib().ssj_feeder_create(po, pt, len(offs) - 1, p, q, n_threads, ctypes.byref(out)))
+    return out.value
+
+
+def ssj_feeder_next(f: int, max_probes: int, max_cands: int):
+    """Next chunk as (probe_ids, cand_offsets, cand_ids, done)."""
+    pr = np.empty(max_probes, dtype=np.uint32)
+    co = np.empty(max_probes + 1, dtype=np.uint64)
+    ci = np.empty(max(max_cands, 1), dtype=np.uint32)
+    npb, nc, done = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_int()
+    _check(None, lib().ssj_feeder_next(f, max_probes, max_cands, pr.ctypes.data, co.ctypes.data, ci.ctypes.data,
+                                       ctypes.byref(npb), ctypes.byref(nc), ctypes.byref(done)))
+    k = npb.value
+    return pr[:k], co[:k + 1], ci[:nc.value], bool(done.value)
+
+
+def ssj_feeder_progress(f: int) -> tuple[int, int, int]:
+    nc, probed, n = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(None, lib().ssj_feeder_progress(f, ctypes.byref(nc), ctypes.byref(probed), ctypes.byref(n)))
+    return nc.value, probed.value, n.value
+
+
+def ssj_feeder_destroy(f: int) -> None:
+    lib().ssj_feeder_destroy(f)
+
+
+def feeder_all(offsets, tokens, p: int, q: int, n_threads: int = 1, chunk: int = 1 << 22):
+    """Run the feeder to completion; returns one concatenated batch (probe_ids, offsets, cands)."""
+    f = ssj_feeder_create(offsets, tokens, p, q, n_threads)
+    try:
+        probes, offs, cands = [], [np.zeros(1, dtype=np.uint64)], []
+        base = 0
+        n_sets = len(offsets) - 1
+        while True:
+            pr, co, ci, done = ssj_feeder_next(f, max(n_sets, 1), chunk)
+            probes.append(pr)
+            offs.append(co[1:] + base)
+            cands.append(ci)
+            base += len(ci)
+            if done:
+                break
+        return (np.concatenate(probes).astype(np.uint32), np.concatenate(offs).astype(np.uint64),
+                np.concatenate(cands).astype(np.uint32))
+    finally:
+        ssj_feeder_destroy(f)
+
+
+def triples_to_array(t) -> np.ndarray:
+    """Structured triples -> (k, 3) uint32, sorted by (r, s)."""
+    a = np.stack([t["r"], t["s"], t["overlap"]], axis=1).astype(np.uint32) if len(t) else np.zeros((0, 3), np.uint32)
+    if len(a):
+        a = a[np.lexsort((a[:, 1], a[:, 0]))]
+    return a

@@ -1,0 +1,923 @@
+// Host side of the C ABI declared in include/ssj.h: contexts, collection
+// store, batch validation, synchronous and stream-ordered verification, and
+// the continuous-batching serving loop (submit / poll / results).
+//
+// The co-process scheme of Section 3.2 (Fig. executionoverlap) maps onto
+// this file as follows: the caller's filtering thread (H0) submits chunks;
+// each admitted chunk gets a slot with its own CUDA stream, so its copies
+// and kernels overlap with other chunks on the device (H1); a completion
+// thread reads the result count, copies back exactly that many triples and
+// releases device memory (H2).  Admission is by a device-memory budget
+// (M_c, Section 4.1.2) and a slot count.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ssj_internal.h"
+
+namespace ssj {
+cudaError_t layout_lengths(const uint64_t* d_offs, const uint32_t* d_toks, uint32_t n, int validate,
+                           uint64_t* d_scratch, uint32_t* d_err, uint64_t* n_chunks_host, cudaStream_t st,
+                           int num_sms);
+cudaError_t layout_scatter(const uint64_t* d_offs, const uint32_t* d_toks, uint32_t n, const uint64_t* d_scratch,
+                           uint32_t* d_dst, uint2* d_desc, cudaStream_t st, int num_sms);
+size_t layout_scratch_words(uint32_t n);
+void renumber_by_frequency(const uint64_t* offsets, const uint32_t* tokens, uint32_t n, std::vector<uint32_t>& out);
+}  // namespace ssj
+
+using namespace ssj;
+
+namespace {
+
+struct Collection {
+    uint32_t n_sets = 0;
+    uint64_t n_tokens = 0;
+    uint64_t n_chunks = 0;
+    uint32_t* d_toks = nullptr;  // n_chunks * 4 tokens
+    uint2* d_desc = nullptr;
+    bool renumbered = false;
+    uint32_t busy = 0;           // submitted batches not yet collected
+    DevColl dev() const {
+        DevColl d;
+        d.toks4 = reinterpret_cast<const uint4*>(d_toks);
+        d.desc = d_desc;
+        d.n_sets = n_sets;
+        return d;
+    }
+};
+
+enum class TicketState { kRunning, kDone, kFailed };
+
+struct Ticket {
+    uint64_t id = 0;
+    ssj_coll R = 0, S = 0;
+    uint32_t flags = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t kernel_done = nullptr;
+    void* d_mem = nullptr;           // one stream-ordered allocation for the whole batch
+    uint64_t bytes = 0;              // charged to the budget
+    ssj_triple* d_out = nullptr;
+    uint64_t out_cap = 0;
+    uint64_t* h_count = nullptr;     // pinned
+    uint32_t* h_err = nullptr;       // pinned
+    ssj_triple* h_out = nullptr;     // pinned, grown as needed
+    uint64_t count = 0;
+    TicketState state = TicketState::kRunning;
+    std::string error;
+    int slot = -1;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    // pinned staging for host inputs
+    uint32_t* h_probe = nullptr;
+    uint64_t* h_offs = nullptr;
+    uint32_t* h_cand = nullptr;
+    uint64_t h_probe_cap = 0, h_offs_cap = 0, h_cand_cap = 0;
+    ssj_triple* h_out = nullptr;
+    uint64_t h_out_cap = 0;
+    uint64_t* h_count = nullptr;
+    uint32_t* h_err = nullptr;
+    bool busy = false;          // reserved by a ticket until ssj_results collects it
+    struct Ticket* pending = nullptr;  // launched, waiting for the completion thread
+    std::thread completer;
+};
+
+}  // namespace
+
+struct ssj_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t budget = 0;
+    uint32_t max_inflight = 0;
+    uint32_t thread_max_key = 64;
+    uint32_t warp_max_key = 2048;
+    uint32_t block_threads = 256;
+    std::string err;
+
+    std::map<ssj_coll, Collection> colls;
+    ssj_coll next_coll = 1;
+
+    // workspace for synchronous/stream-ordered calls
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // device staging for synchronous host-pointer calls
+    void* io = nullptr;
+    size_t io_bytes = 0;
+    uint64_t* h_count = nullptr;  // pinned
+    uint32_t* h_err = nullptr;    // pinned
+    Counters* last_ctr = nullptr;
+    // kernel timing (SSJ_CTX_PROFILE): events around plan and verify of each launch
+    bool profile = false;
+    std::vector<cudaEvent_t> prof_ev;  // 3 per recorded launch
+    size_t prof_used = 0;             // launches recorded since the last read
+
+    // serving
+    std::mutex mu;
+    std::condition_variable cv;
+    cudaMemPool_t pool = nullptr;
+    std::vector<Slot> slots;
+    std::map<uint64_t, std::unique_ptr<Ticket>> tickets;
+    uint64_t next_ticket = 1;
+    uint64_t used_bytes = 0;
+    bool stopping = false;
+};
+
+namespace {
+
+ssj_status fail(ssj_ctx* ctx, ssj_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+ssj_status cuda_fail(ssj_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, SSJ_EDEVICE, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(ctx, expr)                                   \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+ssj_status ensure_device_buffer(ssj_ctx* ctx, void** buf, size_t* have, size_t need) {
+    if (*have >= need && *buf) return SSJ_OK;
+    if (*buf) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(*buf);
+        *buf = nullptr;
+        *have = 0;
+    }
+    size_t sz = std::max<size_t>(need, 1 << 20);
+    cudaError_t e = cudaMalloc(buf, sz);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        return fail(ctx, SSJ_ENOMEM, "cudaMalloc(%zu): %s", sz, cudaGetErrorString(e));
+    }
+    *have = sz;
+    return SSJ_OK;
+}
+
+template <class T>
+ssj_status ensure_pinned(ssj_ctx* ctx, T** buf, uint64_t* have, uint64_t need) {
+    if (*have >= need && *buf) return SSJ_OK;
+    if (*buf) cudaFreeHost(*buf);
+    *buf = nullptr;
+    uint64_t n = std::max<uint64_t>(need, std::max<uint64_t>(*have * 2, 1024));
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(buf), n * sizeof(T));
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        *have = 0;
+        return fail(ctx, SSJ_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+    }
+    *have = n;
+    return SSJ_OK;
+}
+
+// Host-side checks of a host batch.  Only what the host needs is read here
+// (the first and last offsets); ids and the monotonicity of the offsets are
+// checked on the device by the plan and verify kernels, which report
+// violations through the error word.
+ssj_status validate_host_batch(ssj_ctx* ctx, const ssj_batch* b, uint64_t* n_cands) {
+    if (b->n_probes && (!b->probe_ids || !b->cand_offsets)) return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
+    if (!b->cand_offsets) {
+        *n_cands = 0;
+        return SSJ_OK;
+    }
+    if (b->cand_offsets[0] != 0) return fail(ctx, SSJ_EINVAL, "cand_offsets[0] must be 0");
+    const uint64_t nc = b->cand_offsets[b->n_probes];
+    if (b->n_cands && b->n_cands != nc) return fail(ctx, SSJ_EINVAL, "n_cands != cand_offsets[n_probes]");
+    if (nc && !b->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
+    *n_cands = nc;
+    return SSJ_OK;
+}
+
+ssj_status resolve(ssj_ctx* ctx, const ssj_batch* b, Collection** R, Collection** S) {
+    if (!ctx || !b) return fail(ctx, SSJ_EINVAL, "NULL argument");
+    if (b->p == 0 || b->p > b->q || b->q >= (1u << 31)) return fail(ctx, SSJ_EINVAL, "threshold must be 0 < p <= q < 2^31");
+    auto ir = ctx->colls.find(b->R);
+    auto is = ctx->colls.find(b->S);
+    if (ir == ctx->colls.end() || is == ctx->colls.end()) return fail(ctx, SSJ_ENOTFOUND, "unknown collection");
+    if (b->R != b->S && (ir->second.renumbered || is->second.renumbered))
+        return fail(ctx, SSJ_EINVAL, "renumbered collections can only be self-joined");
+    const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_EMIT_ALL | SSJ_FORCE_THREAD |
+                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK;
+    if (b->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown batch flag");
+    const uint32_t forced = b->flags & (SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK);
+    if (forced & (forced - 1)) return fail(ctx, SSJ_EINVAL, "at most one SSJ_FORCE_* flag");
+    *R = &ir->second;
+    *S = &is->second;
+    return SSJ_OK;
+}
+
+uint32_t vflags(uint32_t f) {
+    uint32_t v = 0;
+    if (f & SSJ_COUNT_ONLY) v |= VF_COUNT_ONLY;
+    if (f & SSJ_EMIT_ALL) v |= VF_EMIT_ALL;
+    if (f & SSJ_FORCE_THREAD) v |= VF_FORCE_THREAD;
+    if (f & SSJ_FORCE_WARP) v |= VF_FORCE_WARP;
+    if (f & SSJ_FORCE_BLOCK) v |= VF_FORCE_BLOCK;
+    return v;
+}
+
+VerifyArgs make_args(ssj_ctx* ctx, const ssj_batch* b, const Collection& R, const Collection& S, uint64_t n_cands) {
+    VerifyArgs a;
+    memset(&a, 0, sizeof(a));
+    a.R = R.dev();
+    a.S = S.dev();
+    a.p = b->p;
+    a.q = b->q;
+    a.self_join = b->R == b->S ? 1u : 0u;
+    a.flags = vflags(b->flags);
+    a.n_probes = b->n_probes;
+    a.n_cands = n_cands;
+    a.thread_max_key = ctx->thread_max_key;
+    a.warp_max_key = ctx->warp_max_key;
+    return a;
+}
+
+// Three timing events for the next launch of a profiling context (else NULL).
+cudaEvent_t* profile_events(ssj_ctx* ctx) {
+    if (!ctx->profile) return nullptr;
+    const size_t need = 3 * (ctx->prof_used + 1);
+    while (ctx->prof_ev.size() < need) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+        ctx->prof_ev.push_back(ev);
+    }
+    cudaEvent_t* evs = &ctx->prof_ev[3 * ctx->prof_used];
+    ctx->prof_used++;
+    return evs;
+}
+
+bool triple_less(const ssj_triple& x, const ssj_triple& y) { return x.r != y.r ? x.r < y.r : x.s < y.s; }
+
+void completion_loop(ssj_ctx* ctx, int slot);
+
+}  // namespace
+
+// ===========================================================================
+// Context
+// ===========================================================================
+
+extern "C" ssj_status ssj_create(const ssj_config* config, ssj_ctx** out) {
+    if (!config || !out) return SSJ_EINVAL;
+    if (config->flags & ~SSJ_CTX_PROFILE) return SSJ_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || config->device < 0 || config->device >= ndev) return SSJ_EINVAL;
+    std::unique_ptr<ssj_ctx> ctx(new ssj_ctx());
+    ctx->device = config->device;
+    ctx->profile = (config->flags & SSJ_CTX_PROFILE) != 0;
+    DeviceGuard g(ctx->device);
+    if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
+        return SSJ_EDEVICE;
+    ctx->budget = config->mem_budget_bytes ? config->mem_budget_bytes : (4ull << 30);
+    ctx->max_inflight = config->max_inflight ? config->max_inflight : 4;
+    if (config->stream) {
+        ctx->stream = static_cast<cudaStream_t>(config->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return SSJ_EDEVICE;
+        ctx->own_stream = true;
+    }
+    if (cudaMallocHost(reinterpret_cast<void**>(&ctx->h_count), sizeof(uint64_t)) != cudaSuccess) return SSJ_EDEVICE;
+    if (cudaMallocHost(reinterpret_cast<void**>(&ctx->h_err), sizeof(uint32_t)) != cudaSuccess) return SSJ_EDEVICE;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) return SSJ_EDEVICE;
+    uint64_t threshold = ctx->budget;
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+    ctx->slots.resize(ctx->max_inflight);
+    for (auto& s : ctx->slots) {
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) return SSJ_EDEVICE;
+        if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) return SSJ_EDEVICE;
+        if (cudaMallocHost(reinterpret_cast<void**>(&s.h_count), sizeof(uint64_t)) != cudaSuccess) return SSJ_EDEVICE;
+        if (cudaMallocHost(reinterpret_cast<void**>(&s.h_err), sizeof(uint32_t)) != cudaSuccess) return SSJ_EDEVICE;
+    }
+    ssj_ctx* raw = ctx.release();
+    for (size_t i = 0; i < raw->slots.size(); ++i) raw->slots[i].completer = std::thread(completion_loop, raw, (int)i);
+    *out = raw;
+    return SSJ_OK;
+}
+
+extern "C" void ssj_destroy(ssj_ctx* ctx) {
+    if (!ctx) return;
+    {
+        std::unique_lock<std::mutex> lk(ctx->mu);
+        ctx->stopping = true;
+    }
+    ctx->cv.notify_all();
+    for (auto& s : ctx->slots)
+        if (s.completer.joinable()) s.completer.join();
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& s : ctx->slots) {
+        cudaStreamSynchronize(s.stream);
+        cudaStreamDestroy(s.stream);
+        cudaEventDestroy(s.ev);
+        cudaFreeHost(s.h_probe);
+        cudaFreeHost(s.h_offs);
+        cudaFreeHost(s.h_cand);
+        cudaFreeHost(s.h_out);
+        cudaFreeHost(s.h_count);
+        cudaFreeHost(s.h_err);
+    }
+    for (auto& kv : ctx->tickets)
+        if (kv.second->d_mem) {
+            cudaFreeAsync(kv.second->d_mem, kv.second->stream);
+            cudaStreamSynchronize(kv.second->stream);
+        }
+    for (auto& kv : ctx->colls) {
+        cudaFree(kv.second.d_toks);
+        cudaFree(kv.second.d_desc);
+    }
+    cudaFree(ctx->ws);
+    cudaFree(ctx->io);
+    cudaFreeHost(ctx->h_count);
+    cudaFreeHost(ctx->h_err);
+    for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" const char* ssj_last_error(ssj_ctx* ctx) {
+    if (!ctx) return "NULL context";
+    return ctx->err.c_str();
+}
+
+extern "C" ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t warp_max_key,
+                                          uint32_t block_threads) {
+    if (!ctx) return SSJ_EINVAL;
+    if (block_threads && block_threads != 128 && block_threads != 256 && block_threads != 512)
+        return fail(ctx, SSJ_EINVAL, "block_threads must be 128, 256 or 512");
+    if (thread_max_key) ctx->thread_max_key = std::min(thread_max_key, kThreadKeyCap);
+    if (warp_max_key) ctx->warp_max_key = warp_max_key;
+    if (block_threads) ctx->block_threads = block_threads;
+    return SSJ_OK;
+}
+
+// ===========================================================================
+// Collections
+// ===========================================================================
+
+extern "C" ssj_status ssj_load_collection(ssj_ctx* ctx, const uint64_t* offsets, const uint32_t* tokens,
+                                          uint32_t n_sets, uint32_t flags, ssj_coll* out) {
+    if (!ctx || !offsets || !out) return fail(ctx, SSJ_EINVAL, "NULL argument");
+    if (flags & ~(SSJ_RENUMBER_BY_FREQ | SSJ_VALIDATE | SSJ_PIN_L2)) return fail(ctx, SSJ_EINVAL, "unknown load flag");
+    if (offsets[0] != 0) return fail(ctx, SSJ_EINVAL, "offsets[0] must be 0");
+    for (uint32_t i = 0; i < n_sets; ++i)
+        if (offsets[i + 1] < offsets[i]) return fail(ctx, SSJ_EINVAL, "offsets decrease at set %u", i);
+    const uint64_t total = offsets[n_sets];
+    if (total && !tokens) return fail(ctx, SSJ_EINVAL, "NULL tokens");
+    DeviceGuard g(ctx->device);
+
+    std::vector<uint32_t> renum;
+    const uint32_t* src = tokens;
+    if ((flags & SSJ_RENUMBER_BY_FREQ) && total) {
+        if (flags & SSJ_VALIDATE) {  // validate the caller's order before it is rewritten
+            for (uint32_t s = 0; s < n_sets; ++s)
+                for (uint64_t t = offsets[s] + 1; t < offsets[s + 1]; ++t)
+                    if (tokens[t - 1] >= tokens[t]) return fail(ctx, SSJ_EINVAL, "set %u is not strictly increasing", s);
+        }
+        renumber_by_frequency(offsets, tokens, n_sets, renum);
+        src = renum.data();
+    }
+
+    // raw copies on the device, then the padded layout built there
+    uint64_t* d_offs = nullptr;
+    uint32_t* d_raw = nullptr;
+    uint64_t* d_scratch = nullptr;
+    uint32_t* d_err = nullptr;
+    Collection c;
+    c.n_sets = n_sets;
+    c.n_tokens = total;
+    c.renumbered = (flags & SSJ_RENUMBER_BY_FREQ) != 0;
+    auto cleanup = [&]() {
+        cudaFree(d_offs);
+        cudaFree(d_raw);
+        cudaFree(d_scratch);
+        cudaFree(d_err);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_offs, sizeof(uint64_t) * (n_sets + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&d_raw, sizeof(uint32_t) * std::max<uint64_t>(total, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&d_scratch, sizeof(uint64_t) * layout_scratch_words(n_sets))) != cudaSuccess ||
+        (e = cudaMalloc(&d_err, sizeof(uint32_t))) != cudaSuccess) {
+        cleanup();
+        return fail(ctx, SSJ_ENOMEM, "collection staging: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t st = ctx->stream;
+    if ((e = cudaMemcpyAsync(d_offs, offsets, sizeof(uint64_t) * (n_sets + 1), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (total && (e = cudaMemcpyAsync(d_raw, src, sizeof(uint32_t) * total, cudaMemcpyHostToDevice, st)) !=
+                      cudaSuccess)) {
+        cleanup();
+        return cuda_fail(ctx, e, "collection upload");
+    }
+    const int validate = (flags & SSJ_VALIDATE) && !(flags & SSJ_RENUMBER_BY_FREQ);
+    e = layout_lengths(d_offs, d_raw, n_sets, validate, d_scratch, d_err, ctx->h_count, st, ctx->num_sms);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(ctx, e, "layout_lengths");
+    }
+    c.n_chunks = *ctx->h_count;
+    cudaMemcpy(ctx->h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (*ctx->h_err) {
+        cleanup();
+        return fail(ctx, SSJ_EINVAL, (*ctx->h_err & 1u) ? "a set holds 2^31 tokens or more" : "a set is not strictly increasing");
+    }
+    if ((e = cudaMalloc(&c.d_toks, 16 * std::max<uint64_t>(c.n_chunks, 1) + 16)) != cudaSuccess ||
+        (e = cudaMalloc(&c.d_desc, sizeof(uint2) * std::max<uint32_t>(n_sets, 1))) != cudaSuccess) {
+        cudaFree(c.d_toks);
+        cleanup();
+        return fail(ctx, SSJ_ENOMEM, "collection: %s", cudaGetErrorString(e));
+    }
+    e = layout_scatter(d_offs, d_raw, n_sets, d_scratch, c.d_toks, c.d_desc, st, ctx->num_sms);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) {
+        cudaFree(c.d_toks);
+        cudaFree(c.d_desc);
+        return cuda_fail(ctx, e, "layout_scatter");
+    }
+    if (flags & SSJ_PIN_L2) {
+        // Persisting-L2 window over the token array on the library's streams.  The set-aside is a
+        // per-context limit; it is left as the context found it when the window does not fit.
+        size_t setaside = 0;
+        cudaDeviceGetLimit(&setaside, cudaLimitPersistingL2CacheSize);
+        const size_t bytes = 16 * c.n_chunks;
+        if (setaside > 0 && bytes > 0) {
+            cudaStreamAttrValue v;
+            memset(&v, 0, sizeof(v));
+            v.accessPolicyWindow.base_ptr = c.d_toks;
+            v.accessPolicyWindow.num_bytes = std::min(bytes, setaside);
+            v.accessPolicyWindow.hitRatio = 1.0f;
+            v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+            v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+            cudaStreamSetAttribute(ctx->stream, cudaStreamAttributeAccessPolicyWindow, &v);
+            for (auto& s : ctx->slots) cudaStreamSetAttribute(s.stream, cudaStreamAttributeAccessPolicyWindow, &v);
+        }
+    }
+    const ssj_coll h = ctx->next_coll++;
+    ctx->colls[h] = c;
+    *out = h;
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_unload_collection(ssj_ctx* ctx, ssj_coll coll) {
+    if (!ctx) return SSJ_EINVAL;
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    auto it = ctx->colls.find(coll);
+    if (it == ctx->colls.end()) return fail(ctx, SSJ_ENOTFOUND, "unknown collection %u", coll);
+    if (it->second.busy) return fail(ctx, SSJ_EBUSY, "collection %u is used by submitted batches", coll);
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(it->second.d_toks);
+    cudaFree(it->second.d_desc);
+    ctx->colls.erase(it);
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, uint64_t* n_tokens) {
+    if (!ctx) return SSJ_EINVAL;
+    auto it = ctx->colls.find(coll);
+    if (it == ctx->colls.end()) return fail(ctx, SSJ_ENOTFOUND, "unknown collection %u", coll);
+    if (n_sets) *n_sets = it->second.n_sets;
+    if (n_tokens) *n_tokens = it->second.n_tokens;
+    return SSJ_OK;
+}
+
+// ===========================================================================
+// Stream-ordered and synchronous verification
+// ===========================================================================
+
+extern "C" ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands) {
+    if (!ctx) return SSJ_EINVAL;
+    DeviceGuard g(ctx->device);
+    return ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(n_probes, n_cands));
+}
+
+extern "C" ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* d_out, uint64_t cap,
+                                             uint64_t* d_count, void* stream) {
+    Collection *R, *S;
+    ssj_status st = resolve(ctx, batch, &R, &S);
+    if (st != SSJ_OK) return st;
+    if (!d_count) return fail(ctx, SSJ_EINVAL, "d_count is required");
+    if (batch->n_probes && (!batch->probe_ids || !batch->cand_offsets))
+        return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
+    if (batch->n_cands && !batch->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
+    if (cap && !d_out && !(batch->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output");
+    DeviceGuard g(ctx->device);
+    st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(batch->n_probes, batch->n_cands));
+    if (st != SSJ_OK) return st;
+    VerifyArgs a = make_args(ctx, batch, *R, *S, batch->n_cands);
+    a.probe_ids = batch->probe_ids;
+    a.cand_offsets = batch->cand_offsets;
+    a.cand_ids = batch->cand_ids;
+    a.out = d_out;
+    a.cap = (batch->flags & SSJ_COUNT_ONLY) ? 0 : cap;
+    a.count = reinterpret_cast<unsigned long long*>(d_count);
+    bind_workspace(a, ctx->ws, batch->n_probes, batch->n_cands);
+    ctx->last_ctr = a.ctr;
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    cudaError_t e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_verify");
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_device_error(ssj_ctx* ctx, uint32_t* code) {
+    if (!ctx || !code) return SSJ_EINVAL;
+    *code = 0;
+    if (!ctx->last_ctr) return SSJ_OK;
+    DeviceGuard g(ctx->device);
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_err, &ctx->last_ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    *code = *ctx->h_err;
+    CUDA_TRY(ctx, cudaMemsetAsync(&ctx->last_ctr->err, 0, sizeof(uint32_t), ctx->stream));
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* out, uint64_t cap,
+                                       uint64_t* n_out) {
+    Collection *R, *S;
+    ssj_status st = resolve(ctx, batch, &R, &S);
+    if (st != SSJ_OK) return st;
+    if (!n_out) return fail(ctx, SSJ_EINVAL, "n_out is required");
+    if (cap && !out && !(batch->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output with cap > 0");
+    DeviceGuard g(ctx->device);
+    const bool dev = (batch->flags & SSJ_DEVICE_PTRS) != 0;
+    const bool count_only = (batch->flags & SSJ_COUNT_ONLY) != 0;
+    cudaStream_t s = ctx->stream;
+    uint64_t n_cands = 0;
+    VerifyArgs a;
+    uint64_t* d_count = nullptr;
+    if (!dev) {
+        st = validate_host_batch(ctx, batch, &n_cands);
+        if (st != SSJ_OK) return st;
+        a = make_args(ctx, batch, *R, *S, n_cands);
+        // device staging: probe ids, offsets, candidates, count, output
+        const uint64_t out_cap = count_only ? 0 : std::min<uint64_t>(cap, n_cands);
+        size_t off = 0;
+        const size_t o_probe = off; off += align256(4ull * std::max<uint32_t>(batch->n_probes, 1));
+        const size_t o_offs = off;  off += align256(8ull * (batch->n_probes + 1));
+        const size_t o_cand = off;  off += align256(4ull * std::max<uint64_t>(n_cands, 1));
+        const size_t o_cnt = off;   off += 256;
+        const size_t o_out = off;   off += align256(sizeof(ssj_triple) * std::max<uint64_t>(out_cap, 1));
+        st = ensure_device_buffer(ctx, &ctx->io, &ctx->io_bytes, off);
+        if (st != SSJ_OK) return st;
+        char* base = static_cast<char*>(ctx->io);
+        uint32_t* d_probe = reinterpret_cast<uint32_t*>(base + o_probe);
+        uint64_t* d_offs = reinterpret_cast<uint64_t*>(base + o_offs);
+        uint32_t* d_cand = reinterpret_cast<uint32_t*>(base + o_cand);
+        d_count = reinterpret_cast<uint64_t*>(base + o_cnt);
+        ssj_triple* d_out = reinterpret_cast<ssj_triple*>(base + o_out);
+        if (batch->n_probes) {
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_probe, batch->probe_ids, 4ull * batch->n_probes, cudaMemcpyHostToDevice, s));
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_offs, batch->cand_offsets, 8ull * (batch->n_probes + 1),
+                                          cudaMemcpyHostToDevice, s));
+        }
+        if (n_cands)
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_cand, batch->cand_ids, 4ull * n_cands, cudaMemcpyHostToDevice, s));
+        a.probe_ids = d_probe;
+        a.cand_offsets = d_offs;
+        a.cand_ids = d_cand;
+        a.out = d_out;
+        a.cap = out_cap;
+    } else {
+        n_cands = batch->n_cands;
+        if (batch->n_probes && (!batch->probe_ids || !batch->cand_offsets))
+            return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
+        if (n_cands && !batch->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
+        a = make_args(ctx, batch, *R, *S, n_cands);
+        a.probe_ids = batch->probe_ids;
+        a.cand_offsets = batch->cand_offsets;
+        a.cand_ids = batch->cand_ids;
+        a.out = out;
+        a.cap = count_only ? 0 : cap;
+        st = ensure_device_buffer(ctx, &ctx->io, &ctx->io_bytes, 256);
+        if (st != SSJ_OK) return st;
+        d_count = static_cast<uint64_t*>(ctx->io);
+    }
+    st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(batch->n_probes, n_cands));
+    if (st != SSJ_OK) return st;
+    a.count = reinterpret_cast<unsigned long long*>(d_count);
+    bind_workspace(a, ctx->ws, batch->n_probes, n_cands);
+    ctx->last_ctr = a.ctr;
+    cudaError_t e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_verify");
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_count, d_count, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_err, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const uint64_t count = *ctx->h_count;
+    const uint32_t derr = *ctx->h_err;
+    *n_out = count;
+    if (derr)
+        return fail(ctx, SSJ_EINVAL, "batch rejected by the device checks (code %u: %s%s%s)", derr,
+                    (derr & ERR_PROBE_ID) ? "probe id out of range " : "",
+                    (derr & ERR_CAND_ID) ? "candidate id out of range " : "",
+                    (derr & ERR_OFFSETS) ? "offsets not nondecreasing from 0 to n_cands" : "");
+    if (count_only) return SSJ_OK;
+    const uint64_t n_copy = std::min(count, cap);
+    if (!dev) {
+        if (n_copy) CUDA_TRY(ctx, cudaMemcpy(out, a.out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost));
+        if (batch->flags & SSJ_SORTED) std::sort(out, out + n_copy, triple_less);
+    } else if ((batch->flags & SSJ_SORTED) && n_copy) {
+        std::vector<ssj_triple> h(n_copy);
+        CUDA_TRY(ctx, cudaMemcpy(h.data(), out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost));
+        std::sort(h.begin(), h.end(), triple_less);
+        CUDA_TRY(ctx, cudaMemcpy(out, h.data(), sizeof(ssj_triple) * n_copy, cudaMemcpyHostToDevice));
+    }
+    if (count > cap) return fail(ctx, SSJ_ENOMEM, "%llu result pairs, room for %llu", (unsigned long long)count,
+                                 (unsigned long long)cap);
+    return SSJ_OK;
+}
+
+// ===========================================================================
+// Serving: continuous batching
+// ===========================================================================
+
+namespace {
+
+uint64_t batch_device_bytes(uint32_t n_probes, uint64_t n_cands, bool count_only, bool dev_ptrs) {
+    uint64_t b = 0;
+    if (!dev_ptrs) {
+        b += align256(4ull * std::max<uint32_t>(n_probes, 1));
+        b += align256(8ull * (n_probes + 1));
+        b += align256(4ull * std::max<uint64_t>(n_cands, 1));
+    }
+    b += 256;  // count
+    b += align256(workspace_bytes(n_probes, n_cands));
+    if (!count_only) b += align256(sizeof(ssj_triple) * std::max<uint64_t>(n_cands, 1));
+    return b;
+}
+
+void completion_loop(ssj_ctx* ctx, int slot) {
+    cudaSetDevice(ctx->device);
+    Slot& sl = ctx->slots[slot];
+    for (;;) {
+        Ticket* t = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(ctx->mu);
+            ctx->cv.wait(lk, [&] { return ctx->stopping || sl.pending != nullptr; });
+            if (!sl.pending) return;  // stopping with nothing in flight
+            t = sl.pending;
+        }
+        std::string err;
+        cudaError_t e = cudaEventSynchronize(t->kernel_done);
+        uint64_t count = 0;
+        if (e == cudaSuccess) {
+            count = *sl.h_count;
+            if (*sl.h_err) err = "device-side batch check failed";
+        } else {
+            err = std::string("batch failed: ") + cudaGetErrorString(e);
+        }
+        if (err.empty() && !(t->flags & SSJ_COUNT_ONLY)) {
+            const uint64_t n_copy = std::min(count, t->out_cap);
+            if (n_copy) {
+                if (ensure_pinned(nullptr, &sl.h_out, &sl.h_out_cap, n_copy) != SSJ_OK) err = "pinned output";
+                if (err.empty()) {
+                    e = cudaMemcpyAsync(sl.h_out, t->d_out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost,
+                                        sl.stream);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(sl.stream);
+                    if (e != cudaSuccess) err = std::string("result copy: ") + cudaGetErrorString(e);
+                }
+            }
+        }
+        if (t->d_mem) {
+            cudaFreeAsync(t->d_mem, sl.stream);
+            t->d_mem = nullptr;
+        }
+        {
+            std::unique_lock<std::mutex> lk(ctx->mu);
+            t->count = count;
+            t->h_out = sl.h_out;
+            t->error = err;
+            t->state = err.empty() ? TicketState::kDone : TicketState::kFailed;
+            ctx->used_bytes -= t->bytes;
+            t->bytes = 0;
+            sl.pending = nullptr;
+        }
+        ctx->cv.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t* ticket) {
+    if (!ctx || !batch || !ticket) return fail(ctx, SSJ_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    Collection *R, *S;
+    ssj_status st = resolve(ctx, batch, &R, &S);
+    if (st != SSJ_OK) return st;
+    const bool dev = (batch->flags & SSJ_DEVICE_PTRS) != 0;
+    const bool count_only = (batch->flags & SSJ_COUNT_ONLY) != 0;
+    uint64_t n_cands = batch->n_cands;
+    if (!dev) {
+        lk.unlock();  // validation reads only the caller's arrays and immutable collection sizes
+        st = validate_host_batch(ctx, batch, &n_cands);
+        lk.lock();
+        if (st != SSJ_OK) return st;
+    }
+    const uint64_t bytes = batch_device_bytes(batch->n_probes, n_cands, count_only, dev);
+    if (bytes > ctx->budget) return fail(ctx, SSJ_EINVAL, "batch needs %llu bytes, budget is %llu",
+                                         (unsigned long long)bytes, (unsigned long long)ctx->budget);
+    int slot = -1;
+    for (size_t i = 0; i < ctx->slots.size(); ++i)
+        if (!ctx->slots[i].busy) { slot = (int)i; break; }
+    if (slot < 0 || ctx->used_bytes + bytes > ctx->budget) return SSJ_EAGAIN;
+    // reserve the slot, the budget and the collections, then work without the lock
+    Slot& sl = ctx->slots[slot];
+    sl.busy = true;
+    ctx->used_bytes += bytes;
+    R->busy++;
+    S->busy++;
+    std::unique_ptr<Ticket> t(new Ticket());
+    t->id = ctx->next_ticket++;
+    VerifyArgs a = make_args(ctx, batch, *R, *S, n_cands);
+    lk.unlock();
+
+    auto unreserve = [&](ssj_status code) {
+        std::unique_lock<std::mutex> l2(ctx->mu);
+        sl.busy = false;
+        ctx->used_bytes -= bytes;
+        R->busy--;
+        S->busy--;
+        return code;
+    };
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = sl.stream;
+    t->R = batch->R;
+    t->S = batch->S;
+    t->flags = batch->flags;
+    t->stream = s;
+    t->kernel_done = sl.ev;
+    t->slot = slot;
+    t->bytes = bytes;
+    cudaError_t e = cudaMallocFromPoolAsync(&t->d_mem, bytes, ctx->pool, s);
+    if (e != cudaSuccess) return unreserve(fail(ctx, SSJ_ENOMEM, "pool allocation: %s", cudaGetErrorString(e)));
+    char* base = static_cast<char*>(t->d_mem);
+    size_t off = 0;
+    if (!dev) {
+        // copy host inputs to pinned staging, so the caller may reuse them at once
+        if ((st = ensure_pinned(ctx, &sl.h_probe, &sl.h_probe_cap, std::max<uint64_t>(batch->n_probes, 1))) != SSJ_OK ||
+            (st = ensure_pinned(ctx, &sl.h_offs, &sl.h_offs_cap, batch->n_probes + 1ull)) != SSJ_OK ||
+            (st = ensure_pinned(ctx, &sl.h_cand, &sl.h_cand_cap, std::max<uint64_t>(n_cands, 1))) != SSJ_OK) {
+            cudaFreeAsync(t->d_mem, s);
+            return unreserve(st);
+        }
+        if (batch->n_probes) {
+            memcpy(sl.h_probe, batch->probe_ids, 4ull * batch->n_probes);
+            memcpy(sl.h_offs, batch->cand_offsets, 8ull * (batch->n_probes + 1));
+        } else {
+            sl.h_offs[0] = 0;
+        }
+        if (n_cands) memcpy(sl.h_cand, batch->cand_ids, 4ull * n_cands);
+        uint32_t* d_probe = reinterpret_cast<uint32_t*>(base + off); off += align256(4ull * std::max<uint32_t>(batch->n_probes, 1));
+        uint64_t* d_offs = reinterpret_cast<uint64_t*>(base + off);  off += align256(8ull * (batch->n_probes + 1));
+        uint32_t* d_cand = reinterpret_cast<uint32_t*>(base + off);  off += align256(4ull * std::max<uint64_t>(n_cands, 1));
+        if (batch->n_probes) {
+            cudaMemcpyAsync(d_probe, sl.h_probe, 4ull * batch->n_probes, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(d_offs, sl.h_offs, 8ull * (batch->n_probes + 1), cudaMemcpyHostToDevice, s);
+        }
+        if (n_cands) cudaMemcpyAsync(d_cand, sl.h_cand, 4ull * n_cands, cudaMemcpyHostToDevice, s);
+        a.probe_ids = d_probe;
+        a.cand_offsets = d_offs;
+        a.cand_ids = d_cand;
+    } else {
+        a.probe_ids = batch->probe_ids;
+        a.cand_offsets = batch->cand_offsets;
+        a.cand_ids = batch->cand_ids;
+    }
+    uint64_t* d_count = reinterpret_cast<uint64_t*>(base + off); off += 256;
+    void* ws = base + off; off += align256(workspace_bytes(batch->n_probes, n_cands));
+    ssj_triple* d_out = count_only ? nullptr : reinterpret_cast<ssj_triple*>(base + off);
+    a.out = d_out;
+    a.cap = count_only ? 0 : n_cands;
+    a.count = reinterpret_cast<unsigned long long*>(d_count);
+    bind_workspace(a, ws, batch->n_probes, n_cands);
+    e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_count, d_count, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_err, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(t->d_mem, s);
+        return unreserve(cuda_fail(ctx, e, "submit"));
+    }
+    t->d_out = d_out;
+    t->out_cap = a.cap;
+    lk.lock();
+    Ticket* raw = t.get();
+    ctx->tickets[raw->id] = std::move(t);
+    sl.pending = raw;
+    *ticket = raw->id;
+    lk.unlock();
+    ctx->cv.notify_all();
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_poll(ssj_ctx* ctx, uint64_t ticket, int timeout_ms, int* done) {
+    if (!ctx || !done) return SSJ_EINVAL;
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(ctx, SSJ_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Ticket* t = it->second.get();
+    auto ready = [&] { return t->state != TicketState::kRunning; };
+    if (timeout_ms < 0) {
+        ctx->cv.wait(lk, ready);
+    } else if (timeout_ms > 0) {
+        ctx->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    }
+    *done = ready() ? 1 : 0;
+    if (!*done) return SSJ_ETIMEDOUT;
+    if (t->state == TicketState::kFailed) return fail(ctx, SSJ_EDEVICE, "%s", t->error.c_str());
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_results(ssj_ctx* ctx, uint64_t ticket, ssj_triple* out, uint64_t cap, uint64_t* n_out) {
+    if (!ctx || !n_out) return SSJ_EINVAL;
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(ctx, SSJ_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Ticket* t = it->second.get();
+    if (t->state == TicketState::kRunning) return SSJ_EAGAIN;
+    *n_out = t->count;
+    if (!out && t->state == TicketState::kDone) return SSJ_OK;
+    ssj_status st = SSJ_OK;
+    if (t->state == TicketState::kFailed) {
+        st = fail(ctx, SSJ_EDEVICE, "%s", t->error.c_str());
+    } else if (!(t->flags & SSJ_COUNT_ONLY)) {
+        if (cap < t->count) return fail(ctx, SSJ_ENOMEM, "%llu result pairs, room for %llu",
+                                        (unsigned long long)t->count, (unsigned long long)cap);
+        if (t->count) memcpy(out, t->h_out, sizeof(ssj_triple) * t->count);
+        if (t->flags & SSJ_SORTED) std::sort(out, out + t->count, triple_less);
+    }
+    ctx->slots[t->slot].busy = false;
+    auto ir = ctx->colls.find(t->R);
+    if (ir != ctx->colls.end() && ir->second.busy) ir->second.busy--;
+    auto is = ctx->colls.find(t->S);
+    if (is != ctx->colls.end() && is->second.busy) is->second.busy--;
+    ctx->tickets.erase(it);
+    return st;
+}
+
+extern "C" ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double* plan_ms, double* verify_ms) {
+    if (!ctx || !launches || !plan_ms || !verify_ms) return SSJ_EINVAL;
+    *launches = 0;
+    *plan_ms = 0;
+    *verify_ms = 0;
+    if (!ctx->profile) return fail(ctx, SSJ_EINVAL, "context was created without SSJ_CTX_PROFILE");
+    DeviceGuard g(ctx->device);
+    for (size_t i = 0; i < ctx->prof_used; ++i) {
+        cudaEvent_t* ev = &ctx->prof_ev[3 * i];
+        CUDA_TRY(ctx, cudaEventSynchronize(ev[2]));
+        float a = 0, b = 0;
+        CUDA_TRY(ctx, cudaEventElapsedTime(&a, ev[0], ev[1]));
+        CUDA_TRY(ctx, cudaEventElapsedTime(&b, ev[1], ev[2]));
+        *plan_ms += a;
+        *verify_ms += b;
+    }
+    *launches = (uint32_t)ctx->prof_used;
+    ctx->prof_used = 0;
+    return SSJ_OK;
+}

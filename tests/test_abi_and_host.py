@@ -1,0 +1,122 @@
+"""CPU-only checks of the C ABI library and the host-side feeder.
+
+No compute call reaches the GPU here: the library is loaded, its exported
+symbols are compared with the declarations in include/*.h, and the CPU
+candidate feeder (host code) is checked for completeness against the oracle.
+"""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import ROOT
+
+import paper_1812_09141_gb300 as ssj
+from paper_1812_09141_gb300 import _build
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    return ssj.lib()
+
+
+def _declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(ssj_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_function_is_exported_and_bound():
+    declared = _declared_functions()
+    assert "ssj_verify_batch" in declared and "ssj_submit" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", ssj.LIB_PATH], capture_output=True, text=True, check=True)
+    exported = {ln.split()[-1] for ln in out.stdout.splitlines() if " T " in ln}
+    missing = declared - exported
+    assert not missing, f"declared but not exported: {missing}"
+    assert declared == set(ssj.SIGNATURES), (declared ^ set(ssj.SIGNATURES))
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1812_09141_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\boracle\b", text), f"{f} mentions the oracle"
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(ssj.SsjError):
+        ssj.ssj_create(0)
+
+
+# ---------------------------------------------------------------- feeder (host code)
+
+def _planted(n=600, frac=0.15, edits=2, seed=1001):
+    spec = synth.tiny_self_join(seed=seed, n=n)
+    spec.plant_frac, spec.plant_edits = frac, edits
+    return synth.collection(spec)
+
+
+@pytest.mark.parametrize("pq", [(19, 20), (4, 5), (7, 10), (3, 5), (1, 2), (1, 1)])
+def test_feeder_candidates_cover_every_result(pq):
+    c = _planted()
+    pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, *pq, n_threads=3, chunk=997)
+    assert co[0] == 0 and np.all(np.diff(co.astype(np.int64)) >= 0) and co[-1] == len(ci)
+    # every pair at most once, never (r, r)
+    pairs = set()
+    for k in range(len(pr)):
+        for s in ci[co[k]:co[k + 1]]:
+            key = (min(pr[k], s), max(pr[k], s))
+            assert pr[k] != s and key not in pairs
+            pairs.add(key)
+    bf = oracle.bruteforce_self(c.offsets, c.tokens, *pq)
+    assert {(int(r), int(s)) for r, s, _ in bf} <= pairs
+    tr = oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, *pq, pr, co, ci)
+    assert np.array_equal(oracle.sort_triples(tr), oracle.sort_triples(bf))
+
+
+def test_feeder_threads_and_chunking_do_not_change_candidates():
+    c = _planted(n=800)
+    ref = ssj.feeder_all(c.offsets, c.tokens, 3, 5, n_threads=1, chunk=1 << 20)
+    for threads, chunk in [(4, 1), (2, 13), (8, 4096)]:
+        got = ssj.feeder_all(c.offsets, c.tokens, 3, 5, n_threads=threads, chunk=chunk)
+        # chunking may split a probe's list; compare the flat (probe, cand) sequence
+        def flat(b):
+            pr, co, ci = b
+            return np.repeat(pr, np.diff(co.astype(np.int64))), ci
+        assert all(np.array_equal(x, y) for x, y in zip(flat(ref), flat(got)))
+
+
+def test_feeder_rejects_bad_input():
+    c = synth.from_lists([[1, 2], [3, 3]])
+    with pytest.raises(ssj.SsjError):
+        ssj.ssj_feeder_create(c.offsets, c.tokens, 1, 2)
+    c = synth.from_lists([[1, 2], [3]])
+    with pytest.raises(ssj.SsjError):
+        ssj.ssj_feeder_create(c.offsets, c.tokens, 0, 2)
+    with pytest.raises(ssj.SsjError):
+        ssj.ssj_feeder_create(c.offsets, c.tokens, 3, 2)
+
+
+def test_feeder_handles_empty_sets_and_empty_collection():
+    c = synth.from_lists([[], [1, 2], [], [1, 2]])
+    pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, 1, 2)
+    assert sorted((min(a, b), max(a, b)) for a, b in zip(np.repeat(pr, np.diff(co.astype(np.int64))), ci)) == [(1, 3)]
+    c = synth.from_lists([])
+    pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, 1, 2)
+    assert len(pr) == 0 and len(ci) == 0

@@ -1,0 +1,346 @@
+"""GPU parity: the CUDA verification path against the CPU oracle.
+
+Every comparison is bit-exact on sorted (r, s, overlap) triples: the join
+result is unique, only its order is free.  Inputs come from the seeded
+generators in synth/, never from the CUDA path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+import paper_1812_09141_gb300 as ssj
+from paper_1812_09141_gb300 import _build
+
+pytestmark = pytest.mark.gpu
+
+GRANULARITIES = [0, ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK]
+T_ALL = [(19, 20), (9, 10), (17, 20), (4, 5), (3, 4), (7, 10), (13, 20), (3, 5)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    _build.build()
+    h = ssj.ssj_create(0)
+    yield h
+    ssj.ssj_destroy(h)
+
+
+def load(ctx, c, flags=ssj.SSJ_VALIDATE):
+    return ssj.ssj_load_collection(ctx, c.offsets, c.tokens, flags)
+
+
+def gpu(ctx, R, S, p, q, b, flags=0):
+    res = ssj.ssj_verify_batch(ctx, R, S, p, q, b.probe_ids, b.cand_offsets, b.cand_ids, flags=flags)
+    return ssj.triples_to_array(res)
+
+
+def ora(cR, cS, self_join, p, q, b, flags=oracle.EARLY):
+    return oracle.sort_triples(oracle.verify_batch(cR.offsets, cR.tokens, cS.offsets, cS.tokens, self_join, p, q,
+                                                   b.probe_ids, b.cand_offsets, b.cand_ids, flags=flags))
+
+
+def planted_tiny(n=1000, frac=0.1, edits=2, seed=1001):
+    spec = synth.tiny_self_join(seed=seed, n=n)
+    spec.plant_frac, spec.plant_edits = frac, edits
+    return synth.collection(spec)
+
+
+def feeder_batch(c, p, q, threads=8):
+    pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=threads)
+    return synth.Batch(pr, co, ci)
+
+
+# ----------------------------------------------------------------- tiny, all pairs
+
+@pytest.mark.parametrize("gran", GRANULARITIES)
+def test_tiny_all_pairs_planted_matches_bruteforce(ctx, gran):
+    c = planted_tiny()
+    h = load(ctx, c)
+    b = synth.all_pairs_batch(c.n)
+    assert b.n_cands == 499_500
+    for p, q in [(4, 5), (3, 5), (9, 10), (1, 1), (1, 10)]:
+        want = oracle.sort_triples(oracle.bruteforce_self(c.offsets, c.tokens, p, q))
+        got = gpu(ctx, h, h, p, q, b, gran)
+        assert np.array_equal(got, want), (gran, p, q, len(got), len(want))
+    ssj.ssj_unload_collection(ctx, h)
+
+
+@pytest.mark.parametrize("gran", GRANULARITIES)
+def test_tiny_every_overlap_matches(ctx, gran):
+    """SSJ_EMIT_ALL: all 499,500 overlaps of the tiny workload, element by element."""
+    c = synth.collection(synth.tiny_self_join())
+    h = load(ctx, c)
+    b = synth.all_pairs_batch(c.n)
+    want = ora(c, c, True, 4, 5, b, flags=oracle.EMIT_ALL)
+    got = gpu(ctx, h, h, 4, 5, b, ssj.SSJ_EMIT_ALL | gran)
+    assert len(got) == 499_500
+    assert np.array_equal(got, want)
+    ssj.ssj_unload_collection(ctx, h)
+
+
+# ----------------------------------------------------------------- prefix-filter workloads
+
+@pytest.mark.parametrize("renumber", [False, True])
+def test_short_sets_scaled_all_thresholds(ctx, renumber):
+    c = synth.collection(synth.short_sets(n=20_000))
+    h = load(ctx, c, ssj.SSJ_VALIDATE | (ssj.SSJ_RENUMBER_BY_FREQ if renumber else 0))
+    for p, q in [(9, 10), (4, 5), (7, 10), (3, 5)]:
+        b = feeder_batch(c, p, q)
+        want, _ = oracle.allpairs_self(c.offsets, c.tokens, p, q)
+        want = oracle.sort_triples(want)
+        assert np.array_equal(ora(c, c, True, p, q, b), want)
+        for gran in GRANULARITIES:
+            assert np.array_equal(gpu(ctx, h, h, p, q, b, gran), want), (p, q, gran)
+    ssj.ssj_unload_collection(ctx, h)
+
+
+def test_long_sets_scaled(ctx):
+    c = synth.collection(synth.long_sets(n=1500))
+    h = load(ctx, c)
+    for p, q in [(3, 5), (4, 5)]:
+        b = feeder_batch(c, p, q)
+        want = oracle.sort_triples(oracle.allpairs_self(c.offsets, c.tokens, p, q)[0])
+        for gran in GRANULARITIES:
+            assert np.array_equal(gpu(ctx, h, h, p, q, b, gran), want), (p, q, gran)
+        every = ora(c, c, True, p, q, b, flags=oracle.EMIT_ALL)
+        for gran in GRANULARITIES:
+            assert np.array_equal(gpu(ctx, h, h, p, q, b, ssj.SSJ_EMIT_ALL | gran), every), gran
+    ssj.ssj_unload_collection(ctx, h)
+
+
+def test_planted_long_sets_many_survivors(ctx):
+    spec = synth.long_sets(n=800)
+    spec.plant_frac, spec.plant_edits = 0.3, 20
+    c = synth.collection(spec)
+    h = load(ctx, c)
+    b = feeder_batch(c, 3, 5)
+    want = oracle.sort_triples(oracle.allpairs_self(c.offsets, c.tokens, 3, 5)[0])
+    assert len(want) > 50
+    for gran in GRANULARITIES:
+        assert np.array_equal(gpu(ctx, h, h, 3, 5, b, gran), want)
+    ssj.ssj_unload_collection(ctx, h)
+
+
+# ----------------------------------------------------------------- arbitrary batches
+
+@pytest.mark.parametrize("seed", range(3))
+def test_random_batches_self_and_rs(ctx, seed):
+    cR = planted_tiny(n=700, frac=0.3, edits=1, seed=50 + seed)
+    cS = planted_tiny(n=500, frac=0.3, edits=1, seed=80 + seed)
+    hR, hS = load(ctx, cR), load(ctx, cS)
+    b = synth.random_batch(seed, cR.n, cR.n, 3000, 40)
+    b2 = synth.random_batch(seed + 100, cR.n, cS.n, 3000, 40)
+    for p, q in [(1, 10), (1, 3), (3, 5)]:
+        for gran in GRANULARITIES:
+            assert np.array_equal(gpu(ctx, hR, hR, p, q, b, gran), ora(cR, cR, True, p, q, b))
+            assert np.array_equal(gpu(ctx, hR, hS, p, q, b2, gran), ora(cR, cS, False, p, q, b2))
+            assert np.array_equal(gpu(ctx, hR, hS, p, q, b2, gran | ssj.SSJ_EMIT_ALL),
+                                  ora(cR, cS, False, p, q, b2, flags=oracle.EMIT_ALL))
+    ssj.ssj_unload_collection(ctx, hR)
+    ssj.ssj_unload_collection(ctx, hS)
+
+
+def test_edge_sets_and_sizes(ctx):
+    rng = np.random.default_rng(5)
+    sets = [[], [7], [7], [1, 2, 3], [1, 2, 3], list(range(0, 6000, 2)), list(range(0, 6000, 2)),
+            list(range(0, 5000, 2)) + [5001], list(range(1, 4000, 3)), list(range(100, 400)),
+            list(range(100, 399)) + [1000]]
+    for k in (31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 1023, 1024, 1025, 2047, 2048, 2049, 4093, 4100):
+        base = np.sort(rng.choice(20_000, size=k, replace=False))
+        other = base.copy()
+        other[rng.integers(0, k)] = 20_001 + k
+        sets.append(base.tolist())
+        sets.append(np.unique(other).tolist())
+    c = synth.from_lists(sets)
+    h = load(ctx, c)
+    b = synth.all_pairs_batch(c.n)
+    for p, q in [(1, 1), (9, 10), (1, 2), (1, 100)]:
+        want = oracle.sort_triples(oracle.bruteforce_self(c.offsets, c.tokens, p, q))
+        for gran in GRANULARITIES:
+            assert np.array_equal(gpu(ctx, h, h, p, q, b, gran), want), (p, q, gran)
+    every = ora(c, c, True, 1, 2, b, flags=oracle.EMIT_ALL)
+    for gran in GRANULARITIES:
+        assert np.array_equal(gpu(ctx, h, h, 1, 2, b, ssj.SSJ_EMIT_ALL | gran), every)
+    ssj.ssj_unload_collection(ctx, h)
+
+
+def test_empty_and_degenerate_batches(ctx):
+    c = planted_tiny(n=50)
+    h = load(ctx, c)
+    empty = synth.Batch(np.zeros(0, np.uint32), np.zeros(1, np.uint64), np.zeros(0, np.uint32))
+    assert len(gpu(ctx, h, h, 1, 2, empty)) == 0
+    zero_c = synth.Batch(np.arange(5, dtype=np.uint32), np.zeros(6, np.uint64), np.zeros(0, np.uint32))
+    assert len(gpu(ctx, h, h, 1, 2, zero_c)) == 0
+    # only self pairs
+    selfb = synth.Batch(np.arange(10, dtype=np.uint32), np.arange(11, dtype=np.uint64), np.arange(10, dtype=np.uint32))
+    assert len(gpu(ctx, h, h, 1, 100, selfb)) == 0
+    # many probes with zero candidates around a few with many (chunks span many probes)
+    k = 200
+    counts = np.zeros(k, dtype=np.int64)
+    counts[[3, 77, 150]] = [40, 1, 33]
+    offs = np.zeros(k + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum(counts)
+    cands = np.random.default_rng(1).integers(0, c.n, size=int(offs[-1])).astype(np.uint32)
+    b = synth.Batch(np.random.default_rng(2).integers(0, c.n, size=k).astype(np.uint32), offs, cands)
+    for gran in GRANULARITIES:
+        assert np.array_equal(gpu(ctx, h, h, 1, 50, b, gran | ssj.SSJ_EMIT_ALL),
+                              ora(c, c, True, 1, 50, b, flags=oracle.EMIT_ALL))
+    ssj.ssj_unload_collection(ctx, h)
+
+
+# ----------------------------------------------------------------- API behaviour
+
+def test_count_only_sorted_and_capacity(ctx):
+    c = planted_tiny(n=600, frac=0.3)
+    h = load(ctx, c)
+    b = synth.all_pairs_batch(c.n)
+    want = oracle.sort_triples(oracle.bruteforce_self(c.offsets, c.tokens, 1, 2))
+    n = ssj.ssj_verify_batch(ctx, h, h, 1, 2, b.probe_ids, b.cand_offsets, b.cand_ids, flags=ssj.SSJ_COUNT_ONLY)
+    assert n == len(want)
+    res = ssj.ssj_verify_batch(ctx, h, h, 1, 2, b.probe_ids, b.cand_offsets, b.cand_ids, flags=ssj.SSJ_SORTED)
+    arr = np.stack([res["r"], res["s"], res["overlap"]], axis=1)
+    assert np.array_equal(arr, want)  # already in (r, s) order
+    with pytest.raises(ssj.SsjError) as ei:
+        ssj.ssj_verify_batch(ctx, h, h, 1, 2, b.probe_ids, b.cand_offsets, b.cand_ids, cap=len(want) - 1)
+    assert ei.value.status == ssj.SSJ_ENOMEM
+    ssj.ssj_unload_collection(ctx, h)
+
+
+def test_invalid_inputs_are_rejected(ctx):
+    c = planted_tiny(n=30)
+    h = load(ctx, c)
+    b = synth.all_pairs_batch(c.n)
+    for args in [(0, 2), (3, 2), (1, 2 ** 31)]:
+        with pytest.raises(ssj.SsjError) as ei:
+            ssj.ssj_verify_batch(ctx, h, h, *args, b.probe_ids, b.cand_offsets, b.cand_ids)
+        assert ei.value.status == ssj.SSJ_EINVAL
+    bad = b.cand_ids.copy()
+    bad[5] = c.n
+    with pytest.raises(ssj.SsjError):
+        ssj.ssj_verify_batch(ctx, h, h, 1, 2, b.probe_ids, b.cand_offsets, bad)
+    with pytest.raises(ssj.SsjError):
+        ssj.ssj_verify_batch(ctx, h, 999, 1, 2, b.probe_ids, b.cand_offsets, b.cand_ids)
+    unsorted = synth.from_lists([[3, 1]])
+    with pytest.raises(ssj.SsjError):
+        ssj.ssj_load_collection(ctx, unsorted.offsets, unsorted.tokens, ssj.SSJ_VALIDATE)
+    hr = load(ctx, c, ssj.SSJ_RENUMBER_BY_FREQ)
+    with pytest.raises(ssj.SsjError):
+        ssj.ssj_verify_batch(ctx, h, hr, 1, 2, b.probe_ids, b.cand_offsets, b.cand_ids)
+    assert ssj.ssj_collection_info(ctx, h) == (c.n, len(c.tokens))
+    ssj.ssj_unload_collection(ctx, h)
+    ssj.ssj_unload_collection(ctx, hr)
+
+
+def test_device_pointers_sync_and_async(ctx):
+    import torch
+    c = planted_tiny(n=900, frac=0.2)
+    h = load(ctx, c)
+    b = synth.all_pairs_batch(c.n)
+    want = oracle.sort_triples(oracle.bruteforce_self(c.offsets, c.tokens, 3, 5))
+    dev = torch.device("cuda:0")
+    pr = torch.from_numpy(b.probe_ids.astype(np.int32)).to(dev)
+    co = torch.from_numpy(b.cand_offsets.astype(np.int64)).to(dev)
+    ci = torch.from_numpy(b.cand_ids.astype(np.int32)).to(dev)
+    cap = 100_000
+    out = torch.zeros(cap * 3, dtype=torch.int32, device=dev)
+    n = ssj.ssj_verify_batch(ctx, h, h, 3, 5, pr, co, ci, flags=ssj.SSJ_DEVICE_PTRS, out=out, cap=cap,
+                             n_cands=b.n_cands)
+    got = out[:3 * n].view(-1, 3).cpu().numpy().astype(np.uint32)
+    assert np.array_equal(oracle.sort_triples(got), want)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream()
+    ssj.ssj_reserve(ctx, b.n_probes, b.n_cands)
+    with torch.cuda.stream(stream):
+        out.zero_()
+        ssj.ssj_verify_batch_async(ctx, h, h, 3, 5, pr, co, ci, b.n_cands, out, cap, cnt,
+                                   stream=stream.cuda_stream)
+    stream.synchronize()
+    n2 = int(cnt.item())
+    got2 = out[:3 * n2].view(-1, 3).cpu().numpy().astype(np.uint32)
+    assert np.array_equal(oracle.sort_triples(got2), want)
+    assert ssj.ssj_device_error(ctx) == 0
+    # a bad candidate id is caught on the device and reported
+    ci_bad = ci.clone()
+    ci_bad[17] = c.n + 5
+    ssj.ssj_verify_batch_async(ctx, h, h, 3, 5, pr, co, ci_bad, b.n_cands, out, cap, cnt)
+    assert ssj.ssj_device_error(ctx) & 2
+    ssj.ssj_unload_collection(ctx, h)
+
+
+def test_serving_results_alone_equal_results_in_the_mix(ctx):
+    """Continuous batching: batches admitted together give what each gives alone."""
+    c = synth.collection(synth.short_sets(n=30_000))
+    h = load(ctx, c)
+    batches = []
+    for p, q in [(9, 10), (4, 5), (7, 10), (3, 5)]:
+        b = feeder_batch(c, p, q)
+        # split into uneven pieces
+        cuts = [0, b.n_probes // 7, b.n_probes // 2, b.n_probes]
+        for a, z in zip(cuts[:-1], cuts[1:]):
+            o = b.cand_offsets[a:z + 1]
+            batches.append(((p, q), synth.Batch(b.probe_ids[a:z], o - o[0], b.cand_ids[int(o[0]):int(o[-1])])))
+    alone = [gpu(ctx, h, h, p, q, bb) for (p, q), bb in batches]
+    sctx = ssj.ssj_create(0, mem_budget_bytes=256 << 20, max_inflight=3)
+    try:
+        hs = load(sctx, c)
+        pending, done = {}, {}
+        queue = list(enumerate(batches))
+        while queue or pending:
+            while queue:
+                i, ((p, q), bb) = queue[0]
+                t = ssj.ssj_submit(sctx, hs, hs, p, q, bb.probe_ids, bb.cand_offsets, bb.cand_ids)
+                if t is None:
+                    break
+                pending[t] = i
+                queue.pop(0)
+            for t in list(pending):
+                if ssj.ssj_poll(sctx, t, 1):
+                    done[pending.pop(t)] = ssj.triples_to_array(ssj.ssj_results(sctx, t))
+        for i, want in enumerate(alone):
+            assert np.array_equal(done[i], want), i
+    finally:
+        ssj.ssj_destroy(sctx)
+    ssj.ssj_unload_collection(ctx, h)
+
+
+# ----------------------------------------------------------------- full-size workloads
+
+def test_full_short_sets_all_thresholds(ctx):
+    """200,000 short sets (the bench workload), every threshold, exact result sets."""
+    c = synth.collection(synth.short_sets())
+    h = load(ctx, c, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
+    for p, q in [(9, 10), (4, 5), (7, 10), (3, 5)]:
+        b = feeder_batch(c, p, q)
+        want = oracle.sort_triples(oracle.allpairs_self(c.offsets, c.tokens, p, q)[0])
+        assert np.array_equal(gpu(ctx, h, h, p, q, b), want), (p, q)
+    ssj.ssj_unload_collection(ctx, h)
+
+
+def test_full_long_sets_sampled(ctx):
+    """50,000 long sets at t = 3/5 (about 1e8 candidates): every reported triple is re-verified by
+    the oracle, and a uniform sample of candidate pairs is checked for membership."""
+    c = synth.collection(synth.long_sets())
+    h = load(ctx, c, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
+    b = feeder_batch(c, 3, 5)
+    got = gpu(ctx, h, h, 3, 5, b)
+    n = ssj.ssj_verify_batch(ctx, h, h, 3, 5, b.probe_ids, b.cand_offsets, b.cand_ids, flags=ssj.SSJ_COUNT_ONLY)
+    assert n == len(got)
+    assert len(np.unique(got[:, :2], axis=0)) == len(got)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(len(got), size=min(len(got), 20_000), replace=False) if len(got) else []
+    for r, s, o in got[idx]:
+        ok, oo, _, _ = oracle.verify_pair(c.set(r), c.set(s), 3, 5, early=False)
+        assert ok and oo == o
+    # membership of a uniform sample of candidates
+    pair_probe = np.repeat(b.probe_ids, np.diff(b.cand_offsets.astype(np.int64)))
+    pick = rng.choice(b.n_cands, size=50_000, replace=False)
+    keys = set(map(tuple, got[:, :2].tolist()))
+    for m in pick:
+        r, s = int(pair_probe[m]), int(b.cand_ids[m])
+        ok, _, _, _ = oracle.verify_pair(c.set(r), c.set(s), 3, 5)
+        assert ok == ((min(r, s), max(r, s)) in keys)
+    ssj.ssj_unload_collection(ctx, h)
