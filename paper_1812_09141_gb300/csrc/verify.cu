@@ -365,10 +365,11 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
             const bool valid = c < a.n_cands;
 
             // resolve the probe of each lane: k = hint + #{offsets <= c}
-            uint32_t kk = a.hint[m];
+            // (every shuffle below is executed by all 32 lanes)
+            uint32_t kk = min(a.hint[m], a.n_probes - 1);
             uint32_t k = kk;
             bool resolved = !valid;
-            for (;;) {
+            for (uint32_t guard = 0;; ++guard) {
                 const uint32_t idx = kk + 1 + lane;
                 const uint64_t b = idx <= a.n_probes ? a.cand_offsets[idx] : ~0ull;
                 uint32_t pos = 0;
@@ -377,9 +378,17 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
                     const uint64_t bm = __shfl_sync(kFull, b, pos + step - 1);
                     if (bm <= c) pos += step;
                 }
-                if (pos == 31 && __shfl_sync(kFull, b, 31) <= c) pos = 32;
+                const uint64_t b_last = __shfl_sync(kFull, b, 31);
+                if (pos == 31 && b_last <= c) pos = 32;
                 if (!resolved && pos < 32) { k = kk + pos; resolved = true; }
                 if (__all_sync(kFull, resolved)) break;
+                // offsets are validated by plan_kernel, so the owner is found within
+                // n_probes/32 windows; the guard only turns a broken invariant into an error
+                if (guard > (a.n_probes >> 5) + 1 || kk + 32 >= a.n_probes) {
+                    if (lane == 0) atomicOr(&a.ctr->err, ERR_OFFSETS);
+                    if (!resolved) { k = a.n_probes; resolved = true; }
+                    break;
+                }
                 kk += 32;
             }
 
