@@ -236,7 +236,7 @@ def run_ours(args, rank, world, local_rank):
         dev_batches.append((p, q, t_pr, t_co, t_ci, len(pr), len(ci), out, cap, cnt))
         max_probes, max_cands = max(max_probes, len(pr)), max(max_cands, len(ci))
     ssj.ssj_reserve(ctx, max_probes, max_cands)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush = torch.empty(max(args.l2_flush_mb << 18, 1), dtype=torch.int32, device=dev)
     torch.cuda.synchronize(dev)
 
     def step(events=None):
@@ -291,12 +291,12 @@ def run_ours(args, rank, world, local_rank):
         ti = torch.from_numpy(ci.astype(np.uint32).view(np.int32)).pin_memory()
         pinned.append((p, q, tp.numpy().view(np.uint32), tc.numpy().view(np.uint64), ti.numpy().view(np.uint32),
                        (tp, tc, ti)))
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 20))
     e2e_t = 0.0
     h2d = sum(4 * len(b[2]) + 8 * (len(b[2]) + 1) + 4 * len(b[4]) for b in pinned)
     d2h = 0
     with torch.cuda.stream(stream):
-        for it in range(e2e_steps + 1):
+        for it in range(e2e_steps + 1 if e2e_steps else 0):
             flush.fill_(1)
             stream.synchronize()
             t0 = time.perf_counter()
@@ -314,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
 
     result = {"total_ms": total_ms, "step_ms": step_ms, "batch_ms": batch_ms, "verify_ms": verify_ms,
               "plan_ms": plan_ms, "launches": launches, "counts": counts, "pairs_step": pairs_step,
-              "e2e_value": pairs_step * e2e_steps / e2e_t * world, "h2d": h2d, "d2h": d2h,
+              "e2e_value": pairs_step * e2e_steps / e2e_t * world if e2e_t > 0 else None, "h2d": h2d, "d2h": d2h,
               "clocks": clocks.summary(), "cfg": cfg}
     return result, c, batches
 
@@ -327,6 +327,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="short_sets")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--l2-flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
+                    help="bytes written between timed steps to evict L2 (0 disables; only for profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
@@ -342,7 +345,7 @@ def main():
         batches = make_batches(c, ts)
         import oracle
         pairs_step = sum(len(b[4]) for b in batches)
-        for _ in range(args.warmup if args.warmup < 2 else 1):
+        for _ in range(1):
             for p, q, pr, co, ci in batches:
                 oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci)
         t0 = time.perf_counter()
@@ -375,7 +378,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict(res["cfg"], pairs_per_step=pairs_step, batches_per_step=len(batches),
-                           l2="flushed before every timed step (512 MiB write); inputs fit in L2",
+                           l2=(f"flushed before every timed step ({args.l2_flush_mb} MiB write); inputs fit in L2"
+                               if args.l2_flush_mb else "not flushed (profiling run)"),
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU")}
     bm = sorted(res["batch_ms"])
     line["latency_ms"] = {"p50": float(np.percentile(bm, 50)), "p99": float(np.percentile(bm, 99)),

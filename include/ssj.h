@@ -240,12 +240,14 @@ ssj_status ssj_results(ssj_ctx* ctx, uint64_t ticket, ssj_triple* out, uint64_t 
  * run through ssj_submit are not recorded.  SSJ_EINVAL without the flag. */
 ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double* plan_ms, double* verify_ms);
 
-/* Granularity bins keyed by |r|+|s| (estimated per probe as 2|r|): a probe
- * whose key is <= thread_max_key is verified one pair per thread, <=
- * warp_max_key one pair per warp, otherwise one pair per thread block
- * (the rule of Section 5.4: per-thread work for small sets, cooperative
- * Intersect Path for large ones).  thread_max_key is capped at 256.
- * block_threads is 128, 256 or 512.  Zero leaves a value unchanged. */
+/* Granularity bins keyed by |r|+|s| (estimated per probe as 2|r|, since the
+ * length filter keeps |s| within [t|r|, |r|/t]): a probe whose key is <=
+ * thread_max_key is verified one pair per thread, <= warp_max_key one pair
+ * per warp, otherwise one pair per thread block (the rule of Section 5.4:
+ * per-thread work for small sets, cooperative Intersect Path for large
+ * ones).  Defaults 128 and 2048; thread_max_key is capped at 1024.
+ * block_threads is 128, 256 or 512 (default 256).  Zero leaves a value
+ * unchanged. */
 ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t warp_max_key,
                                uint32_t block_threads);
 

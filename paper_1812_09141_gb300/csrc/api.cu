@@ -25,6 +25,7 @@
 
 #include <cuda_runtime.h>
 
+#include "arith.h"
 #include "ssj_internal.h"
 
 namespace ssj {
@@ -105,7 +106,7 @@ struct ssj_ctx {
     bool own_stream = false;
     uint64_t budget = 0;
     uint32_t max_inflight = 0;
-    uint32_t thread_max_key = 64;
+    uint32_t thread_max_key = 128;
     uint32_t warp_max_key = 2048;
     uint32_t block_threads = 256;
     std::string err;
@@ -264,6 +265,8 @@ VerifyArgs make_args(ssj_ctx* ctx, const ssj_batch* b, const Collection& R, cons
     a.S = S.dev();
     a.p = b->p;
     a.q = b->q;
+    a.den = b->p + b->q;
+    a.magic = div_magic(a.den);
     a.self_join = b->R == b->S ? 1u : 0u;
     a.flags = vflags(b->flags);
     a.n_probes = b->n_probes;
@@ -534,7 +537,7 @@ extern "C" ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t*
 extern "C" ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands) {
     if (!ctx) return SSJ_EINVAL;
     DeviceGuard g(ctx->device);
-    return ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(n_probes, n_cands));
+    return ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(n_probes, n_cands, ctx->num_sms));
 }
 
 extern "C" ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* d_out, uint64_t cap,
@@ -548,7 +551,7 @@ extern "C" ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batc
     if (batch->n_cands && !batch->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
     if (cap && !d_out && !(batch->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output");
     DeviceGuard g(ctx->device);
-    st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(batch->n_probes, batch->n_cands));
+    st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(batch->n_probes, batch->n_cands, ctx->num_sms));
     if (st != SSJ_OK) return st;
     VerifyArgs a = make_args(ctx, batch, *R, *S, batch->n_cands);
     a.probe_ids = batch->probe_ids;
@@ -557,7 +560,7 @@ extern "C" ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batc
     a.out = d_out;
     a.cap = (batch->flags & SSJ_COUNT_ONLY) ? 0 : cap;
     a.count = reinterpret_cast<unsigned long long*>(d_count);
-    bind_workspace(a, ctx->ws, batch->n_probes, batch->n_cands);
+    bind_workspace(a, ctx->ws, batch->n_probes, batch->n_cands, ctx->num_sms);
     ctx->last_ctr = a.ctr;
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
     cudaError_t e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
@@ -639,10 +642,10 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
         if (st != SSJ_OK) return st;
         d_count = static_cast<uint64_t*>(ctx->io);
     }
-    st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(batch->n_probes, n_cands));
+    st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(batch->n_probes, n_cands, ctx->num_sms));
     if (st != SSJ_OK) return st;
     a.count = reinterpret_cast<unsigned long long*>(d_count);
-    bind_workspace(a, ctx->ws, batch->n_probes, n_cands);
+    bind_workspace(a, ctx->ws, batch->n_probes, n_cands, ctx->num_sms);
     ctx->last_ctr = a.ctr;
     cudaError_t e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_verify");
@@ -679,7 +682,7 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
 
 namespace {
 
-uint64_t batch_device_bytes(uint32_t n_probes, uint64_t n_cands, bool count_only, bool dev_ptrs) {
+uint64_t batch_device_bytes(uint32_t n_probes, uint64_t n_cands, bool count_only, bool dev_ptrs, int num_sms) {
     uint64_t b = 0;
     if (!dev_ptrs) {
         b += align256(4ull * std::max<uint32_t>(n_probes, 1));
@@ -687,7 +690,7 @@ uint64_t batch_device_bytes(uint32_t n_probes, uint64_t n_cands, bool count_only
         b += align256(4ull * std::max<uint64_t>(n_cands, 1));
     }
     b += 256;  // count
-    b += align256(workspace_bytes(n_probes, n_cands));
+    b += align256(workspace_bytes(n_probes, n_cands, num_sms));
     if (!count_only) b += align256(sizeof(ssj_triple) * std::max<uint64_t>(n_cands, 1));
     return b;
 }
@@ -759,7 +762,7 @@ extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t*
         lk.lock();
         if (st != SSJ_OK) return st;
     }
-    const uint64_t bytes = batch_device_bytes(batch->n_probes, n_cands, count_only, dev);
+    const uint64_t bytes = batch_device_bytes(batch->n_probes, n_cands, count_only, dev, ctx->num_sms);
     if (bytes > ctx->budget) return fail(ctx, SSJ_EINVAL, "batch needs %llu bytes, budget is %llu",
                                          (unsigned long long)bytes, (unsigned long long)ctx->budget);
     int slot = -1;
@@ -830,12 +833,12 @@ extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t*
         a.cand_ids = batch->cand_ids;
     }
     uint64_t* d_count = reinterpret_cast<uint64_t*>(base + off); off += 256;
-    void* ws = base + off; off += align256(workspace_bytes(batch->n_probes, n_cands));
+    void* ws = base + off; off += align256(workspace_bytes(batch->n_probes, n_cands, ctx->num_sms));
     ssj_triple* d_out = count_only ? nullptr : reinterpret_cast<ssj_triple*>(base + off);
     a.out = d_out;
     a.cap = count_only ? 0 : n_cands;
     a.count = reinterpret_cast<unsigned long long*>(d_count);
-    bind_workspace(a, ws, batch->n_probes, n_cands);
+    bind_workspace(a, ws, batch->n_probes, n_cands, ctx->num_sms);
     e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, nullptr);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_count, d_count, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_err, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);

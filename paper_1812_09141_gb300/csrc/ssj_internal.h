@@ -18,20 +18,30 @@ struct DevColl {
     uint32_t n_sets;
 };
 
-// Work item for block-per-pair verification: n candidates of probe r
-// starting at candidate index c0.
-struct BlockItem {
+// Work item for warp- or block-per-pair verification: n candidates of probe
+// set r starting at candidate index c0.
+struct WorkItem {
     uint32_t r;
     uint32_t n;
     uint64_t c0;
 };
 
+// One short pair of the compacted list: probe index k (into probe_ids) and
+// candidate set id s.
+struct PairRef {
+    uint32_t k;
+    uint32_t s;
+};
+
 // Per-call counters, cleared by one memset before the plan kernel.
 struct Counters {
-    uint32_t block_items;   // block items written by the plan kernel
-    uint32_t block_cursor;  // block items taken by the verify kernel
-    uint32_t chunk_cursor;  // 32-candidate chunks taken by the verify kernel
-    uint32_t err;           // device-side check bits (see ssj_device_error)
+    unsigned long long thread_pairs;  // entries of the compacted short-pair list
+    unsigned long long warp_items;    // warp work items written by the plan kernel
+    unsigned long long block_items;   // block work items written by the plan kernel
+    uint32_t block_cursor;            // dynamic cursors of the verify kernel
+    uint32_t warp_cursor;
+    uint32_t chunk_cursor;
+    uint32_t err;                     // device-side check bits (see ssj_device_error)
 };
 
 enum : uint32_t {
@@ -48,13 +58,16 @@ enum : uint32_t {
     VF_FORCE_BLOCK = 16u,
 };
 
-constexpr uint32_t kChunk = 32;          // candidates per flat chunk (one per lane)
-constexpr uint32_t kBlockItemCands = 32; // candidates per block work item
-constexpr uint32_t kThreadKeyCap = 256;  // largest |r|+|s| verified by one thread
+constexpr uint32_t kChunk = 32;          // short pairs per warp step (one per lane)
+constexpr uint32_t kWarpItemCands = 8;   // most candidates per warp work item
+constexpr uint32_t kBlockItemCands = 16; // most candidates per block work item
+constexpr uint32_t kThreadKeyCap = 1024; // largest 2|r| verified one pair per thread
 
 struct VerifyArgs {
     DevColl R, S;
     uint32_t p, q;
+    uint32_t den;                 // p + q
+    uint64_t magic;               // div_magic(p + q), for the required overlap
     uint32_t self_join;
     uint32_t flags;               // VF_*
     uint32_t n_probes;
@@ -66,18 +79,22 @@ struct VerifyArgs {
     uint64_t cap;
     unsigned long long* count;    // result pairs (may exceed cap)
     Counters* ctr;
-    uint32_t* hint;               // probe index of candidate 32*m, per chunk m
-    BlockItem* items;
-    uint32_t item_cap;
-    uint32_t thread_max_key;      // |r|+|s| <= this: one thread per pair
-    uint32_t warp_max_key;        // 2|r| > this: one block per pair
+    uint2* rdesc;                 // per probe: descriptor of its set r (plan output)
+    PairRef* pairs;               // compacted short pairs (plan output)
+    WorkItem* warp_items;
+    WorkItem* block_items;
+    uint32_t warp_item_cap, block_item_cap;
+    uint32_t warp_item_cands, block_item_cands;  // candidates per work item
+    uint32_t thread_max_key;      // 2|r| <= this: one thread per pair
+    uint32_t warp_max_key;        // 2|r| <= this: one warp per pair; above: one block
 };
 
-// Scratch a call needs, in bytes, for n_probes / n_cands.
-size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands);
+// Scratch a call needs, in bytes, for n_probes / n_cands on a device with
+// num_sms SMs.
+size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands, int num_sms);
 
 // Carve the workspace and fill the scratch pointers of a.
-void bind_workspace(VerifyArgs& a, void* ws, uint32_t n_probes, uint64_t n_cands);
+void bind_workspace(VerifyArgs& a, void* ws, uint32_t n_probes, uint64_t n_cands, int num_sms);
 
 // Enqueue the whole verification (counter clear, plan, verify) on st.
 // ev (optional, 3 events): recorded before the plan kernel, between plan and

@@ -9,16 +9,21 @@
 // How the work is laid out (the paper's Alternatives A-C of Section 3.3.2,
 // re-designed for one GB300):
 //   * plan_kernel, one thread per probe: validates the grouped candidate
-//     list, records for every 32-candidate chunk which probe owns its first
-//     candidate, and emits block work items for probes whose sets are long.
-//   * verify_kernel, persistent (one wave of CTAs over the 152 SMs):
+//     list and bins each probe by |r|+|s| (estimated as 2|r|; the length
+//     filter keeps |s| within [t|r|, |r|/t]).  Short probes append their
+//     pairs to a compacted (probe, candidate) list; longer probes become
+//     warp or block work items.  Space is reserved with one atomic per warp.
+//   * verify_kernel, persistent (one wave of CTAs over the SMs):
 //       phase 1 - block items: one CTA per pair, Intersect Path across the
-//                 whole CTA (Alternative C, Section 4.2.2-4.2.3);
-//       phase 2 - a flat pass over the candidate stream in 32-candidate
-//                 chunks: each lane resolves its probe with a shuffle
-//                 search, short pairs are merged one per thread
-//                 (Alternative A/B), medium pairs by the whole warp with a
-//                 32-lane merge path.
+//                 whole CTA (Alternative C, Sections 4.2.2-4.2.3), r kept in
+//                 shared memory for the item's candidates;
+//       phase 2 - warp items: one warp per pair, 32-lane merge path, r kept
+//                 in the warp's shared memory for the item's candidates;
+//       phase 3 - the compacted short pairs, one pair per thread
+//                 (Alternatives A/B), 32 consecutive pairs per warp.
+//     Heavy work goes first so that short pairs fill the tail.  The first
+//     unit of each phase is assigned statically (CTA / warp index), later
+//     ones through one atomic per unit, so small batches need no atomics.
 //   The cooperative merges run in windows of G*D merge steps; the
 //   positional bound is tested between windows, and a pair that is not
 //   rejected runs to the end of the merge so its overlap is exact.
@@ -29,6 +34,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "arith.h"
 #include "ssj_internal.h"
 
 namespace ssj {
@@ -38,20 +44,21 @@ namespace {
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr int kWarpD = 8;                          // merge steps per lane per window (warp)
 constexpr uint32_t kWarpWin = 32 * kWarpD;         // merge steps per window (warp)
-constexpr uint32_t kWarpBuf = kWarpWin + 16;       // tokens staged per side (warp)
+constexpr uint32_t kWarpRCap = 1024;               // r kept whole in a warp's shared memory up to this
+constexpr uint32_t kWarpABuf = kWarpRCap + 16;     // r buffer (whole r, or one window of it)
+constexpr uint32_t kWarpBBuf = kWarpWin + 16;      // s window buffer
 constexpr int kBlockD = 8;                         // merge steps per thread per window (block)
 constexpr uint32_t kBlockRCap = 4096;              // r kept whole in shared memory up to this
+constexpr uint32_t kFlatGrab = 4;                  // 32-pair chunks taken per atomic in phase 3
 
 __device__ __forceinline__ uint32_t sel4(const uint4& v, uint32_t k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
-// ceil(p*(nr+ns)/(p+q)): Jaccard's equivalent overlap with t = p/q.
-// nr, ns < 2^31 and p, q < 2^31 keep every product below 2^63.
-__device__ __forceinline__ uint32_t required_overlap(uint32_t nr, uint32_t ns, uint32_t p, uint32_t q) {
-    const uint64_t num = (uint64_t)p * (uint64_t)(nr + ns);
-    const uint64_t den = (uint64_t)p + (uint64_t)q;
-    return (uint32_t)((num + den - 1) / den);
+// ceil(p*(nr+ns)/(p+q)): Jaccard's equivalent overlap with t = p/q, by the
+// batch's precomputed reciprocal of p+q (exact; see arith.h).
+__device__ __forceinline__ uint32_t required_overlap(const VerifyArgs& a, uint32_t nr, uint32_t ns) {
+    return required_overlap_magic(nr, ns, a.p, a.den, a.magic);
 }
 
 __device__ __forceinline__ void emit_triple(const VerifyArgs& a, unsigned long long idx, uint32_t r, uint32_t s,
@@ -68,32 +75,41 @@ __device__ __forceinline__ void emit_triple(const VerifyArgs& a, unsigned long l
 
 // -------------------------------------------------------------------------
 // Sequential merge of one pair by one thread (Alternatives A/B).  Both sets
-// are read from global memory 16 bytes at a time (sets start 16-byte
-// aligned; the padding keeps the last 16-byte read inside the array).
-// Returns the overlap; *rejected is set when the positional bound fired.
+// are read 16 bytes at a time (sets start 16-byte aligned and are padded to
+// a multiple of 16 bytes); the next 16 bytes of each side are prefetched
+// one step ahead.  Returns the overlap; *rejected is set when the positional
+// bound fired.
 // -------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t thread_merge(const uint4* __restrict__ r4, uint32_t nr,
                                                  const uint4* __restrict__ s4, uint32_t ns, uint32_t req,
                                                  bool early, bool* rejected) {
-    uint32_t i = 0, j = 0, o = 0;
     *rejected = false;
     if (nr == 0 || ns == 0) return 0;
-    uint4 rv = __ldg(r4), sv = __ldg(s4);
+    const uint32_t rq = (nr + 3) >> 2, sq = (ns + 3) >> 2;
+    uint4 r0 = __ldg(r4), s0 = __ldg(s4);
+    uint4 r1 = rq > 1 ? __ldg(r4 + 1) : r0;
+    uint4 s1 = sq > 1 ? __ldg(s4 + 1) : s0;
+    uint32_t i = 0, j = 0, o = 0;
     while (i < nr && j < ns) {
-        if (early) {
-            const uint32_t left = min(nr - i, ns - j);
-            if (o + left < req) { *rejected = true; break; }
-        }
-        const uint32_t x = sel4(rv, i & 3u), y = sel4(sv, j & 3u);
+        if (early && o + min(nr - i, ns - j) < req) { *rejected = true; break; }
+        const uint32_t x = sel4(r0, i & 3u), y = sel4(s0, j & 3u);
         const bool ta = x <= y, tb = x >= y;
         o += (ta && tb) ? 1u : 0u;
         if (ta) {
             ++i;
-            if ((i & 3u) == 0 && i < nr) rv = __ldg(r4 + (i >> 2));
+            if ((i & 3u) == 0) {
+                r0 = r1;
+                const uint32_t nq = (i >> 2) + 1;
+                if (nq < rq) r1 = __ldg(r4 + nq);
+            }
         }
         if (tb) {
             ++j;
-            if ((j & 3u) == 0 && j < ns) sv = __ldg(s4 + (j >> 2));
+            if ((j & 3u) == 0) {
+                s0 = s1;
+                const uint32_t nq = (j >> 2) + 1;
+                if (nq < sq) s1 = __ldg(s4 + nq);
+            }
         }
     }
     return o;
@@ -149,10 +165,12 @@ __device__ __forceinline__ void lane_merge(const uint32_t* A, uint32_t rw, const
 
 // -------------------------------------------------------------------------
 // Warp-cooperative merge of one pair (all 32 lanes, uniform arguments).
-// abuf, bbuf: this warp's staging buffers (kWarpBuf tokens each).
+// If r_staged, abuf holds all of r (abuf[k] = r[k]); otherwise abuf is a
+// window buffer.  bbuf is the s window buffer.
 // -------------------------------------------------------------------------
 __device__ uint32_t warp_merge(const uint4* __restrict__ r4, uint32_t nr, const uint4* __restrict__ s4, uint32_t ns,
-                               uint32_t req, bool early, uint32_t* abuf, uint32_t* bbuf, int lane, bool* rejected) {
+                               uint32_t req, bool early, bool r_staged, uint32_t* abuf, uint32_t* bbuf, int lane,
+                               bool* rejected) {
     uint32_t i0 = 0, j0 = 0, o = 0;
     *rejected = false;
     for (;;) {
@@ -162,10 +180,15 @@ __device__ uint32_t warp_merge(const uint4* __restrict__ r4, uint32_t nr, const 
         const uint32_t rem = (nr - i0) + (ns - j0);
         const uint32_t Wc = min(kWarpWin, rem);
         const uint32_t rw = min(nr - i0, Wc), sw = min(ns - j0, Wc);
-        stage<32>(r4, i0, rw, abuf, lane);
+        const uint32_t* A;
+        if (r_staged) {
+            A = abuf + i0;
+        } else {
+            stage<32>(r4, i0, rw, abuf, lane);
+            A = abuf + (i0 & 3u);
+        }
         stage<32>(s4, j0, sw, bbuf, lane);
         __syncwarp();
-        const uint32_t* A = abuf + (i0 & 3u);
         const uint32_t* B = bbuf + (j0 & 3u);
         const uint32_t d = min((uint32_t)lane * kWarpD, Wc), de = min(d + kWarpD, Wc);
         uint32_t c = 0, ie = 0, je = 0;
@@ -237,41 +260,120 @@ __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const
     return o;
 }
 
+// Warp-local survivor buffer for pairs decided by the whole warp: lane k
+// holds the k-th buffered triple; flushed with one atomic per 32.
+struct WarpOut {
+    uint32_t r = 0, s = 0, o = 0, n = 0;
+
+    __device__ void push(const VerifyArgs& a, int lane, uint32_t pr, uint32_t ps, uint32_t po) {
+        if (lane == (int)n) { r = pr; s = ps; o = po; }
+        if (++n == 32) flush(a, lane);
+    }
+    __device__ void flush(const VerifyArgs& a, int lane) {
+        if (n == 0) return;
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)n);
+        b0 = __shfl_sync(kFull, b0, 0);
+        if ((uint32_t)lane < n) emit_triple(a, b0 + lane, r, s, o);
+        n = 0;
+    }
+};
+
+__device__ __forceinline__ uint32_t probe_bin(const VerifyArgs& a, uint32_t nr) {
+    if (a.flags & VF_FORCE_BLOCK) return 2;
+    if (a.flags & VF_FORCE_WARP) return 1;
+    if (a.flags & VF_FORCE_THREAD) return 0;
+    const uint64_t key = 2ull * nr;  // |r|+|s| at |s| = |r|
+    return key <= a.thread_max_key ? 0u : (key <= a.warp_max_key ? 1u : 2u);
+}
+
+// Reserve `want` slots of a shared counter for every lane of the warp with
+// one atomic (all 32 lanes call this); returns this lane's first slot.
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* counter, unsigned long long want,
+                                                           int lane) {
+    unsigned long long incl = want;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const unsigned long long total = __shfl_sync(kFull, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, total);
+    base = __shfl_sync(kFull, base, 31);
+    return base + incl - want;
+}
+
 }  // namespace
 
 // -------------------------------------------------------------------------
-// Plan: one thread per probe.
+// Plan: one thread per probe; every warp iterates in lockstep so the
+// warp-level reservations see all 32 lanes.
 // -------------------------------------------------------------------------
 __global__ void plan_kernel(VerifyArgs a) {
+    const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_probes; k += stride) {
-        const uint64_t c0 = a.cand_offsets[k], c1 = a.cand_offsets[k + 1];
-        if ((k == 0 && c0 != 0) || (k + 1 == a.n_probes && c1 != a.n_cands) || c1 < c0 || c1 > a.n_cands) {
-            atomicOr(&a.ctr->err, ERR_OFFSETS);
-            continue;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < a.n_probes; base += stride) {
+        const uint32_t k = base + threadIdx.x;
+        uint64_t c0 = 0, n = 0;
+        uint32_t r = 0, bin = 0;
+        if (k < a.n_probes) {
+            c0 = a.cand_offsets[k];
+            const uint64_t c1 = a.cand_offsets[k + 1];
+            if ((k == 0 && c0 != 0) || (k + 1 == a.n_probes && c1 != a.n_cands) || c1 < c0 || c1 > a.n_cands) {
+                atomicOr(&a.ctr->err, ERR_OFFSETS);
+            } else {
+                r = a.probe_ids[k];
+                if (r >= a.R.n_sets) {
+                    if (c1 > c0) atomicOr(&a.ctr->err, ERR_PROBE_ID);
+                } else {
+                    const uint2 dr = a.R.desc[r];
+                    a.rdesc[k] = dr;
+                    n = c1 - c0;
+                    bin = probe_bin(a, dr.y);
+                }
+            }
         }
-        if (c1 == c0) continue;
-        // chunks whose first candidate belongs to this probe
-        for (uint64_t m = (c0 + kChunk - 1) / kChunk; m * kChunk < c1; ++m) a.hint[m] = k;
-        const uint32_t r = a.probe_ids[k];
-        if (r >= a.R.n_sets) continue;  // reported by the verify pass
-        const uint32_t nr = a.R.desc[r].y;
-        bool block;
-        if (a.flags & VF_FORCE_BLOCK) block = true;
-        else if (a.flags & (VF_FORCE_THREAD | VF_FORCE_WARP)) block = false;
-        else block = 2ull * nr > (uint64_t)a.warp_max_key;
-        if (!block) continue;
-        const uint64_t n = c1 - c0;
-        const uint32_t items = (uint32_t)((n + kBlockItemCands - 1) / kBlockItemCands);
-        const uint32_t base = atomicAdd(&a.ctr->block_items, items);
-        for (uint32_t it = 0; it < items; ++it) {
-            if (base + it >= a.item_cap) { atomicOr(&a.ctr->err, ERR_OFFSETS); break; }
-            const uint64_t s0 = c0 + (uint64_t)it * kBlockItemCands;
-            BlockItem bi;
+        // short probes: append (probe, candidate) pairs to the compacted list;
+        // the warp copies each lane's candidates together (coalesced)
+        const unsigned long long tn = (bin == 0) ? n : 0;
+        const unsigned long long tbase = warp_reserve(&a.ctr->thread_pairs, tn, lane);
+        for (int l = 0; l < 32; ++l) {
+            const unsigned long long nl = __shfl_sync(kFull, tn, l);
+            if (nl == 0) continue;  // warp-uniform
+            const unsigned long long bl = __shfl_sync(kFull, tbase, l);
+            const uint64_t cl = __shfl_sync(kFull, c0, l);
+            const uint32_t kl = __shfl_sync(kFull, k, l);
+            for (unsigned long long i = lane; i < nl; i += 32) {
+                PairRef pr;
+                pr.k = kl;
+                pr.s = a.cand_ids[cl + i];
+                a.pairs[bl + i] = pr;
+            }
+        }
+        // longer probes: work items of up to warp_item_cands / block_item_cands candidates
+        const uint32_t wc = a.warp_item_cands, bc = a.block_item_cands;
+        const unsigned long long wn = (bin == 1) ? (n + wc - 1) / wc : 0;
+        const unsigned long long wbase = warp_reserve(&a.ctr->warp_items, wn, lane);
+        for (unsigned long long it = 0; it < wn; ++it) {
+            if (wbase + it >= a.warp_item_cap) { atomicOr(&a.ctr->err, ERR_OFFSETS); break; }
+            const uint64_t s0 = c0 + it * wc;
+            WorkItem wi;
+            wi.r = r;
+            wi.n = (uint32_t)min((uint64_t)wc, c0 + n - s0);
+            wi.c0 = s0;
+            a.warp_items[wbase + it] = wi;
+        }
+        const unsigned long long bn = (bin == 2) ? (n + bc - 1) / bc : 0;
+        const unsigned long long bbase = warp_reserve(&a.ctr->block_items, bn, lane);
+        for (unsigned long long it = 0; it < bn; ++it) {
+            if (bbase + it >= a.block_item_cap) { atomicOr(&a.ctr->err, ERR_OFFSETS); break; }
+            const uint64_t s0 = c0 + it * bc;
+            WorkItem bi;
             bi.r = r;
-            bi.n = (uint32_t)min((uint64_t)kBlockItemCands, c1 - s0);
+            bi.n = (uint32_t)min((uint64_t)bc, c0 + n - s0);
             bi.c0 = s0;
-            a.items[base + it] = bi;
+            a.block_items[bbase + it] = bi;
         }
     }
 }
@@ -284,30 +386,34 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ BlockSmem<BT> bsm;
     constexpr uint32_t kBlockWin = BT * kBlockD;
+    constexpr int kWarps = BT / 32;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
+    const uint32_t n_warps_total = gridDim.x * kWarps;
+    const uint32_t gwarp = blockIdx.x * kWarps + warp;
     const bool count_only = (a.flags & VF_COUNT_ONLY) != 0;
     const bool emit_all = (a.flags & VF_EMIT_ALL) != 0;
     const bool early = !emit_all;
-    unsigned long long local_count = 0;  // count-only mode
+    unsigned long long local_count = 0;  // count-only mode (per lane)
 
-    if (a.ctr->err & ERR_OFFSETS) return;  // hints are not trustworthy
+    if (a.ctr->err & ERR_OFFSETS) return;  // the plan is not trustworthy
 
     // ---------------- phase 1: block-per-pair items ----------------------
-    {
+    const unsigned long long n_block = min(a.ctr->block_items, (unsigned long long)a.block_item_cap);
+    if (n_block) {
         uint32_t* rbuf = smem;                                // kBlockRCap + 16
         uint32_t* wr = smem + kBlockRCap + 16;                // kBlockWin + 16
         uint32_t* ws = wr + kBlockWin + 16;                   // kBlockWin + 16
-        const uint32_t n_items = a.ctr->block_items;
-        for (;;) {
-            if (tid == 0) bsm.item = atomicAdd(&a.ctr->block_cursor, 1u);
+        for (uint32_t round = 0;; ++round) {
+            if (tid == 0)
+                bsm.item = round == 0 ? blockIdx.x : gridDim.x + atomicAdd(&a.ctr->block_cursor, 1u);
             __syncthreads();
             const uint32_t it = bsm.item;
             __syncthreads();
-            if (it >= n_items || it >= a.item_cap) break;
-            const BlockItem bi = a.items[it];
+            if (it >= n_block) break;
+            const WorkItem bi = a.block_items[it];
             const uint2 dr = a.R.desc[bi.r];
             const uint32_t nr = dr.y;
             const uint4* r4 = a.R.toks4 + dr.x;
@@ -317,8 +423,7 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
                 __syncthreads();
             }
             for (uint32_t m = 0; m < bi.n; ++m) {
-                const uint64_t c = bi.c0 + m;
-                const uint32_t s = a.cand_ids[c];
+                const uint32_t s = a.cand_ids[bi.c0 + m];
                 if (s >= a.S.n_sets) {
                     if (tid == 0) atomicOr(&a.ctr->err, ERR_CAND_ID);
                     continue;
@@ -326,12 +431,12 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
                 if (a.self_join && s == bi.r) continue;
                 const uint2 ds = a.S.desc[s];
                 const uint32_t ns = ds.y;
-                const uint32_t req = required_overlap(nr, ns, a.p, a.q);
+                const uint32_t req = required_overlap(a, nr, ns);
                 if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
                 bool rej;
                 const uint32_t o = block_merge<BT>(r4, nr, a.S.toks4 + ds.x, ns, req, early, rbuf, r_staged, wr, ws,
                                                    &bsm, &rej);
-                const bool pass = emit_all || (!rej && nr + ns > 0 && o >= req);
+                const bool pass = emit_all || (!rej && o >= req);
                 if (pass && tid == 0) {
                     if (count_only) {
                         ++local_count;
@@ -345,85 +450,83 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
         }
     }
 
-    // ---------------- phase 2: flat chunks of 32 candidates -------------
-    {
-        uint32_t* abuf = smem + warp * (2 * kWarpBuf);
-        uint32_t* bbuf = abuf + kWarpBuf;
-        const uint64_t n_chunks = (a.n_cands + kChunk - 1) / kChunk;
-        // warp-local survivor buffer for cooperative pairs: lane k holds the k-th
-        uint32_t buf_r = 0, buf_s = 0, buf_o = 0, nbuf = 0;
-        const bool force_thread = (a.flags & VF_FORCE_THREAD) != 0;
-        const bool force_warp = (a.flags & VF_FORCE_WARP) != 0;
-        const bool force_block = (a.flags & VF_FORCE_BLOCK) != 0;
-        for (;;) {
-            uint32_t m32 = 0;
-            if (lane == 0) m32 = atomicAdd(&a.ctr->chunk_cursor, 1u);
-            const uint64_t m = __shfl_sync(kFull, m32, 0);
-            if (m >= n_chunks || force_block) break;
-            const uint64_t base = m * kChunk;
-            const uint64_t c = base + lane;
-            const bool valid = c < a.n_cands;
-
-            // resolve the probe of each lane: k = hint + #{offsets <= c}
-            // (every shuffle below is executed by all 32 lanes)
-            uint32_t kk = min(a.hint[m], a.n_probes - 1);
-            uint32_t k = kk;
-            bool resolved = !valid;
-            for (uint32_t guard = 0;; ++guard) {
-                const uint32_t idx = kk + 1 + lane;
-                const uint64_t b = idx <= a.n_probes ? a.cand_offsets[idx] : ~0ull;
-                uint32_t pos = 0;
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const uint64_t bm = __shfl_sync(kFull, b, pos + step - 1);
-                    if (bm <= c) pos += step;
-                }
-                const uint64_t b_last = __shfl_sync(kFull, b, 31);
-                if (pos == 31 && b_last <= c) pos = 32;
-                if (!resolved && pos < 32) { k = kk + pos; resolved = true; }
-                if (__all_sync(kFull, resolved)) break;
-                // offsets are validated by plan_kernel, so the owner is found within
-                // n_probes/32 windows; the guard only turns a broken invariant into an error
-                if (guard > (a.n_probes >> 5) + 1 || kk + 32 >= a.n_probes) {
-                    if (lane == 0) atomicOr(&a.ctr->err, ERR_OFFSETS);
-                    if (!resolved) { k = a.n_probes; resolved = true; }
-                    break;
-                }
-                kk += 32;
+    WarpOut wout;
+    // ---------------- phase 2: warp-per-pair items -----------------------
+    const unsigned long long n_warp = min(a.ctr->warp_items, (unsigned long long)a.warp_item_cap);
+    if (n_warp) {
+        uint32_t* abuf = smem + warp * (kWarpABuf + kWarpBBuf);
+        uint32_t* bbuf = abuf + kWarpABuf;
+        for (uint32_t round = 0;; ++round) {
+            uint32_t it = 0;
+            if (lane == 0) it = round == 0 ? gwarp : n_warps_total + atomicAdd(&a.ctr->warp_cursor, 1u);
+            it = __shfl_sync(kFull, it, 0);
+            if (it >= n_warp) break;
+            const WorkItem wi = a.warp_items[it];
+            const uint2 dr = a.R.desc[wi.r];
+            const uint32_t nr = dr.y;
+            const uint4* r4 = a.R.toks4 + dr.x;
+            const bool r_staged = nr + 4 <= kWarpRCap;
+            if (r_staged) {
+                stage<32>(r4, 0, nr, abuf, lane);
+                __syncwarp();
             }
+            for (uint32_t m = 0; m < wi.n; ++m) {
+                const uint32_t s = a.cand_ids[wi.c0 + m];
+                if (s >= a.S.n_sets) {
+                    if (lane == 0) atomicOr(&a.ctr->err, ERR_CAND_ID);
+                    continue;
+                }
+                if (a.self_join && s == wi.r) continue;
+                const uint2 ds = a.S.desc[s];
+                const uint32_t ns = ds.y;
+                const uint32_t req = required_overlap(a, nr, ns);
+                if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
+                bool rej;
+                const uint32_t o =
+                    warp_merge(r4, nr, a.S.toks4 + ds.x, ns, req, early, r_staged, abuf, bbuf, lane, &rej);
+                const bool pass = emit_all || (!rej && o >= req);
+                if (pass) {
+                    if (count_only) local_count += (lane == 0) ? 1u : 0u;
+                    else wout.push(a, lane, wi.r, s, o);
+                }
+            }
+            __syncwarp();  // abuf reuse
+        }
+    }
 
-            // per-lane pair
+    // ---------------- phase 3: compacted short pairs, one per thread -----
+    const unsigned long long n_pairs = a.ctr->thread_pairs;
+    const unsigned long long n_units = (n_pairs + kChunk * kFlatGrab - 1) / (kChunk * kFlatGrab);
+    for (uint32_t round = 0;; ++round) {
+        uint32_t u = 0;
+        if (lane == 0) u = round == 0 ? gwarp : n_warps_total + atomicAdd(&a.ctr->chunk_cursor, 1u);
+        u = __shfl_sync(kFull, u, 0);
+        if (u >= n_units) break;
+        for (uint32_t sub = 0; sub < kFlatGrab; ++sub) {
+            const unsigned long long first = ((unsigned long long)u * kFlatGrab + sub) * kChunk;
+            if (first >= n_pairs) break;  // warp-uniform
+            const unsigned long long e = first + lane;
             uint32_t r = 0, s = 0, nr = 0, ns = 0, req = 0;
             uint2 dr = make_uint2(0, 0), ds = make_uint2(0, 0);
             bool live = false;
-            if (valid && k < a.n_probes) {
-                r = a.probe_ids[k];
-                s = __ldcs(a.cand_ids + c);
-                if (r >= a.R.n_sets) {
-                    atomicOr(&a.ctr->err, ERR_PROBE_ID);
-                } else if (s >= a.S.n_sets) {
+            if (e < n_pairs) {
+                const PairRef pr = a.pairs[e];
+                s = pr.s;
+                dr = a.rdesc[pr.k];
+                r = a.probe_ids[pr.k];
+                if (s >= a.S.n_sets) {
                     atomicOr(&a.ctr->err, ERR_CAND_ID);
                 } else if (!(a.self_join && r == s)) {
-                    dr = a.R.desc[r];
+                    ds = a.S.desc[s];
                     nr = dr.y;
-                    const bool block_probe =
-                        force_block || (!force_thread && !force_warp && 2ull * nr > (uint64_t)a.warp_max_key);
-                    if (!block_probe) {
-                        ds = a.S.desc[s];
-                        ns = ds.y;
-                        req = required_overlap(nr, ns, a.p, a.q);
-                        live = emit_all || (nr + ns > 0 && req <= min(nr, ns));  // length filter
-                    }
+                    ns = ds.y;
+                    req = required_overlap(a, nr, ns);
+                    live = emit_all || (nr + ns > 0 && req <= min(nr, ns));  // length filter
                 }
             }
-            const bool thread_pair =
-                live && !force_warp && (force_thread || (uint64_t)nr + ns <= (uint64_t)a.thread_max_key);
-            const bool warp_pair = live && !thread_pair;
-
-            // one pair per thread
             bool pass = false;
             uint32_t o = 0;
-            if (thread_pair) {
+            if (live) {
                 bool rej;
                 o = thread_merge(a.R.toks4 + dr.x, nr, a.S.toks4 + ds.x, ns, req, early, &rej);
                 pass = emit_all || (!rej && o >= req);
@@ -439,50 +542,11 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
                     if (pass) emit_triple(a, b0 + __popc(pmask & ((1u << lane) - 1u)), r, s, o);
                 }
             }
-
-            // one pair per warp, for the lanes that hold medium pairs
-            uint32_t wmask = __ballot_sync(kFull, warp_pair);
-            while (wmask) {
-                const int src = __ffs(wmask) - 1;
-                wmask &= wmask - 1;
-                const uint32_t pr = __shfl_sync(kFull, r, src);
-                const uint32_t ps = __shfl_sync(kFull, s, src);
-                const uint32_t pnr = __shfl_sync(kFull, nr, src);
-                const uint32_t pns = __shfl_sync(kFull, ns, src);
-                const uint32_t preq = __shfl_sync(kFull, req, src);
-                const uint32_t rx = __shfl_sync(kFull, dr.x, src);
-                const uint32_t sx = __shfl_sync(kFull, ds.x, src);
-                bool rej;
-                const uint32_t po =
-                    warp_merge(a.R.toks4 + rx, pnr, a.S.toks4 + sx, pns, preq, early, abuf, bbuf, lane, &rej);
-                const bool ppass = emit_all || (!rej && po >= preq);
-                if (ppass) {
-                    if (count_only) {
-                        local_count += (lane == 0) ? 1u : 0u;
-                    } else {
-                        if (lane == (int)nbuf) { buf_r = pr; buf_s = ps; buf_o = po; }
-                        ++nbuf;
-                        if (nbuf == 32) {
-                            unsigned long long b0 = 0;
-                            if (lane == 0) b0 = atomicAdd(a.count, 32ull);
-                            b0 = __shfl_sync(kFull, b0, 0);
-                            emit_triple(a, b0 + lane, buf_r, buf_s, buf_o);
-                            nbuf = 0;
-                        }
-                    }
-                }
-            }
-        }
-        if (nbuf) {
-            unsigned long long b0 = 0;
-            if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)nbuf);
-            b0 = __shfl_sync(kFull, b0, 0);
-            if ((uint32_t)lane < nbuf) emit_triple(a, b0 + lane, buf_r, buf_s, buf_o);
         }
     }
+    wout.flush(a, lane);
 
     if (count_only) {
-        // lanes hold partial counts; one atomic per warp
         unsigned long long v = local_count;
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) v += __shfl_down_sync(kFull, v, off);
@@ -496,33 +560,53 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static uint32_t block_item_cap(uint32_t n_probes, uint64_t n_cands) {
-    const uint64_t cap = (uint64_t)n_probes + (n_cands + kBlockItemCands - 1) / kBlockItemCands;
-    return (uint32_t)(cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : cap);
+static uint64_t item_cap(uint32_t n_probes, uint64_t n_cands, uint32_t per_item) {
+    const uint64_t cap = (uint64_t)n_probes + (n_cands + per_item - 1) / per_item;
+    return cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : cap;
 }
 
-size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands) {
-    const uint64_t n_chunks = (n_cands + kChunk - 1) / kChunk;
-    return align256(sizeof(Counters)) + align256(sizeof(uint32_t) * (n_chunks + 1)) +
-           align256(sizeof(BlockItem) * ((size_t)block_item_cap(n_probes, n_cands) + 1));
+// Candidates per warp / block work item: small batches get one candidate
+// per item so that every warp holds at most one pair of the critical path;
+// large batches get up to kWarpItemCands / kBlockItemCands to bound the
+// number of dynamic-scheduling atomics.  (Estimates: 32 resident warps and
+// 4 resident CTAs per SM.)
+static void item_sizes(uint64_t n_cands, int num_sms, uint32_t* per_warp_item, uint32_t* per_block_item) {
+    const uint64_t warps = 32ull * (uint64_t)num_sms, ctas = 4ull * (uint64_t)num_sms;
+    uint64_t w = n_cands / (64 * warps), b = n_cands / (64 * ctas);
+    *per_warp_item = (uint32_t)(w < 1 ? 1 : (w > kWarpItemCands ? kWarpItemCands : w));
+    *per_block_item = (uint32_t)(b < 1 ? 1 : (b > kBlockItemCands ? kBlockItemCands : b));
 }
 
-void bind_workspace(VerifyArgs& a, void* ws, uint32_t n_probes, uint64_t n_cands) {
+size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands, int num_sms) {
+    uint32_t wc, bc;
+    item_sizes(n_cands, num_sms, &wc, &bc);
+    return align256(sizeof(Counters)) + align256(sizeof(uint2) * ((size_t)n_probes + 1)) +
+           align256(sizeof(PairRef) * ((size_t)n_cands + 1)) +
+           align256(sizeof(WorkItem) * ((size_t)item_cap(n_probes, n_cands, wc) + 1)) +
+           align256(sizeof(WorkItem) * ((size_t)item_cap(n_probes, n_cands, bc) + 1));
+}
+
+void bind_workspace(VerifyArgs& a, void* ws, uint32_t n_probes, uint64_t n_cands, int num_sms) {
     char* p = static_cast<char*>(ws);
-    const uint64_t n_chunks = (n_cands + kChunk - 1) / kChunk;
+    item_sizes(n_cands, num_sms, &a.warp_item_cands, &a.block_item_cands);
     a.ctr = reinterpret_cast<Counters*>(p);
     p += align256(sizeof(Counters));
-    a.hint = reinterpret_cast<uint32_t*>(p);
-    p += align256(sizeof(uint32_t) * (n_chunks + 1));
-    a.items = reinterpret_cast<BlockItem*>(p);
-    a.item_cap = block_item_cap(n_probes, n_cands);
+    a.rdesc = reinterpret_cast<uint2*>(p);
+    p += align256(sizeof(uint2) * ((size_t)n_probes + 1));
+    a.pairs = reinterpret_cast<PairRef*>(p);
+    p += align256(sizeof(PairRef) * ((size_t)n_cands + 1));
+    a.warp_items = reinterpret_cast<WorkItem*>(p);
+    a.warp_item_cap = (uint32_t)item_cap(n_probes, n_cands, a.warp_item_cands);
+    p += align256(sizeof(WorkItem) * ((size_t)a.warp_item_cap + 1));
+    a.block_items = reinterpret_cast<WorkItem*>(p);
+    a.block_item_cap = (uint32_t)item_cap(n_probes, n_cands, a.block_item_cands);
 }
 
 template <int BT>
 static size_t verify_smem_bytes() {
     constexpr uint32_t kBlockWin = BT * kBlockD;
     const size_t block_phase = sizeof(uint32_t) * (kBlockRCap + 16 + 2 * (kBlockWin + 16));
-    const size_t warp_phase = sizeof(uint32_t) * (BT / 32) * 2 * kWarpBuf;
+    const size_t warp_phase = sizeof(uint32_t) * (BT / 32) * (kWarpABuf + kWarpBBuf);
     return block_phase > warp_phase ? block_phase : warp_phase;
 }
 
@@ -579,7 +663,7 @@ cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uin
     {
         const int threads = 256;
         uint64_t blocks = (a.n_probes + threads - 1) / threads;
-        const uint64_t max_blocks = (uint64_t)num_sms * 16;
+        const uint64_t max_blocks = (uint64_t)num_sms * 8;
         if (blocks > max_blocks) blocks = max_blocks;
         plan_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
         e = cudaGetLastError();
