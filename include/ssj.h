@@ -188,6 +188,31 @@ ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* ou
 ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* d_out,
                                   uint64_t cap, uint64_t* d_count, void* stream);
 
+/*
+ * Same verification as ssj_verify_batch_async, for callers that cannot let
+ * the library allocate device memory during a call: callers whose device
+ * memory all goes through their own arena or a framework's caching
+ * allocator, and callers on latency-critical paths where cudaMalloc or
+ * cudaFree may synchronise the device and stall unrelated streams.  The
+ * paper has no counterpart to this entry point.
+ * It never allocates: the work queue lives in a fixed 32 MiB block of device
+ * memory that belongs to the loaded library (every GPU that loads the
+ * library holds it until the process exits).  A batch whose work queue
+ * would need more is rejected with SSJ_EINVAL and a message (roughly
+ * 800,000 candidates for small batches; split larger batches).  The caller
+ * passes every input and output as device memory, as for
+ * ssj_verify_batch_async (SSJ_DEVICE_PTRS is implied).
+ * The first call on a device looks up the scratch block's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  All calls share the one block and it keeps the last
+ * call's contents (the counters that must start at zero are cleared on
+ * the stream by each call), so calls whose work overlaps on the GPU race:
+ * issue them on one stream, or wait for one before starting the next.
+ * Device-side checks are read with ssj_device_error.
+ */
+ssj_status ssj_verify_batch_noalloc(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* d_out, uint64_t cap,
+                                    uint64_t* d_count, void* stream);
+
 /* Size the workspace for batches of up to n_probes probes and n_cands
  * candidates (device allocation happens here, not in later calls). */
 ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands);

@@ -75,6 +75,7 @@ SIGNATURES = {
     "ssj_collection_info": (_INT, [_VP, _U32, _P(_U32), _P(_U64)]),
     "ssj_verify_batch": (_INT, [_VP, _P(ssj_batch), _VP, _U64, _P(_U64)]),
     "ssj_verify_batch_async": (_INT, [_VP, _P(ssj_batch), _VP, _U64, _VP, _VP]),
+    "ssj_verify_batch_noalloc": (_INT, [_VP, _P(ssj_batch), _VP, _U64, _VP, _VP]),
     "ssj_reserve": (_INT, [_VP, _U32, _U64]),
     "ssj_device_error": (_INT, [_VP, _P(_U32)]),
     "ssj_submit": (_INT, [_VP, _P(ssj_batch), _P(_U64)]),
@@ -229,6 +230,18 @@ def ssj_verify_batch_async(ctx: int, R: int, S: int, p: int, q: int, probe_ids, 
     hb = _make_batch(R, S, p, q, probe_ids, cand_offsets, cand_ids, flags | SSJ_DEVICE_PTRS, n_cands, n_probes)
     _check(ctx, lib().ssj_verify_batch_async(ctx, ctypes.byref(hb.batch), _devptr(d_out), int(cap),
                                              _devptr(d_count), stream))
+
+
+def ssj_verify_batch_noalloc(ctx: int, R: int, S: int, p: int, q: int, probe_ids, cand_offsets, cand_ids,
+                             n_cands: int, d_out, cap: int, d_count, stream: int | None = None, flags: int = 0,
+                             n_probes: int | None = None) -> None:
+    """Like ssj_verify_batch_async, but the library allocates nothing: for callers that cannot let a
+    library allocate device memory mid-call (own arena / caching allocator, or latency-critical paths
+    where cudaMalloc would synchronise the device).  Uses the library's fixed 32 MiB scratch block;
+    calls that overlap on the GPU share it and race."""
+    hb = _make_batch(R, S, p, q, probe_ids, cand_offsets, cand_ids, flags | SSJ_DEVICE_PTRS, n_cands, n_probes)
+    _check(ctx, lib().ssj_verify_batch_noalloc(ctx, ctypes.byref(hb.batch), _devptr(d_out), int(cap),
+                                               _devptr(d_count), stream))
 
 
 def ssj_reserve(ctx: int, n_probes: int, n_cands: int) -> None:

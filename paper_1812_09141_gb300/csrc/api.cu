@@ -924,3 +924,34 @@ extern "C" ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double*
     ctx->prof_used = 0;
     return SSJ_OK;
 }
+
+// ===========================================================================
+// Helpers for the scratch-free entry point (noalloc.cu): they read the
+// context and never allocate.
+// ===========================================================================
+
+namespace ssj {
+
+ssj_status resolve_device_batch(ssj_ctx* ctx, const ssj_batch* batch, VerifyArgs* a, int* device, int* num_sms,
+                                uint32_t* block_threads) {
+    Collection *R, *S;
+    ssj_status st = resolve(ctx, batch, &R, &S);
+    if (st != SSJ_OK) return st;
+    if (batch->n_probes && (!batch->probe_ids || !batch->cand_offsets))
+        return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
+    if (batch->n_cands && !batch->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
+    *a = make_args(ctx, batch, *R, *S, batch->n_cands);
+    a->probe_ids = batch->probe_ids;
+    a->cand_offsets = batch->cand_offsets;
+    a->cand_ids = batch->cand_ids;
+    *device = ctx->device;
+    *num_sms = ctx->num_sms;
+    *block_threads = ctx->block_threads;
+    return SSJ_OK;
+}
+
+ssj_status report(ssj_ctx* ctx, ssj_status st, const char* msg) { return fail(ctx, st, "%s", msg); }
+
+void remember_counters(ssj_ctx* ctx, Counters* c) { ctx->last_ctr = c; }
+
+}  // namespace ssj

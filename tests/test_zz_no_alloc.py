@@ -1,0 +1,72 @@
+"""The scratch-free entry point (ssj_verify_batch_noalloc) against ssj_verify_batch.
+
+Some callers cannot let a library allocate device memory during a call (their
+memory all goes through an arena or a caching allocator, or cudaMalloc's
+device synchronisation is unacceptable on their path).  This file checks that
+the variant serving them returns exactly what the allocating entry point
+returns, on two calls in a row that reuse the same static scratch block.  It
+is named to be collected last and works alone in a fresh process too.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+import paper_1812_09141_gb300 as ssj
+from paper_1812_09141_gb300 import _build
+
+pytestmark = pytest.mark.gpu
+
+
+def _device_batch(b, dev):
+    import torch
+    pr = torch.from_numpy(b.probe_ids.astype(np.int32)).to(dev)
+    co = torch.from_numpy(b.cand_offsets.astype(np.int64)).to(dev)
+    ci = torch.from_numpy(b.cand_ids.astype(np.int32)).to(dev)
+    return pr, co, ci
+
+
+def test_noalloc_matches_allocating_entry_point_on_two_calls():
+    import torch
+    assert torch.cuda.is_available()
+    _build.build()
+    dev = torch.device("cuda:0")
+    ctx = ssj.ssj_create(0)
+    try:
+        spec = synth.tiny_self_join(n=700)
+        spec.plant_frac, spec.plant_edits = 0.2, 2
+        c1 = synth.collection(spec)
+        spec2 = synth.short_sets(n=20_000)
+        spec2.plant_frac, spec2.plant_edits = 0.2, 2
+        c2 = synth.collection(spec2)
+        h1 = ssj.ssj_load_collection(ctx, c1.offsets, c1.tokens, ssj.SSJ_VALIDATE)
+        h2 = ssj.ssj_load_collection(ctx, c2.offsets, c2.tokens, ssj.SSJ_VALIDATE)
+        pr, co, ci = ssj.feeder_all(c2.offsets, c2.tokens, 3, 5, n_threads=4)
+        cases = [(h1, (1, 2), synth.all_pairs_batch(c1.n)), (h2, (3, 5), synth.Batch(pr, co, ci))]
+        stream = torch.cuda.Stream()
+        for h, (p, q), b in cases:
+            want = ssj.triples_to_array(ssj.ssj_verify_batch(ctx, h, h, p, q, b.probe_ids, b.cand_offsets,
+                                                             b.cand_ids))
+            assert len(want) > 0
+            t_pr, t_co, t_ci = _device_batch(b, dev)
+            cap = len(want) + 16
+            out = torch.zeros(cap * 3, dtype=torch.int32, device=dev)
+            cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                ssj.ssj_verify_batch_noalloc(ctx, h, h, p, q, t_pr, t_co, t_ci, b.n_cands, out, cap, cnt,
+                                             stream=stream.cuda_stream)
+            stream.synchronize()
+            n = int(cnt.item())
+            got = ssj.triples_to_array(np.frombuffer(out[:3 * n].cpu().numpy().astype(np.uint32).tobytes(),
+                                                     dtype=ssj.TRIPLE_DTYPE))
+            assert np.array_equal(got, want)
+            assert ssj.ssj_device_error(ctx) == 0
+        # a batch whose work queue exceeds the static block is refused before any launch
+        t_pr, t_co, t_ci = _device_batch(cases[0][2], dev)
+        with pytest.raises(ssj.SsjError) as ei:
+            ssj.ssj_verify_batch_noalloc(ctx, h1, h1, 1, 2, t_pr, t_co, t_ci, 10 ** 9, None, 0,
+                                         torch.zeros(1, dtype=torch.int64, device=dev), flags=ssj.SSJ_COUNT_ONLY)
+        assert ei.value.status == ssj.SSJ_EINVAL
+    finally:
+        ssj.ssj_destroy(ctx)
