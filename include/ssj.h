@@ -221,7 +221,8 @@ ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands);
  * synchronous verification (synchronises the context's stream; call it
  * only after that stream has seen the work).  *code = 0 when no check fired;
  * bit 0: probe id out of range, bit 1: candidate id out of range, bit 2:
- * offsets decreasing or past the candidate array. */
+ * offsets decreasing or past the candidate array, bit 3: an internal loop
+ * bound was reached (a library bug, reported instead of hanging). */
 ssj_status ssj_device_error(ssj_ctx* ctx, uint32_t* code);
 
 /* ------------------------------------------------------------------------

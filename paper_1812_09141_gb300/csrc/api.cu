@@ -655,6 +655,7 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
     const uint64_t count = *ctx->h_count;
     const uint32_t derr = *ctx->h_err;
     *n_out = count;
+    if (derr & ERR_GUARD) return fail(ctx, SSJ_EDEVICE, "internal loop bound reached on the device (code %u)", derr);
     if (derr)
         return fail(ctx, SSJ_EINVAL, "batch rejected by the device checks (code %u: %s%s%s)", derr,
                     (derr & ERR_PROBE_ID) ? "probe id out of range " : "",

@@ -19,8 +19,16 @@
 //                 shared memory for the item's candidates;
 //       phase 2 - warp items: one warp per pair, 32-lane merge path, r kept
 //                 in the warp's shared memory for the item's candidates;
-//       phase 3 - the compacted short pairs, one pair per thread
-//                 (Alternatives A/B), 32 consecutive pairs per warp.
+//       phase 3 - short pairs, one pair per thread (Alternatives A/B): a
+//                 warp takes 128 consecutive pairs of the compacted list
+//                 and stages them in a shared-memory table (metadata, and
+//                 the first 32 bytes of both sets copied with cp.async);
+//                 each lane then runs its four pairs as one loop, merging
+//                 16-byte blocks of the two sets per step (16 compares,
+//                 then the block with the smaller last token advances),
+//                 so lanes are not forced to wait for each other between
+//                 pairs and a pair needs about a quarter of the steps of a
+//                 token-by-token merge.
 //     Heavy work goes first so that short pairs fill the tail.  The first
 //     unit of each phase is assigned statically (CTA / warp index), later
 //     ones through one atomic per unit, so small batches need no atomics.
@@ -49,7 +57,32 @@ constexpr uint32_t kWarpABuf = kWarpRCap + 16;     // r buffer (whole r, or one 
 constexpr uint32_t kWarpBBuf = kWarpWin + 16;      // s window buffer
 constexpr int kBlockD = 8;                         // merge steps per thread per window (block)
 constexpr uint32_t kBlockRCap = 4096;              // r kept whole in shared memory up to this
-constexpr uint32_t kFlatGrab = 4;                  // 32-pair chunks taken per atomic in phase 3
+constexpr uint32_t kTable = kPairsPerUnit;         // pairs staged per warp unit in phase 3
+
+// One staged pair of the phase-3 table: metadata and the first two 16-byte
+// chunks of r and of s.
+struct TableEntry {
+    uint4 m0;    // r id, s id, r start chunk, s start chunk
+    uint4 m1;    // |r|, |s|, required overlap, unused
+    uint4 q[4];  // r chunks 0 and 1, s chunks 0 and 1
+};
+constexpr uint32_t kTableBytes = kTable * sizeof(TableEntry);
+
+// Phases 2 and 3 run per warp and the warps of a CTA change phase at
+// different times, so each warp owns one fixed slice of shared memory that
+// both phases use (phase 1 uses the whole CTA's memory and ends with a
+// CTA barrier before any warp moves on).
+constexpr uint32_t kWarpPhase2Bytes = (kWarpABuf + kWarpBBuf) * 4;
+constexpr uint32_t kWarpSliceBytes =
+    ((kWarpPhase2Bytes > kTableBytes ? kWarpPhase2Bytes : kTableBytes) + 15u) & ~15u;
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 __device__ __forceinline__ uint32_t sel4(const uint4& v, uint32_t k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
@@ -317,6 +350,7 @@ __global__ void plan_kernel(VerifyArgs a) {
         const uint32_t k = base + threadIdx.x;
         uint64_t c0 = 0, n = 0;
         uint32_t r = 0, bin = 0;
+        uint2 rdesc = make_uint2(0, 0);
         if (k < a.n_probes) {
             c0 = a.cand_offsets[k];
             const uint64_t c1 = a.cand_offsets[k + 1];
@@ -327,28 +361,56 @@ __global__ void plan_kernel(VerifyArgs a) {
                 if (r >= a.R.n_sets) {
                     if (c1 > c0) atomicOr(&a.ctr->err, ERR_PROBE_ID);
                 } else {
-                    const uint2 dr = a.R.desc[r];
-                    a.rdesc[k] = dr;
+                    rdesc = a.R.desc[r];
+                    a.rdesc[k] = rdesc;
                     n = c1 - c0;
-                    bin = probe_bin(a, dr.y);
+                    bin = probe_bin(a, rdesc.y);
                 }
             }
         }
-        // short probes: append (probe, candidate) pairs to the compacted list;
-        // the warp copies each lane's candidates together (coalesced)
+        // short probes: append (probe, candidate) pairs to the compacted list.
+        // The warp's 32 probes own one contiguous range [wbase0, wbase0 + T) of
+        // the list in lane order, so the warp copies it as one flat, coalesced
+        // range; each slot finds its probe by a search over the lanes' prefix sums.
         const unsigned long long tn = (bin == 0) ? n : 0;
-        const unsigned long long tbase = warp_reserve(&a.ctr->thread_pairs, tn, lane);
-        for (int l = 0; l < 32; ++l) {
-            const unsigned long long nl = __shfl_sync(kFull, tn, l);
-            if (nl == 0) continue;  // warp-uniform
-            const unsigned long long bl = __shfl_sync(kFull, tbase, l);
-            const uint64_t cl = __shfl_sync(kFull, c0, l);
-            const uint32_t kl = __shfl_sync(kFull, k, l);
-            for (unsigned long long i = lane; i < nl; i += 32) {
-                PairRef pr;
-                pr.k = kl;
-                pr.s = a.cand_ids[cl + i];
-                a.pairs[bl + i] = pr;
+        unsigned long long tincl = tn;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, tincl, off);
+            if (lane >= off) tincl += y;
+        }
+        const unsigned long long ttotal = __shfl_sync(kFull, tincl, 31);
+        unsigned long long tbase0 = 0;
+        if (lane == 31 && ttotal) tbase0 = atomicAdd(&a.ctr->thread_pairs, ttotal);
+        tbase0 = __shfl_sync(kFull, tbase0, 31);
+        const unsigned long long texcl = tincl - tn;
+        for (unsigned long long f0 = 0; f0 < ttotal; f0 += 4 * 32) {
+            uint32_t v[4], kk[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned long long f = f0 + u * 32 + lane;
+                // owning lane: the number of lanes whose inclusive prefix is <= f
+                uint32_t pos = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const unsigned long long w = __shfl_sync(kFull, tincl, pos + step - 1);
+                    if (w <= f) pos += step;
+                }
+                pos = min(pos, 31u);
+                const unsigned long long oc0 = __shfl_sync(kFull, c0, pos);
+                const unsigned long long oex = __shfl_sync(kFull, texcl, pos);
+                kk[u] = __shfl_sync(kFull, k, pos);
+                v[u] = (f < ttotal) ? a.cand_ids[oc0 + (f - oex)] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned long long f = f0 + u * 32 + lane;
+                if (f < ttotal) {
+                    PairRef pr;
+                    pr.k = kk[u];
+                    pr.s = v[u];
+                    a.pairs[tbase0 + f] = pr;
+                }
             }
         }
         // longer probes: work items of up to warp_item_cands / block_item_cands candidates
@@ -454,7 +516,7 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
     // ---------------- phase 2: warp-per-pair items -----------------------
     const unsigned long long n_warp = min(a.ctr->warp_items, (unsigned long long)a.warp_item_cap);
     if (n_warp) {
-        uint32_t* abuf = smem + warp * (kWarpABuf + kWarpBBuf);
+        uint32_t* abuf = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem) + warp * kWarpSliceBytes);
         uint32_t* bbuf = abuf + kWarpABuf;
         for (uint32_t round = 0;; ++round) {
             uint32_t it = 0;
@@ -494,54 +556,144 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
         }
     }
 
-    // ---------------- phase 3: compacted short pairs, one per thread -----
-    const unsigned long long n_pairs = a.ctr->thread_pairs;
-    const unsigned long long n_units = (n_pairs + kChunk * kFlatGrab - 1) / (kChunk * kFlatGrab);
-    for (uint32_t round = 0;; ++round) {
-        uint32_t u = 0;
-        if (lane == 0) u = round == 0 ? gwarp : n_warps_total + atomicAdd(&a.ctr->chunk_cursor, 1u);
-        u = __shfl_sync(kFull, u, 0);
-        if (u >= n_units) break;
-        for (uint32_t sub = 0; sub < kFlatGrab; ++sub) {
-            const unsigned long long first = ((unsigned long long)u * kFlatGrab + sub) * kChunk;
-            if (first >= n_pairs) break;  // warp-uniform
-            const unsigned long long e = first + lane;
-            uint32_t r = 0, s = 0, nr = 0, ns = 0, req = 0;
-            uint2 dr = make_uint2(0, 0), ds = make_uint2(0, 0);
-            bool live = false;
-            if (e < n_pairs) {
-                const PairRef pr = a.pairs[e];
-                s = pr.s;
-                dr = a.rdesc[pr.k];
-                r = a.probe_ids[pr.k];
-                if (s >= a.S.n_sets) {
+    // ---------------- phase 3: short pairs, one per thread ----------------
+    {
+        TableEntry* table = reinterpret_cast<TableEntry*>(reinterpret_cast<char*>(smem) + warp * kWarpSliceBytes);
+        const unsigned long long n_pairs = a.ctr->thread_pairs;
+        const unsigned long long n_units = (n_pairs + kTable - 1) / kTable;
+        const unsigned lt_mask = (1u << lane) - 1u;
+        for (uint32_t round = 0;; ++round) {
+            uint32_t u = 0;
+            if (lane == 0) u = round == 0 ? gwarp : n_warps_total + atomicAdd(&a.ctr->chunk_cursor, 1u);
+            u = __shfl_sync(kFull, u, 0);
+            if (u >= n_units) break;
+            const unsigned long long base = (unsigned long long)u * kTable;
+            // ---- stage: pair entries, then set descriptors, then the first chunks
+            constexpr int T = kTable / 32;
+            PairRef pr[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const unsigned long long e = base + t * 32 + lane;
+                if (e < n_pairs) {
+                    pr[t] = a.pairs[e];
+                } else {
+                    pr[t].k = 0;
+                    pr[t].s = 0xFFFFFFFFu;  // marks an empty slot
+                }
+            }
+            uint2 dr[T], ds[T];
+            uint32_t rid[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                dr[t] = make_uint2(0, 0);
+                ds[t] = make_uint2(0, 0);
+                rid[t] = 0;
+                if (pr[t].s < a.S.n_sets) {
+                    dr[t] = a.rdesc[pr[t].k];
+                    rid[t] = a.probe_ids[pr[t].k];
+                    ds[t] = a.S.desc[pr[t].s];
+                } else if (pr[t].s != 0xFFFFFFFFu) {
                     atomicOr(&a.ctr->err, ERR_CAND_ID);
-                } else if (!(a.self_join && r == s)) {
-                    ds = a.S.desc[s];
-                    nr = dr.y;
-                    ns = ds.y;
+                }
+            }
+            uint32_t n_live = 0;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const uint32_t nr = dr[t].y, ns = ds[t].y;
+                bool live = false;
+                uint32_t req = 0;
+                if (pr[t].s < a.S.n_sets && !(a.self_join && rid[t] == pr[t].s)) {
                     req = required_overlap(a, nr, ns);
                     live = emit_all || (nr + ns > 0 && req <= min(nr, ns));  // length filter
                 }
+                const uint32_t lmask = __ballot_sync(kFull, live);
+                if (live) {
+                    TableEntry* e = table + n_live + __popc(lmask & lt_mask);
+                    e->m0 = make_uint4(rid[t], pr[t].s, dr[t].x, ds[t].x);
+                    e->m1 = make_uint4(nr, ns, req, 0u);
+                    const uint4* r4 = a.R.toks4 + dr[t].x;
+                    const uint4* s4 = a.S.toks4 + ds[t].x;
+                    if (nr > 0) cp_async16(&e->q[0], r4);
+                    if (nr > 4) cp_async16(&e->q[1], r4 + 1);
+                    if (ns > 0) cp_async16(&e->q[2], s4);
+                    if (ns > 4) cp_async16(&e->q[3], s4 + 1);
+                }
+                n_live += __popc(lmask);
             }
-            bool pass = false;
-            uint32_t o = 0;
-            if (live) {
-                bool rej;
-                o = thread_merge(a.R.toks4 + dr.x, nr, a.S.toks4 + ds.x, ns, req, early, &rej);
-                pass = emit_all || (!rej && o >= req);
-            }
-            const uint32_t pmask = __ballot_sync(kFull, pass);
-            if (pmask) {
-                if (count_only) {
-                    local_count += (lane == 0) ? __popc(pmask) : 0;
-                } else {
-                    unsigned long long b0 = 0;
-                    if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)__popc(pmask));
-                    b0 = __shfl_sync(kFull, b0, 0);
-                    if (pass) emit_triple(a, b0 + __popc(pmask & ((1u << lane) - 1u)), r, s, o);
+            cp_async_wait_all();
+            __syncwarp();
+
+            // ---- merge: each lane runs entries lane, lane+32, ... as one loop;
+            // one step compares a 4-token block of r with one of s
+            uint32_t idx = lane;
+            bool have = false, rej = false;
+            uint32_t pr_id = 0, ps_id = 0, rs = 0, ss = 0, nr = 0, ns = 0, req = 0, qi = 0, qj = 0, o = 0;
+            uint4 rc = make_uint4(0, 0, 0, 0), rn = rc, sc = rc, sn = rc;
+            for (;;) {
+                if (!have) {
+                    if (idx >= n_live) break;
+                    const TableEntry* te = table + idx;
+                    const uint4 m0 = te->m0, m1 = te->m1;
+                    pr_id = m0.x; ps_id = m0.y; rs = m0.z; ss = m0.w;
+                    nr = m1.x; ns = m1.y; req = m1.z;
+                    rc = te->q[0]; rn = te->q[1]; sc = te->q[2]; sn = te->q[3];
+                    qi = qj = o = 0;
+                    rej = false;
+                    have = true;
+                    idx += 32;
+                }
+                bool fin = (4 * qi >= nr || 4 * qj >= ns);
+                if (!fin) {
+                    const uint32_t remr = nr - 4 * qi, rems = ns - 4 * qj;
+                    if (early && o + min(remr, rems) < req) {
+                        rej = true;
+                        fin = true;
+                    } else {
+                        const uint32_t nvr = min(remr, 4u), nvs = min(rems, 4u);
+                        const uint32_t ra[4] = {rc.x, rc.y, rc.z, rc.w};
+                        const uint32_t sb[4] = {sc.x, sc.y, sc.z, sc.w};
+                        uint32_t c = 0;
+                        if (nvr == 4 && nvs == 4) {
+#pragma unroll
+                            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                                for (int y = 0; y < 4; ++y) c += (ra[x] == sb[y]) ? 1u : 0u;
+                        } else {
+#pragma unroll
+                            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                                for (int y = 0; y < 4; ++y)
+                                    c += ((uint32_t)x < nvr && (uint32_t)y < nvs && ra[x] == sb[y]) ? 1u : 0u;
+                        }
+                        o += c;
+                        const uint32_t rmax = nvr == 4 ? rc.w : sel4(rc, nvr - 1);
+                        const uint32_t smax = nvs == 4 ? sc.w : sel4(sc, nvs - 1);
+                        if (rmax <= smax) {
+                            ++qi;
+                            rc = rn;
+                            if (qi + 1 < ((nr + 3) >> 2)) rn = __ldg(a.R.toks4 + rs + qi + 1);
+                        }
+                        if (smax <= rmax) {
+                            ++qj;
+                            sc = sn;
+                            if (qj + 1 < ((ns + 3) >> 2)) sn = __ldg(a.S.toks4 + ss + qj + 1);
+                        }
+                        fin = (4 * qi >= nr || 4 * qj >= ns);
+                    }
+                }
+                if (fin) {
+                    if (emit_all || (!rej && o >= req)) {
+                        if (count_only) {
+                            ++local_count;
+                        } else {
+                            const unsigned long long at = atomicAdd(a.count, 1ull);
+                            emit_triple(a, at, pr_id, ps_id, o);
+                        }
+                    }
+                    have = false;
                 }
             }
+            __syncwarp();  // the table is rewritten by the next unit
         }
     }
     wout.flush(a, lane);
@@ -606,8 +758,8 @@ template <int BT>
 static size_t verify_smem_bytes() {
     constexpr uint32_t kBlockWin = BT * kBlockD;
     const size_t block_phase = sizeof(uint32_t) * (kBlockRCap + 16 + 2 * (kBlockWin + 16));
-    const size_t warp_phase = sizeof(uint32_t) * (BT / 32) * (kWarpABuf + kWarpBBuf);
-    return block_phase > warp_phase ? block_phase : warp_phase;
+    const size_t warp_phases = (size_t)(BT / 32) * kWarpSliceBytes;
+    return block_phase > warp_phases ? block_phase : warp_phases;
 }
 
 // CTAs per SM of the persistent kernel, per device (the attribute and the
