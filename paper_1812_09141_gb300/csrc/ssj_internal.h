@@ -59,7 +59,7 @@ enum : uint32_t {
     VF_FORCE_BLOCK = 16u,
 };
 
-constexpr uint32_t kPairsPerUnit = 64;   // short pairs staged per warp unit in phase 3
+
 constexpr uint32_t kWarpItemCands = 8;   // most candidates per warp work item
 constexpr uint32_t kBlockItemCands = 16; // most candidates per block work item
 constexpr uint32_t kThreadKeyCap = 1024; // largest 2|r| verified one pair per thread

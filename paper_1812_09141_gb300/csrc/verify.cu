@@ -19,16 +19,16 @@
 //                 shared memory for the item's candidates;
 //       phase 2 - warp items: one warp per pair, 32-lane merge path, r kept
 //                 in the warp's shared memory for the item's candidates;
-//       phase 3 - short pairs, one pair per thread (Alternatives A/B): a
-//                 warp takes 128 consecutive pairs of the compacted list
-//                 and stages them in a shared-memory table (metadata, and
-//                 the first 32 bytes of both sets copied with cp.async);
-//                 each lane then runs its four pairs as one loop, merging
-//                 16-byte blocks of the two sets per step (16 compares,
-//                 then the block with the smaller last token advances),
-//                 so lanes are not forced to wait for each other between
-//                 pairs and a pair needs about a quarter of the steps of a
-//                 token-by-token merge.
+//       phase 3 - short pairs, one pair per thread (Alternatives A/B), 32
+//                 consecutive pairs of the compacted list per warp step.
+//                 The merge compares 16-byte blocks (4 tokens of r against
+//                 4 of s, 16 compares; the block with the smaller last token
+//                 advances).  Pass 1: every lane loads the first three blocks
+//                 of both sets and runs exactly three block steps, unrolled
+//                 and predicated, which decides most pairs (the positional
+//                 bound rejects them early).  Pass 2: undecided pairs are
+//                 parked with their merge state in a per-warp shared buffer
+//                 and finished 32 at a time by a loop.
 //     Heavy work goes first so that short pairs fill the tail.  The first
 //     unit of each phase is assigned statically (CTA / warp index), later
 //     ones through one atomic per unit, so small batches need no atomics.
@@ -57,16 +57,16 @@ constexpr uint32_t kWarpABuf = kWarpRCap + 16;     // r buffer (whole r, or one 
 constexpr uint32_t kWarpBBuf = kWarpWin + 16;      // s window buffer
 constexpr int kBlockD = 8;                         // merge steps per thread per window (block)
 constexpr uint32_t kBlockRCap = 4096;              // r kept whole in shared memory up to this
-constexpr uint32_t kTable = kPairsPerUnit;         // pairs staged per warp unit in phase 3
+constexpr uint32_t kFlatGrab = 4;                  // 32-pair chunks taken per dynamic grab in phase 3
+constexpr uint32_t kCont = 64;                     // parked pairs per warp in phase 3
 
-// One staged pair of the phase-3 table: metadata and the first two 16-byte
-// chunks of r and of s.
-struct TableEntry {
-    uint4 m0;    // r id, s id, r start chunk, s start chunk
-    uint4 m1;    // |r|, |s|, required overlap, unused
-    uint4 q[4];  // r chunks 0 and 1, s chunks 0 and 1
+// A pair parked after pass 1 with its merge state.
+struct ContEntry {
+    uint4 m0;  // r id, s id, r start chunk, s start chunk
+    uint4 m1;  // |r|, |s|, required overlap, overlap so far
+    uint4 m2;  // r block index, s block index, unused, unused
 };
-constexpr uint32_t kTableBytes = kTable * sizeof(TableEntry);
+constexpr uint32_t kTableBytes = kCont * sizeof(ContEntry);
 
 // Phases 2 and 3 run per warp and the warps of a CTA change phase at
 // different times, so each warp owns one fixed slice of shared memory that
@@ -76,16 +76,57 @@ constexpr uint32_t kWarpPhase2Bytes = (kWarpABuf + kWarpBBuf) * 4;
 constexpr uint32_t kWarpSliceBytes =
     ((kWarpPhase2Bytes > kTableBytes ? kWarpPhase2Bytes : kTableBytes) + 15u) & ~15u;
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
 __device__ __forceinline__ uint32_t sel4(const uint4& v, uint32_t k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// Merge state of one pair compared block by block.
+struct BlockState {
+    uint32_t qi, qj, o;  // current block of r and of s, overlap so far
+    bool fin, rej;
+};
+
+// One block step: count the matches between block qi of r (rc) and block qj
+// of s (sc), then advance the block whose last valid token is smaller (both
+// on a tie).  Every matching pair of tokens sits in a pair of blocks that is
+// current together exactly once, so the count is exact.  Before the step the
+// positional bound o + min(|r| - 4qi, |s| - 4qj) < req rejects the pair; the
+// bound counts whole current blocks, so it only over-estimates the reachable
+// overlap and never rejects a passing pair.  Tokens past a set's end (the
+// padding of its last block) are masked by position.
+__device__ __forceinline__ void block_step(const uint4& rc, const uint4& sc, uint32_t nr, uint32_t ns, uint32_t req,
+                                           bool early, BlockState& st, bool& adv_r, bool& adv_s) {
+    adv_r = adv_s = false;
+    if (st.fin) return;
+    const uint32_t remr = nr - 4 * st.qi, rems = ns - 4 * st.qj;
+    if (early && st.o + min(remr, rems) < req) {
+        st.rej = true;
+        st.fin = true;
+        return;
+    }
+    const uint32_t nvr = min(remr, 4u), nvs = min(rems, 4u);
+    const uint32_t ra[4] = {rc.x, rc.y, rc.z, rc.w};
+    const uint32_t sb[4] = {sc.x, sc.y, sc.z, sc.w};
+    uint32_t c = 0;
+    if (nvr == 4 && nvs == 4) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) c += (ra[x] == sb[y]) ? 1u : 0u;
+    } else {
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) c += ((uint32_t)x < nvr && (uint32_t)y < nvs && ra[x] == sb[y]) ? 1u : 0u;
+    }
+    st.o += c;
+    const uint32_t rmax = nvr == 4 ? rc.w : sel4(rc, nvr - 1);
+    const uint32_t smax = nvs == 4 ? sc.w : sel4(sc, nvs - 1);
+    adv_r = rmax <= smax;
+    adv_s = smax <= rmax;
+    st.qi += adv_r ? 1u : 0u;
+    st.qj += adv_s ? 1u : 0u;
+    st.fin = (4 * st.qi >= nr || 4 * st.qj >= ns);
 }
 
 // ceil(p*(nr+ns)/(p+q)): Jaccard's equivalent overlap with t = p/q, by the
@@ -558,143 +599,147 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
 
     // ---------------- phase 3: short pairs, one per thread ----------------
     {
-        TableEntry* table = reinterpret_cast<TableEntry*>(reinterpret_cast<char*>(smem) + warp * kWarpSliceBytes);
+        ContEntry* cont = reinterpret_cast<ContEntry*>(reinterpret_cast<char*>(smem) + warp * kWarpSliceBytes);
+        uint32_t n_cont = 0;  // warp-uniform
         const unsigned long long n_pairs = a.ctr->thread_pairs;
-        const unsigned long long n_units = (n_pairs + kTable - 1) / kTable;
+        const unsigned long long n_units = (n_pairs + 32 * kFlatGrab - 1) / (32 * kFlatGrab);
         const unsigned lt_mask = (1u << lane) - 1u;
+        const uint4 zero4 = make_uint4(0, 0, 0, 0);
+
+        // Pass 2: finish the parked pairs [n_cont - m, n_cont), one per lane.
+        auto drain = [&](uint32_t m) {
+            bool have = false;
+            uint32_t pr_id = 0, ps_id = 0, rs = 0, ss = 0, nr = 0, ns = 0, req = 0;
+            BlockState st;
+            st.qi = st.qj = st.o = 0;
+            st.fin = true;
+            st.rej = false;
+            uint4 rc = zero4, rn = zero4, sc = zero4, sn = zero4;
+            if ((uint32_t)lane < m) {
+                const ContEntry* ce = cont + (n_cont - m) + lane;
+                const uint4 m0 = ce->m0, m1 = ce->m1, m2 = ce->m2;
+                pr_id = m0.x; ps_id = m0.y; rs = m0.z; ss = m0.w;
+                nr = m1.x; ns = m1.y; req = m1.z;
+                st.o = m1.w; st.qi = m2.x; st.qj = m2.y;
+                st.fin = false;
+                have = true;
+                const uint32_t rq = (nr + 3) >> 2, sq = (ns + 3) >> 2;
+                rc = __ldg(a.R.toks4 + rs + st.qi);
+                if (st.qi + 1 < rq) rn = __ldg(a.R.toks4 + rs + st.qi + 1);
+                sc = __ldg(a.S.toks4 + ss + st.qj);
+                if (st.qj + 1 < sq) sn = __ldg(a.S.toks4 + ss + st.qj + 1);
+            }
+            while (!st.fin) {
+                bool ar, as;
+                block_step(rc, sc, nr, ns, req, early, st, ar, as);
+                if (ar) {
+                    rc = rn;
+                    if (st.qi + 1 < ((nr + 3) >> 2)) rn = __ldg(a.R.toks4 + rs + st.qi + 1);
+                }
+                if (as) {
+                    sc = sn;
+                    if (st.qj + 1 < ((ns + 3) >> 2)) sn = __ldg(a.S.toks4 + ss + st.qj + 1);
+                }
+            }
+            const bool pass = have && (emit_all || (!st.rej && st.o >= req));
+            const uint32_t pmask = __ballot_sync(kFull, pass);
+            if (pmask) {
+                if (count_only) {
+                    local_count += (lane == 0) ? __popc(pmask) : 0;
+                } else {
+                    unsigned long long b0 = 0;
+                    if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)__popc(pmask));
+                    b0 = __shfl_sync(kFull, b0, 0);
+                    if (pass) emit_triple(a, b0 + __popc(pmask & lt_mask), pr_id, ps_id, st.o);
+                }
+            }
+            n_cont -= m;
+            __syncwarp();  // the parked entries may be overwritten from here on
+        };
+
         for (uint32_t round = 0;; ++round) {
             uint32_t u = 0;
             if (lane == 0) u = round == 0 ? gwarp : n_warps_total + atomicAdd(&a.ctr->chunk_cursor, 1u);
             u = __shfl_sync(kFull, u, 0);
             if (u >= n_units) break;
-            const unsigned long long base = (unsigned long long)u * kTable;
-            // ---- stage: pair entries, then set descriptors, then the first chunks
-            constexpr int T = kTable / 32;
-            PairRef pr[T];
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                const unsigned long long e = base + t * 32 + lane;
-                if (e < n_pairs) {
-                    pr[t] = a.pairs[e];
-                } else {
-                    pr[t].k = 0;
-                    pr[t].s = 0xFFFFFFFFu;  // marks an empty slot
-                }
-            }
-            uint2 dr[T], ds[T];
-            uint32_t rid[T];
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                dr[t] = make_uint2(0, 0);
-                ds[t] = make_uint2(0, 0);
-                rid[t] = 0;
-                if (pr[t].s < a.S.n_sets) {
-                    dr[t] = a.rdesc[pr[t].k];
-                    rid[t] = a.probe_ids[pr[t].k];
-                    ds[t] = a.S.desc[pr[t].s];
-                } else if (pr[t].s != 0xFFFFFFFFu) {
-                    atomicOr(&a.ctr->err, ERR_CAND_ID);
-                }
-            }
-            uint32_t n_live = 0;
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                const uint32_t nr = dr[t].y, ns = ds[t].y;
+            for (uint32_t sub = 0; sub < kFlatGrab; ++sub) {
+                const unsigned long long first = ((unsigned long long)u * kFlatGrab + sub) * 32;
+                if (first >= n_pairs) break;  // warp-uniform
+                const unsigned long long e = first + lane;
+                // ---- pass 1
                 bool live = false;
-                uint32_t req = 0;
-                if (pr[t].s < a.S.n_sets && !(a.self_join && rid[t] == pr[t].s)) {
-                    req = required_overlap(a, nr, ns);
-                    live = emit_all || (nr + ns > 0 && req <= min(nr, ns));  // length filter
-                }
-                const uint32_t lmask = __ballot_sync(kFull, live);
-                if (live) {
-                    TableEntry* e = table + n_live + __popc(lmask & lt_mask);
-                    e->m0 = make_uint4(rid[t], pr[t].s, dr[t].x, ds[t].x);
-                    e->m1 = make_uint4(nr, ns, req, 0u);
-                    const uint4* r4 = a.R.toks4 + dr[t].x;
-                    const uint4* s4 = a.S.toks4 + ds[t].x;
-                    if (nr > 0) cp_async16(&e->q[0], r4);
-                    if (nr > 4) cp_async16(&e->q[1], r4 + 1);
-                    if (ns > 0) cp_async16(&e->q[2], s4);
-                    if (ns > 4) cp_async16(&e->q[3], s4 + 1);
-                }
-                n_live += __popc(lmask);
-            }
-            cp_async_wait_all();
-            __syncwarp();
-
-            // ---- merge: each lane runs entries lane, lane+32, ... as one loop;
-            // one step compares a 4-token block of r with one of s
-            uint32_t idx = lane;
-            bool have = false, rej = false;
-            uint32_t pr_id = 0, ps_id = 0, rs = 0, ss = 0, nr = 0, ns = 0, req = 0, qi = 0, qj = 0, o = 0;
-            uint4 rc = make_uint4(0, 0, 0, 0), rn = rc, sc = rc, sn = rc;
-            for (;;) {
-                if (!have) {
-                    if (idx >= n_live) break;
-                    const TableEntry* te = table + idx;
-                    const uint4 m0 = te->m0, m1 = te->m1;
-                    pr_id = m0.x; ps_id = m0.y; rs = m0.z; ss = m0.w;
-                    nr = m1.x; ns = m1.y; req = m1.z;
-                    rc = te->q[0]; rn = te->q[1]; sc = te->q[2]; sn = te->q[3];
-                    qi = qj = o = 0;
-                    rej = false;
-                    have = true;
-                    idx += 32;
-                }
-                bool fin = (4 * qi >= nr || 4 * qj >= ns);
-                if (!fin) {
-                    const uint32_t remr = nr - 4 * qi, rems = ns - 4 * qj;
-                    if (early && o + min(remr, rems) < req) {
-                        rej = true;
-                        fin = true;
+                uint32_t pr_id = 0, ps_id = 0, nr = 0, ns = 0, req = 0;
+                uint2 dr = make_uint2(0, 0), ds = make_uint2(0, 0);
+                if (e < n_pairs) {
+                    const PairRef pr = a.pairs[e];
+                    ps_id = pr.s;
+                    if (ps_id >= a.S.n_sets) {
+                        atomicOr(&a.ctr->err, ERR_CAND_ID);
                     } else {
-                        const uint32_t nvr = min(remr, 4u), nvs = min(rems, 4u);
-                        const uint32_t ra[4] = {rc.x, rc.y, rc.z, rc.w};
-                        const uint32_t sb[4] = {sc.x, sc.y, sc.z, sc.w};
-                        uint32_t c = 0;
-                        if (nvr == 4 && nvs == 4) {
-#pragma unroll
-                            for (int x = 0; x < 4; ++x)
-#pragma unroll
-                                for (int y = 0; y < 4; ++y) c += (ra[x] == sb[y]) ? 1u : 0u;
-                        } else {
-#pragma unroll
-                            for (int x = 0; x < 4; ++x)
-#pragma unroll
-                                for (int y = 0; y < 4; ++y)
-                                    c += ((uint32_t)x < nvr && (uint32_t)y < nvs && ra[x] == sb[y]) ? 1u : 0u;
+                        dr = a.rdesc[pr.k];
+                        pr_id = a.probe_ids[pr.k];
+                        ds = a.S.desc[ps_id];
+                        nr = dr.y;
+                        ns = ds.y;
+                        if (!(a.self_join && pr_id == ps_id)) {
+                            req = required_overlap(a, nr, ns);
+                            live = emit_all || (nr + ns > 0 && req <= min(nr, ns));  // length filter
                         }
-                        o += c;
-                        const uint32_t rmax = nvr == 4 ? rc.w : sel4(rc, nvr - 1);
-                        const uint32_t smax = nvs == 4 ? sc.w : sel4(sc, nvs - 1);
-                        if (rmax <= smax) {
-                            ++qi;
-                            rc = rn;
-                            if (qi + 1 < ((nr + 3) >> 2)) rn = __ldg(a.R.toks4 + rs + qi + 1);
-                        }
-                        if (smax <= rmax) {
-                            ++qj;
-                            sc = sn;
-                            if (qj + 1 < ((ns + 3) >> 2)) sn = __ldg(a.S.toks4 + ss + qj + 1);
-                        }
-                        fin = (4 * qi >= nr || 4 * qj >= ns);
                     }
                 }
-                if (fin) {
-                    if (emit_all || (!rej && o >= req)) {
-                        if (count_only) {
-                            ++local_count;
-                        } else {
-                            const unsigned long long at = atomicAdd(a.count, 1ull);
-                            emit_triple(a, at, pr_id, ps_id, o);
-                        }
+                uint4 r0 = zero4, r1 = zero4, r2 = zero4, s0 = zero4, s1 = zero4, s2 = zero4;
+                if (live) {
+                    const uint4* r4 = a.R.toks4 + dr.x;
+                    const uint4* s4 = a.S.toks4 + ds.x;
+                    if (nr > 0) r0 = __ldg(r4);
+                    if (nr > 4) r1 = __ldg(r4 + 1);
+                    if (nr > 8) r2 = __ldg(r4 + 2);
+                    if (ns > 0) s0 = __ldg(s4);
+                    if (ns > 4) s1 = __ldg(s4 + 1);
+                    if (ns > 8) s2 = __ldg(s4 + 2);
+                }
+                BlockState st;
+                st.qi = st.qj = st.o = 0;
+                st.rej = false;
+                st.fin = !live || nr == 0 || ns == 0;
+#pragma unroll
+                for (int step = 0; step < 3; ++step) {
+                    bool ar, as;
+                    block_step(r0, s0, nr, ns, req, early, st, ar, as);
+                    if (ar) { r0 = r1; r1 = r2; }
+                    if (as) { s0 = s1; s1 = s2; }
+                }
+                // decided pairs
+                const bool pass = live && st.fin && (emit_all || (!st.rej && st.o >= req));
+                const uint32_t pmask = __ballot_sync(kFull, pass);
+                if (pmask) {
+                    if (count_only) {
+                        local_count += (lane == 0) ? __popc(pmask) : 0;
+                    } else {
+                        unsigned long long b0 = 0;
+                        if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)__popc(pmask));
+                        b0 = __shfl_sync(kFull, b0, 0);
+                        if (pass) emit_triple(a, b0 + __popc(pmask & lt_mask), pr_id, ps_id, st.o);
                     }
-                    have = false;
+                }
+                // undecided pairs: park them with their merge state
+                const bool park = live && !st.fin;
+                const uint32_t kmask = __ballot_sync(kFull, park);
+                if (kmask) {
+                    if (n_cont + 32 > kCont) drain(32);  // room for a full warp of parked pairs
+                    if (park) {
+                        ContEntry* ce = cont + n_cont + __popc(kmask & lt_mask);
+                        ce->m0 = make_uint4(pr_id, ps_id, dr.x, ds.x);
+                        ce->m1 = make_uint4(nr, ns, req, st.o);
+                        ce->m2 = make_uint4(st.qi, st.qj, 0u, 0u);
+                    }
+                    n_cont += __popc(kmask);
+                    __syncwarp();
+                    if (n_cont >= 32) drain(32);
                 }
             }
-            __syncwarp();  // the table is rewritten by the next unit
         }
+        while (n_cont) drain(min(n_cont, 32u));
     }
     wout.flush(a, lane);
 
