@@ -387,8 +387,13 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
 __global__ void plan_kernel(VerifyArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < a.n_probes; base += stride) {
-        const uint32_t k = base + threadIdx.x;
+    const uint32_t n_warps = stride >> 5;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // Lane l of warp w takes probe base + l * n_warps + w: a warp's 32 probes are
+    // spread over the batch, so warps get similar amounts of copying even when
+    // the batch lists probes in size order.
+    for (uint32_t base = 0; base < a.n_probes; base += stride) {
+        const uint32_t k = base + (uint32_t)lane * n_warps + gw;
         uint64_t c0 = 0, n = 0;
         uint32_t r = 0, bin = 0;
         uint2 rdesc = make_uint2(0, 0);
@@ -503,15 +508,25 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
 
     if (a.ctr->err & ERR_OFFSETS) return;  // the plan is not trustworthy
 
-    // ---------------- phase 1: block-per-pair items ----------------------
+    // Static first-round assignment: phase 1 takes CTAs [0, n_bs); phase 2 starts
+    // on the warps after those, phase 3 on the warps after phase 2's, so a small
+    // batch spreads over idle warps at once.  Later rounds are dynamic.
     const unsigned long long n_block = min(a.ctr->block_items, (unsigned long long)a.block_item_cap);
+    const unsigned long long n_warp = min(a.ctr->warp_items, (unsigned long long)a.warp_item_cap);
+    const uint32_t n_bs = (uint32_t)min(n_block, (unsigned long long)gridDim.x);
+    const uint32_t free2 = n_bs * kWarps;                                   // first warp free for phase 2
+    const uint32_t slots2 = n_warps_total - free2;                          // static phase-2 slots
+    const uint32_t free3 = free2 + (uint32_t)min(n_warp, (unsigned long long)slots2);
+    const uint32_t slots3 = n_warps_total - free3;                          // static phase-3 slots
+
+    // ---------------- phase 1: block-per-pair items ----------------------
     if (n_block) {
         uint32_t* rbuf = smem;                                // kBlockRCap + 16
         uint32_t* wr = smem + kBlockRCap + 16;                // kBlockWin + 16
         uint32_t* ws = wr + kBlockWin + 16;                   // kBlockWin + 16
         for (uint32_t round = 0;; ++round) {
             if (tid == 0)
-                bsm.item = round == 0 ? blockIdx.x : gridDim.x + atomicAdd(&a.ctr->block_cursor, 1u);
+                bsm.item = round == 0 ? blockIdx.x : gridDim.x + atomicAdd(&a.ctr->block_cursor, 1u);  // all CTAs are static slots
             __syncthreads();
             const uint32_t it = bsm.item;
             __syncthreads();
@@ -555,13 +570,15 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
 
     WarpOut wout;
     // ---------------- phase 2: warp-per-pair items -----------------------
-    const unsigned long long n_warp = min(a.ctr->warp_items, (unsigned long long)a.warp_item_cap);
     if (n_warp) {
         uint32_t* abuf = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem) + warp * kWarpSliceBytes);
         uint32_t* bbuf = abuf + kWarpABuf;
         for (uint32_t round = 0;; ++round) {
             uint32_t it = 0;
-            if (lane == 0) it = round == 0 ? gwarp : n_warps_total + atomicAdd(&a.ctr->warp_cursor, 1u);
+            if (lane == 0) {
+                if (round == 0 && gwarp >= free2) it = gwarp - free2;
+                else it = slots2 + atomicAdd(&a.ctr->warp_cursor, 1u);
+            }
             it = __shfl_sync(kFull, it, 0);
             if (it >= n_warp) break;
             const WorkItem wi = a.warp_items[it];
@@ -659,7 +676,10 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
 
         for (uint32_t round = 0;; ++round) {
             uint32_t u = 0;
-            if (lane == 0) u = round == 0 ? gwarp : n_warps_total + atomicAdd(&a.ctr->chunk_cursor, 1u);
+            if (lane == 0) {
+                if (round == 0 && gwarp >= free3) u = gwarp - free3;
+                else u = slots3 + atomicAdd(&a.ctr->chunk_cursor, 1u);
+            }
             u = __shfl_sync(kFull, u, 0);
             if (u >= n_units) break;
             for (uint32_t sub = 0; sub < kFlatGrab; ++sub) {
