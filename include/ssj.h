@@ -213,6 +213,44 @@ ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batch, ssj_trip
 ssj_status ssj_verify_batch_noalloc(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* d_out, uint64_t cap,
                                     uint64_t* d_count, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched instances: many independent joins in one launch
+ * ------------------------------------------------------------------------ */
+
+typedef struct ssj_multi ssj_multi;  /* opaque, owned by the library */
+
+/*
+ * Prepare one launch that verifies n_batches independent batches (each with
+ * its own collections and threshold) together: one plan kernel and one
+ * persistent verify kernel whose work queue is binned by |r|+|s| across all
+ * instances (the granularity rule of Section 5.4 applied per probe).
+ * All batch arrays are DEVICE pointers (SSJ_DEVICE_PTRS is implied) and each
+ * batch's n_cands is required.  Batch i writes up to caps[i] triples to
+ * d_outs[i] (device) and its result count to d_counts[i] (a device array of
+ * n_batches uint64); d_outs and caps are host arrays read here.
+ * The workspace is allocated and the instance table uploaded here, once; the
+ * arrays' contents may change between launches, their addresses and sizes
+ * may not.  Collections used by a prepared launch cannot be unloaded until
+ * it is destroyed.  Errors: SSJ_EINVAL (a batch is invalid, see
+ * ssj_verify_batch), SSJ_ENOTFOUND, SSJ_ENOMEM, SSJ_EDEVICE.
+ */
+ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, uint32_t n_batches, ssj_triple* const* d_outs,
+                            const uint64_t* caps, uint64_t* d_counts, ssj_multi** out);
+
+/* Enqueue the prepared launch on `stream` (NULL: the context's stream):
+ * a counter clear, the plan kernel and the verify kernel.  Allocates
+ * nothing and reads no host memory.  Launches of one ssj_multi must not
+ * overlap on the GPU (they share its workspace). */
+ssj_status ssj_multi_launch(ssj_ctx* ctx, ssj_multi* m, void* stream);
+
+/* Same work through a CUDA graph: the first call captures the launch into a
+ * graph owned by m (on an internal stream), every call then launches that
+ * graph on `stream`. */
+ssj_status ssj_multi_graph_launch(ssj_ctx* ctx, ssj_multi* m, void* stream);
+
+/* Free a prepared launch (waits for its work). NULL is ignored. */
+void ssj_multi_destroy(ssj_ctx* ctx, ssj_multi* m);
+
 /* Size the workspace for batches of up to n_probes probes and n_cands
  * candidates (device allocation happens here, not in later calls). */
 ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands);

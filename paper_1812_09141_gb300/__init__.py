@@ -77,6 +77,10 @@ SIGNATURES = {
     "ssj_verify_batch_async": (_INT, [_VP, _P(ssj_batch), _VP, _U64, _VP, _VP]),
     "ssj_verify_batch_noalloc": (_INT, [_VP, _P(ssj_batch), _VP, _U64, _VP, _VP]),
     "ssj_reserve": (_INT, [_VP, _U32, _U64]),
+    "ssj_multi_create": (_INT, [_VP, _P(ssj_batch), _U32, _P(_VP), _P(_U64), _VP, _P(_VP)]),
+    "ssj_multi_launch": (_INT, [_VP, _VP, _VP]),
+    "ssj_multi_graph_launch": (_INT, [_VP, _VP, _VP]),
+    "ssj_multi_destroy": (None, [_VP, _VP]),
     "ssj_device_error": (_INT, [_VP, _P(_U32)]),
     "ssj_submit": (_INT, [_VP, _P(ssj_batch), _P(_U64)]),
     "ssj_poll": (_INT, [_VP, _U64, _INT, _P(_INT)]),
@@ -242,6 +246,44 @@ def ssj_verify_batch_noalloc(ctx: int, R: int, S: int, p: int, q: int, probe_ids
     hb = _make_batch(R, S, p, q, probe_ids, cand_offsets, cand_ids, flags | SSJ_DEVICE_PTRS, n_cands, n_probes)
     _check(ctx, lib().ssj_verify_batch_noalloc(ctx, ctypes.byref(hb.batch), _devptr(d_out), int(cap),
                                                _devptr(d_count), stream))
+
+
+class DeviceBatch:
+    """A batch whose arrays live on the device (torch CUDA tensors or raw addresses)."""
+
+    def __init__(self, R: int, S: int, p: int, q: int, probe_ids, cand_offsets, cand_ids, n_cands: int,
+                 flags: int = 0, n_probes: int | None = None):
+        self._hb = _make_batch(R, S, p, q, probe_ids, cand_offsets, cand_ids, flags | SSJ_DEVICE_PTRS, n_cands,
+                               n_probes)
+
+    @property
+    def batch(self) -> ssj_batch:
+        return self._hb.batch
+
+
+def ssj_multi_create(ctx: int, batches: list, outs: list, caps: list, d_counts) -> int:
+    """Prepare one launch over several device batches (DeviceBatch objects).  outs[i]: device
+    tensor (or address) for batch i's triples, caps[i] its capacity, d_counts: device int64
+    tensor of len(batches)."""
+    n = len(batches)
+    arr = (ssj_batch * max(n, 1))(*[b.batch for b in batches])
+    outp = (ctypes.c_void_p * max(n, 1))(*[_devptr(o) for o in outs])
+    capa = (ctypes.c_uint64 * max(n, 1))(*[int(c) for c in caps])
+    m = ctypes.c_void_p()
+    _check(ctx, lib().ssj_multi_create(ctx, arr, n, outp, capa, _devptr(d_counts), ctypes.byref(m)))
+    return m.value
+
+
+def ssj_multi_launch(ctx: int, m: int, stream: int | None = None) -> None:
+    _check(ctx, lib().ssj_multi_launch(ctx, m, stream))
+
+
+def ssj_multi_graph_launch(ctx: int, m: int, stream: int | None = None) -> None:
+    _check(ctx, lib().ssj_multi_graph_launch(ctx, m, stream))
+
+
+def ssj_multi_destroy(ctx: int, m: int) -> None:
+    lib().ssj_multi_destroy(ctx, m)
 
 
 def ssj_reserve(ctx: int, n_probes: int, n_cands: int) -> None:

@@ -258,19 +258,31 @@ uint32_t vflags(uint32_t f) {
     return v;
 }
 
+// The instance of one batch (arrays, output and count are filled by the caller).
+Instance make_instance(const ssj_batch* b, const Collection& R, const Collection& S, uint64_t n_cands) {
+    Instance I;
+    memset(&I, 0, sizeof(I));
+    I.r_toks4 = reinterpret_cast<const uint4*>(R.d_toks);
+    I.r_desc = R.d_desc;
+    I.r_n_sets = R.n_sets;
+    I.s_toks4 = reinterpret_cast<const uint4*>(S.d_toks);
+    I.s_desc = S.d_desc;
+    I.s_n_sets = S.n_sets;
+    I.p = b->p;
+    I.den = b->p + b->q;
+    I.magic = div_magic(I.den);
+    I.flags = vflags(b->flags) | (b->R == b->S ? VF_SELF_JOIN : 0u);
+    I.n_probes = b->n_probes;
+    I.n_cands = n_cands;
+    I.tile_base = 0;
+    return I;
+}
+
 VerifyArgs make_args(ssj_ctx* ctx, const ssj_batch* b, const Collection& R, const Collection& S, uint64_t n_cands) {
     VerifyArgs a;
     memset(&a, 0, sizeof(a));
-    a.R = R.dev();
-    a.S = S.dev();
-    a.p = b->p;
-    a.q = b->q;
-    a.den = b->p + b->q;
-    a.magic = div_magic(a.den);
-    a.self_join = b->R == b->S ? 1u : 0u;
-    a.flags = vflags(b->flags);
-    a.n_probes = b->n_probes;
-    a.n_cands = n_cands;
+    a.single = make_instance(b, R, S, n_cands);
+    a.table = nullptr;
     a.thread_max_key = ctx->thread_max_key;
     a.warp_max_key = ctx->warp_max_key;
     return a;
@@ -554,12 +566,12 @@ extern "C" ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batc
     st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(batch->n_probes, batch->n_cands, ctx->num_sms));
     if (st != SSJ_OK) return st;
     VerifyArgs a = make_args(ctx, batch, *R, *S, batch->n_cands);
-    a.probe_ids = batch->probe_ids;
-    a.cand_offsets = batch->cand_offsets;
-    a.cand_ids = batch->cand_ids;
-    a.out = d_out;
-    a.cap = (batch->flags & SSJ_COUNT_ONLY) ? 0 : cap;
-    a.count = reinterpret_cast<unsigned long long*>(d_count);
+    a.single.probe_ids = batch->probe_ids;
+    a.single.cand_offsets = batch->cand_offsets;
+    a.single.cand_ids = batch->cand_ids;
+    a.single.out = d_out;
+    a.single.cap = (batch->flags & SSJ_COUNT_ONLY) ? 0 : cap;
+    a.single.count = reinterpret_cast<unsigned long long*>(d_count);
     bind_workspace(a, ctx->ws, batch->n_probes, batch->n_cands, ctx->num_sms);
     ctx->last_ctr = a.ctr;
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
@@ -622,29 +634,29 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
         }
         if (n_cands)
             CUDA_TRY(ctx, cudaMemcpyAsync(d_cand, batch->cand_ids, 4ull * n_cands, cudaMemcpyHostToDevice, s));
-        a.probe_ids = d_probe;
-        a.cand_offsets = d_offs;
-        a.cand_ids = d_cand;
-        a.out = d_out;
-        a.cap = out_cap;
+        a.single.probe_ids = d_probe;
+        a.single.cand_offsets = d_offs;
+        a.single.cand_ids = d_cand;
+        a.single.out = d_out;
+        a.single.cap = out_cap;
     } else {
         n_cands = batch->n_cands;
         if (batch->n_probes && (!batch->probe_ids || !batch->cand_offsets))
             return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
         if (n_cands && !batch->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
         a = make_args(ctx, batch, *R, *S, n_cands);
-        a.probe_ids = batch->probe_ids;
-        a.cand_offsets = batch->cand_offsets;
-        a.cand_ids = batch->cand_ids;
-        a.out = out;
-        a.cap = count_only ? 0 : cap;
+        a.single.probe_ids = batch->probe_ids;
+        a.single.cand_offsets = batch->cand_offsets;
+        a.single.cand_ids = batch->cand_ids;
+        a.single.out = out;
+        a.single.cap = count_only ? 0 : cap;
         st = ensure_device_buffer(ctx, &ctx->io, &ctx->io_bytes, 256);
         if (st != SSJ_OK) return st;
         d_count = static_cast<uint64_t*>(ctx->io);
     }
     st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(batch->n_probes, n_cands, ctx->num_sms));
     if (st != SSJ_OK) return st;
-    a.count = reinterpret_cast<unsigned long long*>(d_count);
+    a.single.count = reinterpret_cast<unsigned long long*>(d_count);
     bind_workspace(a, ctx->ws, batch->n_probes, n_cands, ctx->num_sms);
     ctx->last_ctr = a.ctr;
     cudaError_t e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
@@ -664,7 +676,7 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
     if (count_only) return SSJ_OK;
     const uint64_t n_copy = std::min(count, cap);
     if (!dev) {
-        if (n_copy) CUDA_TRY(ctx, cudaMemcpy(out, a.out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost));
+        if (n_copy) CUDA_TRY(ctx, cudaMemcpy(out, a.single.out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost));
         if (batch->flags & SSJ_SORTED) std::sort(out, out + n_copy, triple_less);
     } else if ((batch->flags & SSJ_SORTED) && n_copy) {
         std::vector<ssj_triple> h(n_copy);
@@ -825,20 +837,20 @@ extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t*
             cudaMemcpyAsync(d_offs, sl.h_offs, 8ull * (batch->n_probes + 1), cudaMemcpyHostToDevice, s);
         }
         if (n_cands) cudaMemcpyAsync(d_cand, sl.h_cand, 4ull * n_cands, cudaMemcpyHostToDevice, s);
-        a.probe_ids = d_probe;
-        a.cand_offsets = d_offs;
-        a.cand_ids = d_cand;
+        a.single.probe_ids = d_probe;
+        a.single.cand_offsets = d_offs;
+        a.single.cand_ids = d_cand;
     } else {
-        a.probe_ids = batch->probe_ids;
-        a.cand_offsets = batch->cand_offsets;
-        a.cand_ids = batch->cand_ids;
+        a.single.probe_ids = batch->probe_ids;
+        a.single.cand_offsets = batch->cand_offsets;
+        a.single.cand_ids = batch->cand_ids;
     }
     uint64_t* d_count = reinterpret_cast<uint64_t*>(base + off); off += 256;
     void* ws = base + off; off += align256(workspace_bytes(batch->n_probes, n_cands, ctx->num_sms));
     ssj_triple* d_out = count_only ? nullptr : reinterpret_cast<ssj_triple*>(base + off);
-    a.out = d_out;
-    a.cap = count_only ? 0 : n_cands;
-    a.count = reinterpret_cast<unsigned long long*>(d_count);
+    a.single.out = d_out;
+    a.single.cap = count_only ? 0 : n_cands;
+    a.single.count = reinterpret_cast<unsigned long long*>(d_count);
     bind_workspace(a, ws, batch->n_probes, n_cands, ctx->num_sms);
     e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, nullptr);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_count, d_count, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
@@ -849,7 +861,7 @@ extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t*
         return unreserve(cuda_fail(ctx, e, "submit"));
     }
     t->d_out = d_out;
-    t->out_cap = a.cap;
+    t->out_cap = a.single.cap;
     lk.lock();
     Ticket* raw = t.get();
     ctx->tickets[raw->id] = std::move(t);
@@ -942,9 +954,9 @@ ssj_status resolve_device_batch(ssj_ctx* ctx, const ssj_batch* batch, VerifyArgs
         return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
     if (batch->n_cands && !batch->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
     *a = make_args(ctx, batch, *R, *S, batch->n_cands);
-    a->probe_ids = batch->probe_ids;
-    a->cand_offsets = batch->cand_offsets;
-    a->cand_ids = batch->cand_ids;
+    a->single.probe_ids = batch->probe_ids;
+    a->single.cand_offsets = batch->cand_offsets;
+    a->single.cand_ids = batch->cand_ids;
     *device = ctx->device;
     *num_sms = ctx->num_sms;
     *block_threads = ctx->block_threads;
@@ -956,3 +968,133 @@ ssj_status report(ssj_ctx* ctx, ssj_status st, const char* msg) { return fail(ct
 void remember_counters(ssj_ctx* ctx, Counters* c) { ctx->last_ctr = c; }
 
 }  // namespace ssj
+
+// ===========================================================================
+// Batched instances
+// ===========================================================================
+
+struct ssj_multi {
+    VerifyArgs a;
+    LaunchShape shape;
+    void* ws = nullptr;
+    std::vector<ssj_coll> colls;  // collections marked busy
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, uint32_t n_batches,
+                                       ssj_triple* const* d_outs, const uint64_t* caps, uint64_t* d_counts,
+                                       ssj_multi** out) {
+    if (!ctx || !out || (n_batches && (!batches || !d_outs || !caps || !d_counts)))
+        return fail(ctx, SSJ_EINVAL, "NULL argument");
+    std::vector<Instance> table(n_batches);
+    LaunchShape sh;
+    sh.n_inst = n_batches;
+    sh.n_tiles = 0;
+    sh.total_probes = 0;
+    sh.total_cands = 0;
+    std::unique_ptr<ssj_multi> m(new ssj_multi());
+    for (uint32_t i = 0; i < n_batches; ++i) {
+        const ssj_batch* b = &batches[i];
+        Collection *R, *S;
+        ssj_status st = resolve(ctx, b, &R, &S);
+        if (st != SSJ_OK) return st;
+        if (b->n_probes && (!b->probe_ids || !b->cand_offsets)) return fail(ctx, SSJ_EINVAL, "batch %u: NULL arrays", i);
+        if (b->n_cands && !b->cand_ids) return fail(ctx, SSJ_EINVAL, "batch %u: NULL cand_ids", i);
+        if (caps[i] && !d_outs[i] && !(b->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "batch %u: NULL output", i);
+        Instance I = make_instance(b, *R, *S, b->n_cands);
+        I.probe_ids = b->probe_ids;
+        I.cand_offsets = b->cand_offsets;
+        I.cand_ids = b->cand_ids;
+        I.out = d_outs[i];
+        I.cap = (b->flags & SSJ_COUNT_ONLY) ? 0 : caps[i];
+        I.count = reinterpret_cast<unsigned long long*>(d_counts + i);
+        I.tile_base = sh.n_tiles;
+        const uint64_t tiles = ((uint64_t)b->n_probes + 31) / 32;
+        if ((uint64_t)sh.n_tiles + tiles > 0x7FFFFFFull) return fail(ctx, SSJ_EINVAL, "too many probes in one launch");
+        sh.n_tiles += (uint32_t)tiles;
+        sh.total_probes += b->n_probes;
+        sh.total_cands += b->n_cands;
+        table[i] = I;
+        m->colls.push_back(b->R);
+        m->colls.push_back(b->S);
+    }
+    DeviceGuard g(ctx->device);
+    const size_t bytes = workspace_bytes(sh, ctx->num_sms);
+    cudaError_t e = cudaMalloc(&m->ws, bytes);
+    if (e != cudaSuccess) return fail(ctx, SSJ_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    memset(&m->a, 0, sizeof(m->a));
+    m->a.thread_max_key = ctx->thread_max_key;
+    m->a.warp_max_key = ctx->warp_max_key;
+    bind_workspace(m->a, m->ws, sh, ctx->num_sms);
+    m->a.table = m->a.table_out;
+    m->shape = sh;
+    if (n_batches) {
+        e = cudaMemcpy(m->a.table_out, table.data(), sizeof(Instance) * n_batches, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(m->ws);
+            return cuda_fail(ctx, e, "instance table upload");
+        }
+    }
+    e = prepare_verify(ctx->block_threads);
+    if (e != cudaSuccess) {
+        cudaFree(m->ws);
+        return cuda_fail(ctx, e, "prepare_verify");
+    }
+    {
+        std::unique_lock<std::mutex> lk(ctx->mu);
+        for (ssj_coll c : m->colls) ctx->colls[c].busy++;
+    }
+    *out = m.release();
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_multi_launch(ssj_ctx* ctx, ssj_multi* m, void* stream) {
+    if (!ctx || !m) return SSJ_EINVAL;
+    DeviceGuard g(ctx->device);
+    ctx->last_ctr = m->a.ctr;
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    cudaError_t e = launch_verify(m->a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_verify");
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_multi_graph_launch(ssj_ctx* ctx, ssj_multi* m, void* stream) {
+    if (!ctx || !m) return SSJ_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!m->exec) {
+        CUDA_TRY(ctx, cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+        CUDA_TRY(ctx, cudaStreamBeginCapture(m->capture_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_verify(m->a, m->capture_stream, ctx->num_sms, ctx->block_threads, nullptr);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(m->capture_stream, &graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "capture launch_verify");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+        m->graph = graph;
+        CUDA_TRY(ctx, cudaGraphInstantiate(&m->exec, m->graph, 0));
+    }
+    ctx->last_ctr = m->a.ctr;
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    CUDA_TRY(ctx, cudaGraphLaunch(m->exec, s));
+    return SSJ_OK;
+}
+
+extern "C" void ssj_multi_destroy(ssj_ctx* ctx, ssj_multi* m) {
+    if (!m) return;
+    if (ctx) {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        std::unique_lock<std::mutex> lk(ctx->mu);
+        for (ssj_coll c : m->colls) {
+            auto it = ctx->colls.find(c);
+            if (it != ctx->colls.end() && it->second.busy) it->second.busy--;
+        }
+        if (ctx->last_ctr == m->a.ctr) ctx->last_ctr = nullptr;
+    }
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->graph) cudaGraphDestroy(m->graph);
+    if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+    cudaFree(m->ws);
+    delete m;
+}

@@ -74,9 +74,9 @@ extern "C" ssj_status ssj_verify_batch_noalloc(ssj_ctx* ctx, const ssj_batch* ba
     void* scratch = nullptr;
     cudaError_t e = scratch_address(device, &scratch);
     if (e == cudaSuccess) {
-        a.out = d_out;
-        a.cap = (batch->flags & SSJ_COUNT_ONLY) ? 0 : cap;
-        a.count = reinterpret_cast<unsigned long long*>(d_count);
+        a.single.out = d_out;
+        a.single.cap = (batch->flags & SSJ_COUNT_ONLY) ? 0 : cap;
+        a.single.count = reinterpret_cast<unsigned long long*>(d_count);
         bind_workspace(a, scratch, batch->n_probes, batch->n_cands, num_sms);
         remember_counters(ctx, a.ctr);
         // launch_verify clears the counters and the count before the kernels run

@@ -1,5 +1,5 @@
-// Internal declarations shared by the host API (api.cu) and the kernels
-// (verify.cu).  Not part of the public ABI.
+// Internal declarations shared by the host API (api.cu, noalloc.cu) and the
+// kernels (verify.cu).  Not part of the public ABI.
 #pragma once
 
 #include <cstdint>
@@ -18,24 +18,61 @@ struct DevColl {
     uint32_t n_sets;
 };
 
+enum : uint32_t {
+    VF_COUNT_ONLY = 1u,
+    VF_EMIT_ALL = 2u,
+    VF_FORCE_THREAD = 4u,
+    VF_FORCE_WARP = 8u,
+    VF_FORCE_BLOCK = 16u,
+    VF_SELF_JOIN = 32u,
+};
+
+// One join instance of a launch: its collections, grouped candidate list,
+// threshold and output.  A launch verifies any number of instances; the
+// table of them lives in device memory (the workspace).
+struct Instance {
+    const uint4* r_toks4;
+    const uint2* r_desc;
+    const uint4* s_toks4;
+    const uint2* s_desc;
+    const uint32_t* probe_ids;
+    const uint64_t* cand_offsets;
+    const uint32_t* cand_ids;
+    ssj_triple* out;
+    unsigned long long* count;  // result pairs of this instance (may exceed cap)
+    uint64_t magic;             // div_magic(p + q)
+    uint64_t n_cands;
+    uint64_t cap;
+    uint32_t r_n_sets, s_n_sets;
+    uint32_t p, den;            // t = p / q, den = p + q
+    uint32_t n_probes;
+    uint32_t tile_base;         // first plan tile (32 probes) of this instance
+    uint32_t flags;             // VF_*
+    uint32_t pad;
+};
+
 // Work item for warp- or block-per-pair verification: n candidates of probe
-// set r starting at candidate index c0.
+// set r starting at candidate index c0, in instance inst.
 struct WorkItem {
     uint32_t r;
     uint32_t n;
     uint64_t c0;
+    uint32_t inst;
+    uint32_t pad;
 };
 
-// One short pair of the compacted list: probe index k (into probe_ids) and
-// candidate set id s.
+// One short pair of the compacted list: probe slot k (index into the
+// launch's per-probe arrays) and candidate set id s.  k == kNoProbe marks a
+// padding slot.
 struct PairRef {
     uint32_t k;
     uint32_t s;
 };
+constexpr uint32_t kNoProbe = 0xFFFFFFFFu;
 
 // Per-call counters, cleared by one memset before the plan kernel.
 struct Counters {
-    unsigned long long thread_pairs;  // entries of the compacted short-pair list
+    unsigned long long thread_pairs;  // slots of the compacted short-pair list (multiple of 32)
     unsigned long long warp_items;    // warp work items written by the plan kernel
     unsigned long long block_items;   // block work items written by the plan kernel
     uint32_t block_cursor;            // dynamic cursors of the verify kernel
@@ -51,51 +88,54 @@ enum : uint32_t {
     ERR_GUARD = 8u,   // an internal loop bound was reached (a bug, reported instead of hanging)
 };
 
-enum : uint32_t {
-    VF_COUNT_ONLY = 1u,
-    VF_EMIT_ALL = 2u,
-    VF_FORCE_THREAD = 4u,
-    VF_FORCE_WARP = 8u,
-    VF_FORCE_BLOCK = 16u,
-};
-
-
 constexpr uint32_t kWarpItemCands = 8;   // most candidates per warp work item
 constexpr uint32_t kBlockItemCands = 16; // most candidates per block work item
 constexpr uint32_t kThreadKeyCap = 1024; // largest 2|r| verified one pair per thread
 
+// Kernel arguments of one launch (passed by value).
 struct VerifyArgs {
-    DevColl R, S;
-    uint32_t p, q;
-    uint32_t den;                 // p + q
-    uint64_t magic;               // div_magic(p + q), for the required overlap
-    uint32_t self_join;
-    uint32_t flags;               // VF_*
-    uint32_t n_probes;
-    const uint32_t* probe_ids;
-    const uint64_t* cand_offsets;
-    const uint32_t* cand_ids;
-    uint64_t n_cands;
-    ssj_triple* out;
-    uint64_t cap;
-    unsigned long long* count;    // result pairs (may exceed cap)
+    Instance single;              // the instance of a one-batch launch (table == nullptr)
+    const Instance* table;        // device table of n_inst instances, or nullptr
+    Instance* table_out;          // where the plan kernel stores `single` for the verify kernel
+    uint32_t n_inst;
+    uint32_t n_tiles;             // plan tiles over all instances
+    uint32_t total_probes;        // probe slots over all instances (instance-major)
+    uint64_t total_cands;
     Counters* ctr;
-    uint2* rdesc;                 // per probe: descriptor of its set r (plan output)
-    PairRef* pairs;               // compacted short pairs (plan output)
+    uint2* rdesc;                 // per probe slot: descriptor of its set r
+    uint32_t* rid;                // per probe slot: id of its set r
+    uint32_t* chunk_inst;         // per 32-slot chunk of the pair list: its instance
+    PairRef* pairs;               // compacted short pairs
     WorkItem* warp_items;
     WorkItem* block_items;
+    uint64_t pair_cap;
     uint32_t warp_item_cap, block_item_cap;
     uint32_t warp_item_cands, block_item_cands;  // candidates per work item
     uint32_t thread_max_key;      // 2|r| <= this: one thread per pair
     uint32_t warp_max_key;        // 2|r| <= this: one warp per pair; above: one block
 };
 
-// Scratch a call needs, in bytes, for n_probes / n_cands on a device with
-// num_sms SMs.
+// Sizes of one launch, from which the workspace is carved.
+struct LaunchShape {
+    uint32_t n_inst;
+    uint32_t n_tiles;
+    uint32_t total_probes;
+    uint64_t total_cands;
+};
+
+// Scratch a launch of this shape needs, in bytes, on a device with num_sms SMs.
+size_t workspace_bytes(const LaunchShape& sh, int num_sms);
+// Shape of a one-batch launch.
+LaunchShape single_shape(uint32_t n_probes, uint64_t n_cands);
 size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands, int num_sms);
 
 // Carve the workspace and fill the scratch pointers of a.
+void bind_workspace(VerifyArgs& a, void* ws, const LaunchShape& sh, int num_sms);
 void bind_workspace(VerifyArgs& a, void* ws, uint32_t n_probes, uint64_t n_cands, int num_sms);
+
+// Set the verify kernel's launch attributes for this device (done by the
+// first launch anyway; call before capturing a launch into a graph).
+cudaError_t prepare_verify(uint32_t block_threads);
 
 // Enqueue the whole verification (counter clear, plan, verify) on st.
 // ev (optional, 3 events): recorded before the plan kernel, between plan and

@@ -130,63 +130,24 @@ __device__ __forceinline__ void block_step(const uint4& rc, const uint4& sc, uin
 }
 
 // ceil(p*(nr+ns)/(p+q)): Jaccard's equivalent overlap with t = p/q, by the
-// batch's precomputed reciprocal of p+q (exact; see arith.h).
-__device__ __forceinline__ uint32_t required_overlap(const VerifyArgs& a, uint32_t nr, uint32_t ns) {
-    return required_overlap_magic(nr, ns, a.p, a.den, a.magic);
+// instance's precomputed reciprocal of p+q (exact; see arith.h).
+__device__ __forceinline__ uint32_t required_overlap(uint32_t p, uint32_t den, uint64_t magic, uint32_t nr,
+                                                     uint32_t ns) {
+    return required_overlap_magic(nr, ns, p, den, magic);
 }
 
-__device__ __forceinline__ void emit_triple(const VerifyArgs& a, unsigned long long idx, uint32_t r, uint32_t s,
-                                            uint32_t o) {
-    if (idx < a.cap) {
+// Write result idx of an instance (if it fits its capacity), as (min, max)
+// ids for a self-join.
+__device__ __forceinline__ void emit_triple(ssj_triple* out, uint64_t cap, bool self_join, unsigned long long idx,
+                                            uint32_t r, uint32_t s, uint32_t o) {
+    if (idx < cap) {
         uint32_t x = r, y = s;
-        if (a.self_join && y < x) { x = s; y = r; }
-        ssj_triple* t = a.out + idx;
+        if (self_join && y < x) { x = s; y = r; }
+        ssj_triple* t = out + idx;
         t->r = x;
         t->s = y;
         t->overlap = o;
     }
-}
-
-// -------------------------------------------------------------------------
-// Sequential merge of one pair by one thread (Alternatives A/B).  Both sets
-// are read 16 bytes at a time (sets start 16-byte aligned and are padded to
-// a multiple of 16 bytes); the next 16 bytes of each side are prefetched
-// one step ahead.  Returns the overlap; *rejected is set when the positional
-// bound fired.
-// -------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t thread_merge(const uint4* __restrict__ r4, uint32_t nr,
-                                                 const uint4* __restrict__ s4, uint32_t ns, uint32_t req,
-                                                 bool early, bool* rejected) {
-    *rejected = false;
-    if (nr == 0 || ns == 0) return 0;
-    const uint32_t rq = (nr + 3) >> 2, sq = (ns + 3) >> 2;
-    uint4 r0 = __ldg(r4), s0 = __ldg(s4);
-    uint4 r1 = rq > 1 ? __ldg(r4 + 1) : r0;
-    uint4 s1 = sq > 1 ? __ldg(s4 + 1) : s0;
-    uint32_t i = 0, j = 0, o = 0;
-    while (i < nr && j < ns) {
-        if (early && o + min(nr - i, ns - j) < req) { *rejected = true; break; }
-        const uint32_t x = sel4(r0, i & 3u), y = sel4(s0, j & 3u);
-        const bool ta = x <= y, tb = x >= y;
-        o += (ta && tb) ? 1u : 0u;
-        if (ta) {
-            ++i;
-            if ((i & 3u) == 0) {
-                r0 = r1;
-                const uint32_t nq = (i >> 2) + 1;
-                if (nq < rq) r1 = __ldg(r4 + nq);
-            }
-        }
-        if (tb) {
-            ++j;
-            if ((j & 3u) == 0) {
-                s0 = s1;
-                const uint32_t nq = (j >> 2) + 1;
-                if (nq < sq) s1 = __ldg(s4 + nq);
-            }
-        }
-    }
-    return o;
 }
 
 // Copy the 16-byte chunks covering tokens [x0, x0+n) of a set into dst
@@ -334,29 +295,30 @@ __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const
     return o;
 }
 
-// Warp-local survivor buffer for pairs decided by the whole warp: lane k
-// holds the k-th buffered triple; flushed with one atomic per 32.
+// Warp-local survivor buffer for pairs decided by the whole warp (one work
+// item, so one instance): lane k holds the k-th buffered triple; flushed
+// with one atomic per 32 and at the end of every item.
 struct WarpOut {
     uint32_t r = 0, s = 0, o = 0, n = 0;
 
-    __device__ void push(const VerifyArgs& a, int lane, uint32_t pr, uint32_t ps, uint32_t po) {
+    __device__ void push(const Instance& I, int lane, uint32_t pr, uint32_t ps, uint32_t po) {
         if (lane == (int)n) { r = pr; s = ps; o = po; }
-        if (++n == 32) flush(a, lane);
+        if (++n == 32) flush(I, lane);
     }
-    __device__ void flush(const VerifyArgs& a, int lane) {
+    __device__ void flush(const Instance& I, int lane) {
         if (n == 0) return;
         unsigned long long b0 = 0;
-        if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)n);
+        if (lane == 0) b0 = atomicAdd(I.count, (unsigned long long)n);
         b0 = __shfl_sync(kFull, b0, 0);
-        if ((uint32_t)lane < n) emit_triple(a, b0 + lane, r, s, o);
+        if ((uint32_t)lane < n) emit_triple(I.out, I.cap, (I.flags & VF_SELF_JOIN) != 0, b0 + lane, r, s, o);
         n = 0;
     }
 };
 
-__device__ __forceinline__ uint32_t probe_bin(const VerifyArgs& a, uint32_t nr) {
-    if (a.flags & VF_FORCE_BLOCK) return 2;
-    if (a.flags & VF_FORCE_WARP) return 1;
-    if (a.flags & VF_FORCE_THREAD) return 0;
+__device__ __forceinline__ uint32_t probe_bin(const VerifyArgs& a, uint32_t flags, uint32_t nr) {
+    if (flags & VF_FORCE_BLOCK) return 2;
+    if (flags & VF_FORCE_WARP) return 1;
+    if (flags & VF_FORCE_THREAD) return 0;
     const uint64_t key = 2ull * nr;  // |r|+|s| at |s| = |r|
     return key <= a.thread_max_key ? 0u : (key <= a.warp_max_key ? 1u : 2u);
 }
@@ -378,46 +340,104 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
     return base + incl - want;
 }
 
+// Instance fields read by the plan kernel (from the kernel parameters for a
+// one-batch launch, else from the device table).
+struct PlanInst {
+    const uint32_t* probe_ids;
+    const uint64_t* cand_offsets;
+    const uint32_t* cand_ids;
+    const uint2* r_desc;
+    uint64_t n_cands;
+    uint32_t r_n_sets, n_probes, tile_base, flags;
+};
+
+__device__ __forceinline__ PlanInst plan_inst(const VerifyArgs& a, uint32_t i) {
+    PlanInst q;
+    if (a.table) {
+        const Instance* I = a.table + i;
+        q.probe_ids = I->probe_ids;
+        q.cand_offsets = I->cand_offsets;
+        q.cand_ids = I->cand_ids;
+        q.r_desc = I->r_desc;
+        q.n_cands = I->n_cands;
+        q.r_n_sets = I->r_n_sets;
+        q.n_probes = I->n_probes;
+        q.tile_base = I->tile_base;
+        q.flags = I->flags;
+    } else {
+        q.probe_ids = a.single.probe_ids;
+        q.cand_offsets = a.single.cand_offsets;
+        q.cand_ids = a.single.cand_ids;
+        q.r_desc = a.single.r_desc;
+        q.n_cands = a.single.n_cands;
+        q.r_n_sets = a.single.r_n_sets;
+        q.n_probes = a.single.n_probes;
+        q.tile_base = a.single.tile_base;
+        q.flags = a.single.flags;
+    }
+    return q;
+}
+
 }  // namespace
 
 // -------------------------------------------------------------------------
-// Plan: one thread per probe; every warp iterates in lockstep so the
-// warp-level reservations see all 32 lanes.
+// Plan.  The probes of every instance are cut into tiles of 32; warp w takes
+// tiles w, w + n_warps, ...  Lane l of tile t of an instance with T tiles
+// takes probe t + l*T, so a warp's 32 probes are spread over the instance and
+// warps get similar amounts of copying even when probes come in size order.
+// Each probe is validated and binned; short probes append their pairs to
+// the compacted list (a warp's range is padded to whole 32-slot chunks, so
+// a chunk never mixes instances), longer probes become work items.
 // -------------------------------------------------------------------------
 __global__ void plan_kernel(VerifyArgs a) {
     const int lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const uint32_t n_warps = stride >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    // Lane l of warp w takes probe base + l * n_warps + w: a warp's 32 probes are
-    // spread over the batch, so warps get similar amounts of copying even when
-    // the batch lists probes in size order.
-    for (uint32_t base = 0; base < a.n_probes; base += stride) {
-        const uint32_t k = base + (uint32_t)lane * n_warps + gw;
+    if (blockIdx.x == 0) {
+        if (!a.table && threadIdx.x == 0) a.table_out[0] = a.single;
+        for (uint32_t i = threadIdx.x; i < a.n_inst; i += blockDim.x)
+            *(a.table ? a.table[i].count : a.single.count) = 0ull;
+    }
+    for (uint32_t g = gw; g < a.n_tiles; g += n_warps) {
+        // instance owning tile g: the last one whose tile_base <= g
+        uint32_t inst = 0;
+        if (a.table) {
+            uint32_t lo = 0, hi = a.n_inst - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (a.table[mid].tile_base <= g) lo = mid; else hi = mid - 1;
+            }
+            inst = lo;
+        }
+        const PlanInst I = plan_inst(a, inst);
+        const uint32_t T = (I.n_probes + 31) >> 5;
+        const uint32_t t = g - I.tile_base;
+        const uint32_t k = t + (uint32_t)lane * T;           // local probe index
+        const uint32_t slot = I.tile_base * 32u + (uint32_t)lane * T + t;  // probe slot, unique per launch
         uint64_t c0 = 0, n = 0;
         uint32_t r = 0, bin = 0;
         uint2 rdesc = make_uint2(0, 0);
-        if (k < a.n_probes) {
-            c0 = a.cand_offsets[k];
-            const uint64_t c1 = a.cand_offsets[k + 1];
-            if ((k == 0 && c0 != 0) || (k + 1 == a.n_probes && c1 != a.n_cands) || c1 < c0 || c1 > a.n_cands) {
+        if (k < I.n_probes) {
+            c0 = I.cand_offsets[k];
+            const uint64_t c1 = I.cand_offsets[k + 1];
+            if ((k == 0 && c0 != 0) || (k + 1 == I.n_probes && c1 != I.n_cands) || c1 < c0 || c1 > I.n_cands) {
                 atomicOr(&a.ctr->err, ERR_OFFSETS);
             } else {
-                r = a.probe_ids[k];
-                if (r >= a.R.n_sets) {
+                r = I.probe_ids[k];
+                if (r >= I.r_n_sets) {
                     if (c1 > c0) atomicOr(&a.ctr->err, ERR_PROBE_ID);
                 } else {
-                    rdesc = a.R.desc[r];
-                    a.rdesc[k] = rdesc;
+                    rdesc = I.r_desc[r];
+                    a.rdesc[slot] = rdesc;
+                    a.rid[slot] = r;
                     n = c1 - c0;
-                    bin = probe_bin(a, rdesc.y);
+                    bin = probe_bin(a, I.flags, rdesc.y);
                 }
             }
         }
-        // short probes: append (probe, candidate) pairs to the compacted list.
-        // The warp's 32 probes own one contiguous range [wbase0, wbase0 + T) of
-        // the list in lane order, so the warp copies it as one flat, coalesced
-        // range; each slot finds its probe by a search over the lanes' prefix sums.
+        // short probes: the warp's pairs form one contiguous, chunk-aligned range
+        // of the list; it is copied flat and coalesced, each slot finding its probe
+        // by a search over the lanes' prefix sums
         const unsigned long long tn = (bin == 0) ? n : 0;
         unsigned long long tincl = tn;
 #pragma unroll
@@ -426,36 +446,41 @@ __global__ void plan_kernel(VerifyArgs a) {
             if (lane >= off) tincl += y;
         }
         const unsigned long long ttotal = __shfl_sync(kFull, tincl, 31);
+        const unsigned long long tpadded = (ttotal + 31) & ~31ull;
         unsigned long long tbase0 = 0;
-        if (lane == 31 && ttotal) tbase0 = atomicAdd(&a.ctr->thread_pairs, ttotal);
+        if (lane == 31 && tpadded) tbase0 = atomicAdd(&a.ctr->thread_pairs, tpadded);
         tbase0 = __shfl_sync(kFull, tbase0, 31);
-        const unsigned long long texcl = tincl - tn;
-        for (unsigned long long f0 = 0; f0 < ttotal; f0 += 4 * 32) {
-            uint32_t v[4], kk[4];
+        if (tbase0 + tpadded > a.pair_cap) {  // cannot happen with a sized workspace
+            if (lane == 0 && tpadded) atomicOr(&a.ctr->err, ERR_GUARD);
+        } else {
+            const unsigned long long texcl = tincl - tn;
+            for (unsigned long long c = lane; c < tpadded / 32; c += 32) a.chunk_inst[tbase0 / 32 + c] = inst;
+            for (unsigned long long f0 = 0; f0 < tpadded; f0 += 4 * 32) {
+                uint32_t v[4], kk[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const unsigned long long f = f0 + u * 32 + lane;
-                // owning lane: the number of lanes whose inclusive prefix is <= f
-                uint32_t pos = 0;
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long f = f0 + u * 32 + lane;
+                    uint32_t pos = 0;
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const unsigned long long w = __shfl_sync(kFull, tincl, pos + step - 1);
-                    if (w <= f) pos += step;
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const unsigned long long w = __shfl_sync(kFull, tincl, pos + step - 1);
+                        if (w <= f) pos += step;
+                    }
+                    pos = min(pos, 31u);
+                    const unsigned long long oc0 = __shfl_sync(kFull, c0, pos);
+                    const unsigned long long oex = __shfl_sync(kFull, texcl, pos);
+                    kk[u] = __shfl_sync(kFull, slot, pos);
+                    v[u] = (f < ttotal) ? I.cand_ids[oc0 + (f - oex)] : 0u;
                 }
-                pos = min(pos, 31u);
-                const unsigned long long oc0 = __shfl_sync(kFull, c0, pos);
-                const unsigned long long oex = __shfl_sync(kFull, texcl, pos);
-                kk[u] = __shfl_sync(kFull, k, pos);
-                v[u] = (f < ttotal) ? a.cand_ids[oc0 + (f - oex)] : 0u;
-            }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const unsigned long long f = f0 + u * 32 + lane;
-                if (f < ttotal) {
-                    PairRef pr;
-                    pr.k = kk[u];
-                    pr.s = v[u];
-                    a.pairs[tbase0 + f] = pr;
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long f = f0 + u * 32 + lane;
+                    if (f < tpadded) {
+                        PairRef pr;
+                        pr.k = (f < ttotal) ? kk[u] : kNoProbe;
+                        pr.s = v[u];
+                        a.pairs[tbase0 + f] = pr;
+                    }
                 }
             }
         }
@@ -464,33 +489,38 @@ __global__ void plan_kernel(VerifyArgs a) {
         const unsigned long long wn = (bin == 1) ? (n + wc - 1) / wc : 0;
         const unsigned long long wbase = warp_reserve(&a.ctr->warp_items, wn, lane);
         for (unsigned long long it = 0; it < wn; ++it) {
-            if (wbase + it >= a.warp_item_cap) { atomicOr(&a.ctr->err, ERR_OFFSETS); break; }
+            if (wbase + it >= a.warp_item_cap) { atomicOr(&a.ctr->err, ERR_GUARD); break; }
             const uint64_t s0 = c0 + it * wc;
             WorkItem wi;
             wi.r = r;
             wi.n = (uint32_t)min((uint64_t)wc, c0 + n - s0);
             wi.c0 = s0;
+            wi.inst = inst;
+            wi.pad = 0;
             a.warp_items[wbase + it] = wi;
         }
         const unsigned long long bn = (bin == 2) ? (n + bc - 1) / bc : 0;
         const unsigned long long bbase = warp_reserve(&a.ctr->block_items, bn, lane);
         for (unsigned long long it = 0; it < bn; ++it) {
-            if (bbase + it >= a.block_item_cap) { atomicOr(&a.ctr->err, ERR_OFFSETS); break; }
+            if (bbase + it >= a.block_item_cap) { atomicOr(&a.ctr->err, ERR_GUARD); break; }
             const uint64_t s0 = c0 + it * bc;
             WorkItem bi;
             bi.r = r;
             bi.n = (uint32_t)min((uint64_t)bc, c0 + n - s0);
             bi.c0 = s0;
+            bi.inst = inst;
+            bi.pad = 0;
             a.block_items[bbase + it] = bi;
         }
     }
 }
 
 // -------------------------------------------------------------------------
-// Persistent verification kernel.
+// Persistent verification kernel.  Instance fields come from the device table
+// (table_out), loaded once per work item or per 32-pair chunk.
 // -------------------------------------------------------------------------
 template <int BT>
-__global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
+__global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ BlockSmem<BT> bsm;
     constexpr uint32_t kBlockWin = BT * kBlockD;
@@ -501,12 +531,9 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
     const int warp = tid >> 5;
     const uint32_t n_warps_total = gridDim.x * kWarps;
     const uint32_t gwarp = blockIdx.x * kWarps + warp;
-    const bool count_only = (a.flags & VF_COUNT_ONLY) != 0;
-    const bool emit_all = (a.flags & VF_EMIT_ALL) != 0;
-    const bool early = !emit_all;
-    unsigned long long local_count = 0;  // count-only mode (per lane)
+    const Instance* table = a.table_out;
 
-    if (a.ctr->err & ERR_OFFSETS) return;  // the plan is not trustworthy
+    if (a.ctr->err & (ERR_OFFSETS | ERR_GUARD)) return;  // the plan is not trustworthy
 
     // Static first-round assignment: phase 1 takes CTAs [0, n_bs); phase 2 starts
     // on the warps after those, phase 3 on the warps after phase 2's, so a small
@@ -514,10 +541,10 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
     const unsigned long long n_block = min(a.ctr->block_items, (unsigned long long)a.block_item_cap);
     const unsigned long long n_warp = min(a.ctr->warp_items, (unsigned long long)a.warp_item_cap);
     const uint32_t n_bs = (uint32_t)min(n_block, (unsigned long long)gridDim.x);
-    const uint32_t free2 = n_bs * kWarps;                                   // first warp free for phase 2
-    const uint32_t slots2 = n_warps_total - free2;                          // static phase-2 slots
+    const uint32_t free2 = n_bs * kWarps;
+    const uint32_t slots2 = n_warps_total - free2;
     const uint32_t free3 = free2 + (uint32_t)min(n_warp, (unsigned long long)slots2);
-    const uint32_t slots3 = n_warps_total - free3;                          // static phase-3 slots
+    const uint32_t slots3 = n_warps_total - free3;
 
     // ---------------- phase 1: block-per-pair items ----------------------
     if (n_block) {
@@ -525,52 +552,51 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
         uint32_t* wr = smem + kBlockRCap + 16;                // kBlockWin + 16
         uint32_t* ws = wr + kBlockWin + 16;                   // kBlockWin + 16
         for (uint32_t round = 0;; ++round) {
-            if (tid == 0)
-                bsm.item = round == 0 ? blockIdx.x : gridDim.x + atomicAdd(&a.ctr->block_cursor, 1u);  // all CTAs are static slots
+            if (tid == 0) bsm.item = round == 0 ? blockIdx.x : gridDim.x + atomicAdd(&a.ctr->block_cursor, 1u);
             __syncthreads();
             const uint32_t it = bsm.item;
             __syncthreads();
             if (it >= n_block) break;
             const WorkItem bi = a.block_items[it];
-            const uint2 dr = a.R.desc[bi.r];
+            const Instance& I = table[bi.inst];
+            const uint32_t flags = I.flags;
+            const bool emit_all = (flags & VF_EMIT_ALL) != 0, early = !emit_all;
+            const bool self_join = (flags & VF_SELF_JOIN) != 0;
+            const uint2 dr = I.r_desc[bi.r];
             const uint32_t nr = dr.y;
-            const uint4* r4 = a.R.toks4 + dr.x;
+            const uint4* r4 = I.r_toks4 + dr.x;
             const bool r_staged = nr + 4 <= kBlockRCap;
             if (r_staged) {
                 stage<BT>(r4, 0, nr, rbuf, tid);
                 __syncthreads();
             }
             for (uint32_t m = 0; m < bi.n; ++m) {
-                const uint32_t s = a.cand_ids[bi.c0 + m];
-                if (s >= a.S.n_sets) {
+                const uint32_t s = I.cand_ids[bi.c0 + m];
+                if (s >= I.s_n_sets) {
                     if (tid == 0) atomicOr(&a.ctr->err, ERR_CAND_ID);
                     continue;
                 }
-                if (a.self_join && s == bi.r) continue;
-                const uint2 ds = a.S.desc[s];
+                if (self_join && s == bi.r) continue;
+                const uint2 ds = I.s_desc[s];
                 const uint32_t ns = ds.y;
-                const uint32_t req = required_overlap(a, nr, ns);
+                const uint32_t req = required_overlap(I.p, I.den, I.magic, nr, ns);
                 if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
                 bool rej;
-                const uint32_t o = block_merge<BT>(r4, nr, a.S.toks4 + ds.x, ns, req, early, rbuf, r_staged, wr, ws,
+                const uint32_t o = block_merge<BT>(r4, nr, I.s_toks4 + ds.x, ns, req, early, rbuf, r_staged, wr, ws,
                                                    &bsm, &rej);
                 const bool pass = emit_all || (!rej && o >= req);
                 if (pass && tid == 0) {
-                    if (count_only) {
-                        ++local_count;
-                    } else {
-                        const unsigned long long idx = atomicAdd(a.count, 1ull);
-                        emit_triple(a, idx, bi.r, s, o);
-                    }
+                    const unsigned long long idx = atomicAdd(I.count, 1ull);
+                    if (!(flags & VF_COUNT_ONLY)) emit_triple(I.out, I.cap, self_join, idx, bi.r, s, o);
                 }
             }
             __syncthreads();  // rbuf reuse
         }
     }
 
-    WarpOut wout;
     // ---------------- phase 2: warp-per-pair items -----------------------
     if (n_warp) {
+        WarpOut wout;
         uint32_t* abuf = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem) + warp * kWarpSliceBytes);
         uint32_t* bbuf = abuf + kWarpABuf;
         for (uint32_t round = 0;; ++round) {
@@ -582,34 +608,42 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
             it = __shfl_sync(kFull, it, 0);
             if (it >= n_warp) break;
             const WorkItem wi = a.warp_items[it];
-            const uint2 dr = a.R.desc[wi.r];
+            const Instance& I = table[wi.inst];
+            const uint32_t flags = I.flags;
+            const bool emit_all = (flags & VF_EMIT_ALL) != 0, early = !emit_all;
+            const bool self_join = (flags & VF_SELF_JOIN) != 0;
+            const uint2 dr = I.r_desc[wi.r];
             const uint32_t nr = dr.y;
-            const uint4* r4 = a.R.toks4 + dr.x;
+            const uint4* r4 = I.r_toks4 + dr.x;
             const bool r_staged = nr + 4 <= kWarpRCap;
             if (r_staged) {
                 stage<32>(r4, 0, nr, abuf, lane);
                 __syncwarp();
             }
             for (uint32_t m = 0; m < wi.n; ++m) {
-                const uint32_t s = a.cand_ids[wi.c0 + m];
-                if (s >= a.S.n_sets) {
+                const uint32_t s = I.cand_ids[wi.c0 + m];
+                if (s >= I.s_n_sets) {
                     if (lane == 0) atomicOr(&a.ctr->err, ERR_CAND_ID);
                     continue;
                 }
-                if (a.self_join && s == wi.r) continue;
-                const uint2 ds = a.S.desc[s];
+                if (self_join && s == wi.r) continue;
+                const uint2 ds = I.s_desc[s];
                 const uint32_t ns = ds.y;
-                const uint32_t req = required_overlap(a, nr, ns);
+                const uint32_t req = required_overlap(I.p, I.den, I.magic, nr, ns);
                 if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
                 bool rej;
                 const uint32_t o =
-                    warp_merge(r4, nr, a.S.toks4 + ds.x, ns, req, early, r_staged, abuf, bbuf, lane, &rej);
+                    warp_merge(r4, nr, I.s_toks4 + ds.x, ns, req, early, r_staged, abuf, bbuf, lane, &rej);
                 const bool pass = emit_all || (!rej && o >= req);
                 if (pass) {
-                    if (count_only) local_count += (lane == 0) ? 1u : 0u;
-                    else wout.push(a, lane, wi.r, s, o);
+                    if (flags & VF_COUNT_ONLY) {
+                        if (lane == 0) atomicAdd(I.count, 1ull);
+                    } else {
+                        wout.push(I, lane, wi.r, s, o);
+                    }
                 }
             }
+            wout.flush(I, lane);
             __syncwarp();  // abuf reuse
         }
     }
@@ -618,56 +652,59 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
     {
         ContEntry* cont = reinterpret_cast<ContEntry*>(reinterpret_cast<char*>(smem) + warp * kWarpSliceBytes);
         uint32_t n_cont = 0;  // warp-uniform
-        const unsigned long long n_pairs = a.ctr->thread_pairs;
+        const unsigned long long n_pairs = min(a.ctr->thread_pairs, (unsigned long long)a.pair_cap);
         const unsigned long long n_units = (n_pairs + 32 * kFlatGrab - 1) / (32 * kFlatGrab);
         const unsigned lt_mask = (1u << lane) - 1u;
         const uint4 zero4 = make_uint4(0, 0, 0, 0);
 
-        // Pass 2: finish the parked pairs [n_cont - m, n_cont), one per lane.
+        // Pass 2: finish the parked pairs [n_cont - m, n_cont), one per lane
+        // (lanes may belong to different instances).
         auto drain = [&](uint32_t m) {
-            bool have = false;
-            uint32_t pr_id = 0, ps_id = 0, rs = 0, ss = 0, nr = 0, ns = 0, req = 0;
+            uint32_t pr_id = 0, ps_id = 0, rs = 0, ss = 0, nr = 0, ns = 0, req = 0, inst = 0;
             BlockState st;
             st.qi = st.qj = st.o = 0;
             st.fin = true;
             st.rej = false;
             uint4 rc = zero4, rn = zero4, sc = zero4, sn = zero4;
+            const uint4* rt = nullptr;
+            const uint4* stk = nullptr;
+            bool early = true;
             if ((uint32_t)lane < m) {
                 const ContEntry* ce = cont + (n_cont - m) + lane;
                 const uint4 m0 = ce->m0, m1 = ce->m1, m2 = ce->m2;
                 pr_id = m0.x; ps_id = m0.y; rs = m0.z; ss = m0.w;
                 nr = m1.x; ns = m1.y; req = m1.z;
-                st.o = m1.w; st.qi = m2.x; st.qj = m2.y;
+                st.o = m1.w; st.qi = m2.x; st.qj = m2.y; inst = m2.z;
                 st.fin = false;
-                have = true;
+                const Instance& I = table[inst];
+                rt = I.r_toks4 + rs;
+                stk = I.s_toks4 + ss;
+                early = !(I.flags & VF_EMIT_ALL);
                 const uint32_t rq = (nr + 3) >> 2, sq = (ns + 3) >> 2;
-                rc = __ldg(a.R.toks4 + rs + st.qi);
-                if (st.qi + 1 < rq) rn = __ldg(a.R.toks4 + rs + st.qi + 1);
-                sc = __ldg(a.S.toks4 + ss + st.qj);
-                if (st.qj + 1 < sq) sn = __ldg(a.S.toks4 + ss + st.qj + 1);
+                rc = __ldg(rt + st.qi);
+                if (st.qi + 1 < rq) rn = __ldg(rt + st.qi + 1);
+                sc = __ldg(stk + st.qj);
+                if (st.qj + 1 < sq) sn = __ldg(stk + st.qj + 1);
             }
+            const bool have = (uint32_t)lane < m;
             while (!st.fin) {
                 bool ar, as;
                 block_step(rc, sc, nr, ns, req, early, st, ar, as);
                 if (ar) {
                     rc = rn;
-                    if (st.qi + 1 < ((nr + 3) >> 2)) rn = __ldg(a.R.toks4 + rs + st.qi + 1);
+                    if (st.qi + 1 < ((nr + 3) >> 2)) rn = __ldg(rt + st.qi + 1);
                 }
                 if (as) {
                     sc = sn;
-                    if (st.qj + 1 < ((ns + 3) >> 2)) sn = __ldg(a.S.toks4 + ss + st.qj + 1);
+                    if (st.qj + 1 < ((ns + 3) >> 2)) sn = __ldg(stk + st.qj + 1);
                 }
             }
-            const bool pass = have && (emit_all || (!st.rej && st.o >= req));
-            const uint32_t pmask = __ballot_sync(kFull, pass);
-            if (pmask) {
-                if (count_only) {
-                    local_count += (lane == 0) ? __popc(pmask) : 0;
-                } else {
-                    unsigned long long b0 = 0;
-                    if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)__popc(pmask));
-                    b0 = __shfl_sync(kFull, b0, 0);
-                    if (pass) emit_triple(a, b0 + __popc(pmask & lt_mask), pr_id, ps_id, st.o);
+            if (have) {
+                const Instance& I = table[inst];
+                if (!early || (!st.rej && st.o >= req)) {
+                    const unsigned long long idx = atomicAdd(I.count, 1ull);
+                    if (!(I.flags & VF_COUNT_ONLY))
+                        emit_triple(I.out, I.cap, (I.flags & VF_SELF_JOIN) != 0, idx, pr_id, ps_id, st.o);
                 }
             }
             n_cont -= m;
@@ -685,32 +722,43 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
             for (uint32_t sub = 0; sub < kFlatGrab; ++sub) {
                 const unsigned long long first = ((unsigned long long)u * kFlatGrab + sub) * 32;
                 if (first >= n_pairs) break;  // warp-uniform
-                const unsigned long long e = first + lane;
+                // the chunk's instance (uniform)
+                const uint32_t inst = a.chunk_inst[first / 32];
+                const Instance& I = table[inst];
+                const uint32_t flags = I.flags;
+                const bool emit_all = (flags & VF_EMIT_ALL) != 0, early = !emit_all;
+                const bool self_join = (flags & VF_SELF_JOIN) != 0;
+                const uint32_t s_n_sets = I.s_n_sets, p = I.p, den = I.den;
+                const uint64_t magic = I.magic;
+                const uint4* r_toks4 = I.r_toks4;
+                const uint4* s_toks4 = I.s_toks4;
                 // ---- pass 1
                 bool live = false;
                 uint32_t pr_id = 0, ps_id = 0, nr = 0, ns = 0, req = 0;
                 uint2 dr = make_uint2(0, 0), ds = make_uint2(0, 0);
-                if (e < n_pairs) {
-                    const PairRef pr = a.pairs[e];
-                    ps_id = pr.s;
-                    if (ps_id >= a.S.n_sets) {
-                        atomicOr(&a.ctr->err, ERR_CAND_ID);
-                    } else {
-                        dr = a.rdesc[pr.k];
-                        pr_id = a.probe_ids[pr.k];
-                        ds = a.S.desc[ps_id];
-                        nr = dr.y;
-                        ns = ds.y;
-                        if (!(a.self_join && pr_id == ps_id)) {
-                            req = required_overlap(a, nr, ns);
-                            live = emit_all || (nr + ns > 0 && req <= min(nr, ns));  // length filter
+                {
+                    const PairRef pr = a.pairs[first + lane];
+                    if (pr.k != kNoProbe) {
+                        ps_id = pr.s;
+                        if (ps_id >= s_n_sets) {
+                            atomicOr(&a.ctr->err, ERR_CAND_ID);
+                        } else {
+                            dr = a.rdesc[pr.k];
+                            pr_id = a.rid[pr.k];
+                            ds = I.s_desc[ps_id];
+                            nr = dr.y;
+                            ns = ds.y;
+                            if (!(self_join && pr_id == ps_id)) {
+                                req = required_overlap(p, den, magic, nr, ns);
+                                live = emit_all || (nr + ns > 0 && req <= min(nr, ns));  // length filter
+                            }
                         }
                     }
                 }
                 uint4 r0 = zero4, r1 = zero4, r2 = zero4, s0 = zero4, s1 = zero4, s2 = zero4;
                 if (live) {
-                    const uint4* r4 = a.R.toks4 + dr.x;
-                    const uint4* s4 = a.S.toks4 + ds.x;
+                    const uint4* r4 = r_toks4 + dr.x;
+                    const uint4* s4 = s_toks4 + ds.x;
                     if (nr > 0) r0 = __ldg(r4);
                     if (nr > 4) r1 = __ldg(r4 + 1);
                     if (nr > 8) r2 = __ldg(r4 + 2);
@@ -733,13 +781,11 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
                 const bool pass = live && st.fin && (emit_all || (!st.rej && st.o >= req));
                 const uint32_t pmask = __ballot_sync(kFull, pass);
                 if (pmask) {
-                    if (count_only) {
-                        local_count += (lane == 0) ? __popc(pmask) : 0;
-                    } else {
-                        unsigned long long b0 = 0;
-                        if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)__popc(pmask));
+                    unsigned long long b0 = 0;
+                    if (lane == 0) b0 = atomicAdd(I.count, (unsigned long long)__popc(pmask));
+                    if (!(flags & VF_COUNT_ONLY)) {
                         b0 = __shfl_sync(kFull, b0, 0);
-                        if (pass) emit_triple(a, b0 + __popc(pmask & lt_mask), pr_id, ps_id, st.o);
+                        if (pass) emit_triple(I.out, I.cap, self_join, b0 + __popc(pmask & lt_mask), pr_id, ps_id, st.o);
                     }
                 }
                 // undecided pairs: park them with their merge state
@@ -751,7 +797,7 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
                         ContEntry* ce = cont + n_cont + __popc(kmask & lt_mask);
                         ce->m0 = make_uint4(pr_id, ps_id, dr.x, ds.x);
                         ce->m1 = make_uint4(nr, ns, req, st.o);
-                        ce->m2 = make_uint4(st.qi, st.qj, 0u, 0u);
+                        ce->m2 = make_uint4(st.qi, st.qj, inst, 0u);
                     }
                     n_cont += __popc(kmask);
                     __syncwarp();
@@ -761,14 +807,6 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
         }
         while (n_cont) drain(min(n_cont, 32u));
     }
-    wout.flush(a, lane);
-
-    if (count_only) {
-        unsigned long long v = local_count;
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) v += __shfl_down_sync(kFull, v, off);
-        if (lane == 0 && v) atomicAdd(a.count, v);
-    }
 }
 
 // -------------------------------------------------------------------------
@@ -777,8 +815,8 @@ __global__ void __launch_bounds__(BT) verify_kernel(VerifyArgs a) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static uint64_t item_cap(uint32_t n_probes, uint64_t n_cands, uint32_t per_item) {
-    const uint64_t cap = (uint64_t)n_probes + (n_cands + per_item - 1) / per_item;
+static uint64_t item_cap(uint64_t n_probes, uint64_t n_cands, uint32_t per_item) {
+    const uint64_t cap = n_probes + (n_cands + per_item - 1) / per_item;
     return cap > 0xFFFFFFF0ull ? 0xFFFFFFF0ull : cap;
 }
 
@@ -794,29 +832,62 @@ static void item_sizes(uint64_t n_cands, int num_sms, uint32_t* per_warp_item, u
     *per_block_item = (uint32_t)(b < 1 ? 1 : (b > kBlockItemCands ? kBlockItemCands : b));
 }
 
-size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands, int num_sms) {
+static uint64_t pair_cap(const LaunchShape& sh) { return sh.total_cands + 32ull * sh.n_tiles + 32; }
+
+LaunchShape single_shape(uint32_t n_probes, uint64_t n_cands) {
+    LaunchShape sh;
+    sh.n_inst = 1;
+    sh.n_tiles = (n_probes + 31) / 32;
+    sh.total_probes = n_probes;
+    sh.total_cands = n_cands;
+    return sh;
+}
+
+size_t workspace_bytes(const LaunchShape& sh, int num_sms) {
     uint32_t wc, bc;
-    item_sizes(n_cands, num_sms, &wc, &bc);
-    return align256(sizeof(Counters)) + align256(sizeof(uint2) * ((size_t)n_probes + 1)) +
-           align256(sizeof(PairRef) * ((size_t)n_cands + 1)) +
-           align256(sizeof(WorkItem) * ((size_t)item_cap(n_probes, n_cands, wc) + 1)) +
-           align256(sizeof(WorkItem) * ((size_t)item_cap(n_probes, n_cands, bc) + 1));
+    item_sizes(sh.total_cands, num_sms, &wc, &bc);
+    const uint64_t slots = 32ull * sh.n_tiles + 1, pc = pair_cap(sh);
+    return align256(sizeof(Counters)) + align256(sizeof(Instance) * ((size_t)sh.n_inst + 1)) +
+           align256(sizeof(uint2) * slots) + align256(sizeof(uint32_t) * slots) +
+           align256(sizeof(uint32_t) * (pc / 32 + 1)) + align256(sizeof(PairRef) * pc) +
+           align256(sizeof(WorkItem) * ((size_t)item_cap(sh.total_probes, sh.total_cands, wc) + 1)) +
+           align256(sizeof(WorkItem) * ((size_t)item_cap(sh.total_probes, sh.total_cands, bc) + 1));
+}
+
+size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands, int num_sms) {
+    return workspace_bytes(single_shape(n_probes, n_cands), num_sms);
+}
+
+void bind_workspace(VerifyArgs& a, void* ws, const LaunchShape& sh, int num_sms) {
+    char* p = static_cast<char*>(ws);
+    item_sizes(sh.total_cands, num_sms, &a.warp_item_cands, &a.block_item_cands);
+    const uint64_t slots = 32ull * sh.n_tiles + 1;
+    a.n_inst = sh.n_inst;
+    a.n_tiles = sh.n_tiles;
+    a.total_probes = sh.total_probes;
+    a.total_cands = sh.total_cands;
+    a.ctr = reinterpret_cast<Counters*>(p);
+    p += align256(sizeof(Counters));
+    a.table_out = reinterpret_cast<Instance*>(p);
+    p += align256(sizeof(Instance) * ((size_t)sh.n_inst + 1));
+    a.rdesc = reinterpret_cast<uint2*>(p);
+    p += align256(sizeof(uint2) * slots);
+    a.rid = reinterpret_cast<uint32_t*>(p);
+    p += align256(sizeof(uint32_t) * slots);
+    a.pair_cap = pair_cap(sh);
+    a.chunk_inst = reinterpret_cast<uint32_t*>(p);
+    p += align256(sizeof(uint32_t) * (a.pair_cap / 32 + 1));
+    a.pairs = reinterpret_cast<PairRef*>(p);
+    p += align256(sizeof(PairRef) * a.pair_cap);
+    a.warp_items = reinterpret_cast<WorkItem*>(p);
+    a.warp_item_cap = (uint32_t)item_cap(sh.total_probes, sh.total_cands, a.warp_item_cands);
+    p += align256(sizeof(WorkItem) * ((size_t)a.warp_item_cap + 1));
+    a.block_items = reinterpret_cast<WorkItem*>(p);
+    a.block_item_cap = (uint32_t)item_cap(sh.total_probes, sh.total_cands, a.block_item_cands);
 }
 
 void bind_workspace(VerifyArgs& a, void* ws, uint32_t n_probes, uint64_t n_cands, int num_sms) {
-    char* p = static_cast<char*>(ws);
-    item_sizes(n_cands, num_sms, &a.warp_item_cands, &a.block_item_cands);
-    a.ctr = reinterpret_cast<Counters*>(p);
-    p += align256(sizeof(Counters));
-    a.rdesc = reinterpret_cast<uint2*>(p);
-    p += align256(sizeof(uint2) * ((size_t)n_probes + 1));
-    a.pairs = reinterpret_cast<PairRef*>(p);
-    p += align256(sizeof(PairRef) * ((size_t)n_cands + 1));
-    a.warp_items = reinterpret_cast<WorkItem*>(p);
-    a.warp_item_cap = (uint32_t)item_cap(n_probes, n_cands, a.warp_item_cands);
-    p += align256(sizeof(WorkItem) * ((size_t)a.warp_item_cap + 1));
-    a.block_items = reinterpret_cast<WorkItem*>(p);
-    a.block_item_cap = (uint32_t)item_cap(n_probes, n_cands, a.block_item_cands);
+    bind_workspace(a, ws, single_shape(n_probes, n_cands), num_sms);
 }
 
 template <int BT>
@@ -861,27 +932,34 @@ static cudaError_t launch_bt(const VerifyArgs& a, cudaStream_t st, int num_sms) 
     return cudaGetLastError();
 }
 
+cudaError_t prepare_verify(uint32_t block_threads) {
+    int per_sm = 0;
+    switch (block_threads) {
+        case 128: return resident_ctas<128>(&per_sm);
+        case 512: return resident_ctas<512>(&per_sm);
+        default: return resident_ctas<256>(&per_sm);
+    }
+}
+
 cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uint32_t block_threads,
                           cudaEvent_t* ev) {
     cudaError_t e = cudaMemsetAsync(a.ctr, 0, sizeof(Counters), st);
     if (e != cudaSuccess) return e;
-    if (a.count) {
-        e = cudaMemsetAsync(a.count, 0, sizeof(unsigned long long), st);
-        if (e != cudaSuccess) return e;
-    }
     if (ev) cudaEventRecord(ev[0], st);
-    if (a.n_probes == 0 || a.n_cands == 0) {
+    if (a.n_inst == 0) {
         if (ev) {
             cudaEventRecord(ev[1], st);
             cudaEventRecord(ev[2], st);
         }
         return cudaSuccess;
     }
+    // the plan kernel also runs for empty batches: it clears the instances' counts
     {
         const int threads = 256;
-        uint64_t blocks = (a.n_probes + threads - 1) / threads;
+        uint64_t blocks = ((uint64_t)a.n_tiles * 32 + threads - 1) / threads;
         const uint64_t max_blocks = (uint64_t)num_sms * 8;
         if (blocks > max_blocks) blocks = max_blocks;
+        if (blocks < 1) blocks = 1;
         plan_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -1,0 +1,156 @@
+"""Batched instances: several independent joins verified in one launch.
+
+Each instance of a multi launch (plain and CUDA-graph replays) must return
+exactly what it returns alone, which the other parity tests tie to the
+oracle; the uneven-instance workload is also compared with the oracle's
+AllPairs join directly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+import paper_1812_09141_gb300 as ssj
+from paper_1812_09141_gb300 import _build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    _build.build()
+    h = ssj.ssj_create(0)
+    yield h
+    ssj.ssj_destroy(h)
+
+
+def _dev(b, dev):
+    import torch
+    return (torch.from_numpy(b.probe_ids.astype(np.int32)).to(dev),
+            torch.from_numpy(b.cand_offsets.astype(np.int64)).to(dev),
+            torch.from_numpy(b.cand_ids.astype(np.int32)).to(dev))
+
+
+def _run_multi(ctx, cases, graph_reps=0):
+    """cases: list of (R, S, p, q, Batch, flags).  Returns per-instance sorted triples for the
+    plain launch and for each graph replay."""
+    import torch
+    dev = torch.device("cuda:0")
+    keep, dbs, outs, caps = [], [], [], []
+    for R, S, p, q, b, fl in cases:
+        t = _dev(b, dev)
+        keep.append(t)
+        dbs.append(ssj.DeviceBatch(R, S, p, q, *t, b.n_cands, flags=fl, n_probes=b.n_probes))
+        cap = max(b.n_cands, 1)
+        outs.append(torch.zeros(3 * cap, dtype=torch.int32, device=dev))
+        caps.append(cap)
+    counts = torch.zeros(len(cases), dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    m = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
+    results = []
+    try:
+        for rep in range(1 + graph_reps):
+            for o in outs:
+                o.zero_()
+            torch.cuda.synchronize()
+            if rep == 0:
+                ssj.ssj_multi_launch(ctx, m)
+            else:
+                ssj.ssj_multi_graph_launch(ctx, m)
+            assert ssj.ssj_device_error(ctx) == 0
+            n = counts.cpu().numpy()
+            res = []
+            for i, o in enumerate(outs):
+                if cases[i][5] & ssj.SSJ_COUNT_ONLY:
+                    res.append(int(n[i]))
+                else:
+                    tr = o[:3 * int(n[i])].view(-1, 3).cpu().numpy().astype(np.uint32)
+                    res.append(oracle.sort_triples(tr))
+            results.append(res)
+    finally:
+        ssj.ssj_multi_destroy(ctx, m)
+    return results
+
+
+def _alone(ctx, R, S, p, q, b, fl):
+    if fl & ssj.SSJ_COUNT_ONLY:
+        return ssj.ssj_verify_batch(ctx, R, S, p, q, b.probe_ids, b.cand_offsets, b.cand_ids, flags=fl)
+    return ssj.triples_to_array(ssj.ssj_verify_batch(ctx, R, S, p, q, b.probe_ids, b.cand_offsets, b.cand_ids,
+                                                     flags=fl))
+
+
+def test_multi_mixed_instances_equal_their_single_launches(ctx):
+    spec = synth.tiny_self_join(n=600)
+    spec.plant_frac, spec.plant_edits = 0.2, 2
+    c_tiny = synth.collection(spec)
+    c_short = synth.collection(synth.short_sets(n=15_000))
+    spec_l = synth.long_sets(n=600)
+    spec_l.plant_frac, spec_l.plant_edits = 0.3, 10
+    c_long = synth.collection(spec_l)
+    cR = synth.collection(synth.tiny_self_join(seed=7, n=300))
+    h_tiny, h_short, h_long, hR = (ssj.ssj_load_collection(ctx, c.offsets, c.tokens)
+                                   for c in (c_tiny, c_short, c_long, cR))
+    fb = lambda c, p, q: synth.Batch(*ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=4))
+    empty = synth.Batch(np.zeros(0, np.uint32), np.zeros(1, np.uint64), np.zeros(0, np.uint32))
+    cases = [
+        (h_tiny, h_tiny, 1, 2, synth.all_pairs_batch(c_tiny.n), 0),
+        (h_short, h_short, 3, 5, fb(c_short, 3, 5), 0),
+        (h_short, h_short, 9, 10, fb(c_short, 9, 10), 0),
+        (h_long, h_long, 3, 5, fb(c_long, 3, 5), 0),
+        (h_tiny, h_tiny, 4, 5, synth.all_pairs_batch(c_tiny.n), ssj.SSJ_FORCE_WARP),
+        (h_long, h_long, 4, 5, fb(c_long, 4, 5), ssj.SSJ_FORCE_BLOCK),
+        (h_tiny, h_tiny, 1, 3, synth.all_pairs_batch(c_tiny.n), ssj.SSJ_COUNT_ONLY),
+        (h_tiny, h_tiny, 1, 2, empty, 0),
+        (hR, h_tiny, 1, 3, synth.random_batch(3, cR.n, c_tiny.n, 500, 30), 0),
+        (h_short, h_short, 7, 10, fb(c_short, 7, 10), ssj.SSJ_EMIT_ALL),
+    ]
+    want = [_alone(ctx, *cs) for cs in cases]
+    for res in _run_multi(ctx, cases, graph_reps=2):
+        for i, (got, w) in enumerate(zip(res, want)):
+            if isinstance(w, int):
+                assert got == w, i
+            else:
+                assert np.array_equal(got, w), (i, len(got), len(w))
+    for h in (h_tiny, h_short, h_long, hR):
+        ssj.ssj_unload_collection(ctx, h)
+
+
+def test_uneven_instances_scaled_match_oracle(ctx):
+    """Sixteen uneven self-join instances (sizes, skews and thresholds drawn as in the batched
+    workload, scaled down) in one launch, each against the oracle's AllPairs join."""
+    specs = synth.uneven_instances(count=16, n_lo=200, n_hi=3000, mean_lo=5, mean_hi=150)
+    cases, wants, handles = [], [], []
+    for ins in specs:
+        ins.coll.plant_frac, ins.coll.plant_edits = 0.1, 1
+        c = synth.collection(ins.coll)
+        h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens, ssj.SSJ_RENUMBER_BY_FREQ)
+        handles.append(h)
+        b = synth.Batch(*ssj.feeder_all(c.offsets, c.tokens, ins.p, ins.q, n_threads=4))
+        cases.append((h, h, ins.p, ins.q, b, 0))
+        wants.append(oracle.sort_triples(oracle.allpairs_self(c.offsets, c.tokens, ins.p, ins.q)[0]))
+    res = _run_multi(ctx, cases, graph_reps=1)
+    for r in res:
+        for i, (got, w) in enumerate(zip(r, wants)):
+            assert np.array_equal(got, w), (i, len(got), len(w))
+    assert sum(len(w) for w in wants) > 0
+    for h in handles:
+        ssj.ssj_unload_collection(ctx, h)
+
+
+def test_multi_keeps_collections_loaded(ctx):
+    import torch
+    c = synth.collection(synth.tiny_self_join(n=100))
+    h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens)
+    b = synth.all_pairs_batch(c.n)
+    t = _dev(b, torch.device("cuda:0"))
+    out = torch.zeros(3 * b.n_cands, dtype=torch.int32, device="cuda:0")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda:0")
+    m = ssj.ssj_multi_create(ctx, [ssj.DeviceBatch(h, h, 1, 2, *t, b.n_cands)], [out], [b.n_cands], cnt)
+    with pytest.raises(ssj.SsjError) as ei:
+        ssj.ssj_unload_collection(ctx, h)
+    assert ei.value.status == ssj.SSJ_EBUSY
+    ssj.ssj_multi_destroy(ctx, m)
+    ssj.ssj_unload_collection(ctx, h)
