@@ -347,6 +347,85 @@ def run_ours(args, rank, world, local_rank):
     return result, colls, batches
 
 
+def run_serving(args):
+    """Continuous batching on a resident 1M-set collection: closed-loop peak, then open-loop
+    Poisson arrivals at 0.5x and 0.9x of that peak, for two device-memory budgets; and the
+    filter/verify co-process (Section 3.2) with chunks handed over as the CPU filter makes them."""
+    import torch
+    import synth
+    import paper_1812_09141_gb300 as ssj
+    from paper_1812_09141_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    c = synth.collection(synth.serving_collection())
+    ts = [(7, 10), (4, 5), (9, 10)]
+    threads = max(1, min(16, os.cpu_count() or 1))
+    pools = []
+    for p, q in ts:
+        pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=threads)
+        pools.append((p, q, pr, co.astype(np.int64), ci))
+    rng = np.random.default_rng(2024)
+    n_req = args.requests
+
+    def make_requests(arrivals, h):
+        reqs, sizes = [], []
+        for i in range(n_req):
+            p, q, pr, co, ci = pools[int(rng.integers(0, len(pools)))]
+            want = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e7)))))
+            want = min(want, int(co[-1]))
+            a = int(rng.integers(0, len(pr)))
+            # probes a .. b-1 with about `want` candidates (wrapping is avoided by moving a back)
+            target = co[a] + want
+            b = int(np.searchsorted(co, target, side="left"))
+            if b > len(pr):
+                b = len(pr)
+                a = int(np.searchsorted(co, co[-1] - want, side="right")) - 1
+                a = max(a, 0)
+            b = max(b, a + 1)
+            offs = (co[a:b + 1] - co[a]).astype(np.uint64)
+            cands = ci[int(co[a]):int(co[b])]
+            reqs.append((h, h, p, q, pr[a:b], offs, cands, float(arrivals[i]), 0))
+            sizes.append(len(cands))
+        return reqs, np.array(sizes)
+
+    out = {"workload": "serving", "collection": "1M sets, lognormal(12, 0.6) clip [2,200], Zipf(1.0) over 2e6",
+           "requests": n_req, "request_sizes": "log-uniform [1e3, 1e7] pairs, slices of the CPU filter's "
+           "candidates at t in {0.7, 0.8, 0.9}", "runs": []}
+    for budget_gb in (4, 1):
+        ctx = ssj.ssj_create(0, mem_budget_bytes=budget_gb << 30, max_inflight=8)
+        try:
+            h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
+            # warm-up and closed-loop peak
+            reqs, sizes = make_requests(np.zeros(n_req), h)
+            ssj.ssj_serve_replay(ctx, reqs[:50])
+            lat, st = ssj.ssj_serve_replay(ctx, reqs)
+            peak = st["pairs"] / st["wall_s"]
+            run = {"budget_gib": budget_gb, "closed_loop": {"pairs_per_s": peak, "p50_ms": 1e3 * np.percentile(lat, 50),
+                                                             "p99_ms": 1e3 * np.percentile(lat, 99),
+                                                             "max_inflight": st["max_inflight"]}}
+            mean_size = float(sizes.mean())
+            for load in (0.5, 0.9):
+                rate = load * peak / mean_size          # requests per second
+                arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+                reqs, sizes2 = make_requests(arrivals, h)
+                lat, st = ssj.ssj_serve_replay(ctx, reqs)
+                run[f"open_loop_{load}"] = {"offered_pairs_per_s": load * peak,
+                                            "achieved_pairs_per_s": st["pairs"] / st["wall_s"],
+                                            "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                                            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                                            "p50_ms_small": 1e3 * float(np.percentile(lat[sizes2 < 1e5], 50)),
+                                            "p99_ms_large": 1e3 * float(np.percentile(lat[sizes2 >= 1e6], 99)),
+                                            "max_inflight": st["max_inflight"], "eagain": st["eagain"]}
+            if budget_gb == 4:
+                cp = ssj.ssj_serve_coprocess(ctx, h, c.offsets, c.tokens, 7, 10, threads, 1 << 20)
+                run["coprocess_t0.7"] = dict(cp, chunk_cands=1 << 20, filter_threads=threads)
+            out["runs"].append(run)
+        finally:
+            ssj.ssj_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,6 +438,7 @@ def main():
                     help="bytes written between timed steps to evict L2 (0 disables; only for profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--out-cap", type=int, default=1 << 26, help="most result triples kept per instance")
+    ap.add_argument("--requests", type=int, default=1000, help="requests of the serving workload")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
@@ -366,6 +446,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "serving" and args.impl == "ours":
+        if rank == 0:
+            run_serving(args)
+        return
 
     if args.impl == "reference":
         if rank != 0:

@@ -59,6 +59,20 @@ class ssj_batch(ctypes.Structure):
                 ("cand_ids", ctypes.c_void_p), ("n_cands", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
 
 
+class ssj_request(ctypes.Structure):
+    _fields_ = [("batch", ssj_batch), ("arrival_s", ctypes.c_double)]
+
+
+class ssj_serve_stats(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("pairs", ctypes.c_uint64), ("results", ctypes.c_uint64),
+                ("eagain", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32)]
+
+
+class ssj_coprocess_stats(ctypes.Structure):
+    _fields_ = [("filter_only_s", ctypes.c_double), ("join_s", ctypes.c_double), ("gpu_busy_s", ctypes.c_double),
+                ("candidates", ctypes.c_uint64), ("results", ctypes.c_uint64), ("chunks", ctypes.c_uint32)]
+
+
 class ssj_triple(ctypes.Structure):
     _fields_ = [("r", ctypes.c_uint32), ("s", ctypes.c_uint32), ("overlap", ctypes.c_uint32)]
 
@@ -87,6 +101,8 @@ SIGNATURES = {
     "ssj_results": (_INT, [_VP, _U64, _VP, _U64, _P(_U64)]),
     "ssj_set_granularity": (_INT, [_VP, _U32, _U32, _U32]),
     "ssj_profile_read": (_INT, [_VP, _P(_U32), _P(ctypes.c_double), _P(ctypes.c_double)]),
+    "ssj_serve_replay": (_INT, [_VP, _P(ssj_request), _U32, _P(ctypes.c_double), _P(ssj_serve_stats)]),
+    "ssj_serve_coprocess": (_INT, [_VP, _U32, _VP, _VP, _U32, _U32, _U32, _U32, _U64, _P(ssj_coprocess_stats)]),
     "ssj_feeder_create": (_INT, [_VP, _VP, _U32, _U32, _U32, _U32, _P(_VP)]),
     "ssj_feeder_next": (_INT, [_VP, _U32, _U64, _VP, _VP, _VP, _P(_U32), _P(_U64), _P(_INT)]),
     "ssj_feeder_progress": (_INT, [_VP, _P(_U64), _P(_U32), _P(_U32)]),
@@ -339,6 +355,38 @@ def ssj_profile_read(ctx: int) -> tuple[int, float, float]:
     n, a, b = ctypes.c_uint32(), ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().ssj_profile_read(ctx, ctypes.byref(n), ctypes.byref(a), ctypes.byref(b)))
     return n.value, a.value, b.value
+
+
+# serving drivers -------------------------------------------------------------
+
+def ssj_serve_replay(ctx: int, requests: list) -> tuple[np.ndarray, dict]:
+    """Open-loop replay.  requests: list of (R, S, p, q, probe_ids, cand_offsets, cand_ids,
+    arrival_s, flags) with host arrays.  Returns (latency_s per request, stats dict)."""
+    n = len(requests)
+    arr = (ssj_request * max(n, 1))()
+    keep = []
+    for i, (R, S, p, q, pr, co, ci, t, fl) in enumerate(requests):
+        hb = _make_batch(R, S, p, q, pr, co, ci, fl)
+        keep.append(hb)
+        arr[i].batch = hb.batch
+        arr[i].arrival_s = float(t)
+    lat = np.zeros(max(n, 1), dtype=np.float64)
+    st = ssj_serve_stats()
+    _check(ctx, lib().ssj_serve_replay(ctx, arr, n, lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       ctypes.byref(st)))
+    return lat[:n], {"wall_s": st.wall_s, "pairs": st.pairs, "results": st.results, "eagain": st.eagain,
+                     "max_inflight": st.max_inflight}
+
+
+def ssj_serve_coprocess(ctx: int, coll: int, offsets, tokens, p: int, q: int, n_threads: int,
+                        chunk_cands: int) -> dict:
+    offs, po = _host(offsets, np.uint64)
+    toks, pt = _host(tokens, np.uint32)
+    st = ssj_coprocess_stats()
+    _check(ctx, lib().ssj_serve_coprocess(ctx, coll, po, pt, len(offs) - 1, p, q, n_threads, chunk_cands,
+                                          ctypes.byref(st)))
+    return {"filter_only_s": st.filter_only_s, "join_s": st.join_s, "gpu_busy_s": st.gpu_busy_s,
+            "candidates": st.candidates, "results": st.results, "chunks": st.chunks}
 
 
 # feeder --------------------------------------------------------------------
