@@ -24,6 +24,8 @@ cpu_baseline / --impl reference  the CPU oracle as it stands, on host cores.
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
+import ctypes
 import hashlib
 import json
 import math
@@ -103,10 +105,12 @@ def oracle_accounting(colls, batches):
     12 B per probe (id + offset), 4 B per candidate id, 8 B per touched set
     descriptor (probe and candidate), 4 B per token the merge must read (the
     probe's tokens once per probe, the candidate's up to the stop point), 12 B
-    per result triple and 8 B for the count."""
+    per result triple and 8 B for the count.  Batches are accounted on several
+    host threads (the C oracle releases the GIL)."""
     import oracle
-    acc = []
-    for k, p, q, pr, co, ci in batches:
+
+    def one(b):
+        k, p, q, pr, co, ci = b
         c = colls[k]
         tr, cr, cs = oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci,
                                          consumed=True)
@@ -118,18 +122,33 @@ def oracle_accounting(colls, batches):
             pr_max[nz] = np.maximum.reduceat(cr.astype(np.int64), starts)
         a = (12 * len(pr) + 4 * len(ci) + 8 * (len(pr) + len(ci)) + 4 * int(pr_max.sum())
              + 4 * int(cs.astype(np.int64).sum()) + 12 * len(tr) + 8)
-        acc.append({"bytes": int(a), "survivors": int(len(tr)), "pairs": int(len(ci))})
-    return acc
+        # the part that comes from HBM even with the collection resident in L2:
+        # the candidate stream and the output
+        a_hbm = 12 * len(pr) + 4 * len(ci) + 12 * len(tr) + 8
+        return {"bytes": int(a), "hbm_bytes": int(a_hbm), "survivors": int(len(tr)), "pairs": int(len(ci))}
+
+    with cf.ThreadPoolExecutor(max(1, min(len(batches), os.cpu_count() or 1))) as ex:
+        return list(ex.map(one, batches))
 
 
-def cpu_baseline(colls, batches, min_seconds=10.0, max_seconds=30.0):
+def cpu_baseline(colls, batches, min_seconds=10.0, max_seconds=30.0, max_call_pairs=8_000_000):
     """The oracle (single-threaded C) timed on the host over the workload's batches, in order,
-    for at least min_seconds (whole steps while they fit, else a prefix of one step)."""
+    for at least min_seconds: whole batches while they are small, else probe-prefix slices of
+    at most max_call_pairs candidates taken from each batch in turn, so the sample stays
+    bounded and covers every instance."""
     import oracle
     pairs_step = sum(len(b[5]) for b in batches)
+    calls = []
+    for k, p, q, pr, co, ci in batches:
+        co = co.astype(np.int64)
+        if co[-1] <= max_call_pairs:
+            calls.append((k, p, q, pr, co.astype(np.uint64), ci))
+        else:
+            b = max(1, int(np.searchsorted(co, max_call_pairs, side="right")) - 1)
+            calls.append((k, p, q, pr[:b], co[:b + 1].astype(np.uint64), ci[:int(co[b])]))
     pairs, total_t, reps = 0, 0.0, 0
     while total_t < min_seconds and reps < 1000:
-        for k, p, q, pr, co, ci in batches:
+        for k, p, q, pr, co, ci in calls:
             c = colls[k]
             t0 = time.perf_counter()
             oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci)
@@ -140,9 +159,53 @@ def cpu_baseline(colls, batches, min_seconds=10.0, max_seconds=30.0):
         reps += 1
         if total_t > max_seconds:
             break
+    whole = all(len(c[5]) == len(b[5]) for c, b in zip(calls, batches))
+    what = (f"{pairs / max(pairs_step, 1):.2f} steps of {pairs_step}" if whole else
+            f"probe-prefix slices of <= {max_call_pairs} candidates of each of the {len(batches)} batches")
     return {"value": pairs / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{pairs} candidate pairs of the workload ({pairs / max(pairs_step, 1):.2f} steps of "
-                      f"{pairs_step}), {total_t:.1f} s of single-threaded CPU work"}
+            "sample": f"{pairs} candidate pairs of the workload ({what}), {total_t:.1f} s of single-threaded CPU work"}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def cpu_baseline_threads(colls, batches, min_seconds=5.0):
+    """The same oracle calls over all host cores: each batch split into contiguous probe ranges
+    of about equal candidate counts, one range per thread (the C oracle releases the GIL)."""
+    import oracle
+    n_thr = os.cpu_count() or 1
+    jobs = []
+    for k, p, q, pr, co, ci in batches:
+        co = co.astype(np.int64)
+        bounds = np.searchsorted(co, np.linspace(0, co[-1], n_thr + 1), side="left")
+        bounds[0], bounds[-1] = 0, len(pr)
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            if b > a:
+                jobs.append((k, p, q, pr[a:b], (co[a:b + 1] - co[a]).astype(np.uint64), ci[co[a]:co[b]]))
+    pairs_step = sum(len(b[5]) for b in batches)
+
+    def run(job):
+        k, p, q, pr, co, ci = job
+        c = colls[k]
+        oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci)
+
+    steps, t = 0, 0.0
+    with cf.ThreadPoolExecutor(n_thr) as ex:
+        while t < min_seconds and steps < 1000:
+            t0 = time.perf_counter()
+            list(ex.map(run, jobs))
+            t += time.perf_counter() - t0
+            steps += 1
+    return {"value": pairs_step * steps / t, "unit": UNIT, "cores": n_thr, "kind": "oracle",
+            "sample": f"{steps} full steps ({pairs_step} pairs each) split into probe ranges over {n_thr} threads"}
 
 
 # --------------------------------------------------------------------------- measurement helpers
@@ -260,6 +323,10 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(max(args.l2_flush_mb << 18, 1), dtype=torch.int32, device=dev)
     torch.cuda.synchronize(dev)
     multi = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
+    # granularity and block size chosen by the library's autotuner on this launch (untimed)
+    tune = ssj.ssj_multi_autotune(ctx, multi, stream.cuda_stream, reps=5)
+    ssj.ssj_set_granularity(ctx, tune["thread_max_key"], tune["lane_max_key"], min(tune["warp_max_key"], 1 << 30),
+                            tune["block_threads"])
 
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -310,6 +377,46 @@ def run_ours(args, rank, world, local_rank):
     if [int(x) for x in counts.cpu().tolist()] != result_counts:
         raise RuntimeError("graph replay returned different counts")
 
+    # warm L2: the same batched launch with nothing evicted in between
+    warm = []
+    with torch.cuda.stream(stream):
+        for _ in range(min(args.steps, 20)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ssj.ssj_multi_launch(ctx, multi, stream.cuda_stream)
+            e1.record(stream)
+            warm.append((e0, e1))
+        stream.synchronize()
+    warm_ms = [a.elapsed_time(b) for a, b in warm]
+
+    # the plain per-batch path: one stream-ordered call (plan + verify) per instance
+    ssj.ssj_reserve(ctx, max(len(b[3]) for b in batches), max(len(b[5]) for b in batches))
+    pcounts = torch.zeros(len(batches), dtype=torch.int64, device=dev)
+    lib = ssj.lib()
+    calls = [(ctypes.byref(db.batch), o.data_ptr(), cap, pcounts.data_ptr() + 8 * i)
+             for i, (db, o, cap) in enumerate(zip(dbs, outs, caps))]
+    plain = []
+    with torch.cuda.stream(stream):
+        for _ in range(min(args.steps, 20)):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for bp, op, cap, cp in calls:
+                st = lib.ssj_verify_batch_async(ctx, bp, op, cap, cp, stream.cuda_stream)
+                if st != ssj.SSJ_OK:
+                    raise RuntimeError(ssj.ssj_last_error(ctx))
+            e1.record(stream)
+            plain.append((e0, e1))
+        stream.synchronize()
+    plain_ms = [a.elapsed_time(b) for a, b in plain]
+    if [int(x) for x in pcounts.cpu().tolist()] != result_counts:
+        raise RuntimeError("per-batch calls returned different counts")
+    ssj.ssj_profile_read(ctx)  # drop their profile records
+
+    # read-bandwidth probes: L2-resident buffer and a buffer far above L2
+    l2_gbs = ssj.ssj_read_bandwidth(ctx, 32 << 20, 200)
+    hbm_read_gbs = ssj.ssj_read_bandwidth(ctx, 4 << 30, 5)
+
     # ---------------- end to end through the public synchronous call, host buffers
     pinned = []
     for ci, p, q, pr, co, cands in batches:
@@ -343,7 +450,8 @@ def run_ours(args, rank, world, local_rank):
     result = {"total_ms": total_ms, "step_ms": step_ms, "verify_ms": verify_ms, "plan_ms": plan_ms,
               "launches": launches, "counts": result_counts, "pairs_step": pairs_step, "graph_ms": graph_ms,
               "e2e_value": pairs_step * e2e_steps / e2e_t * world if e2e_t > 0 else None, "h2d": h2d, "d2h": d2h,
-              "clocks": clocks.summary(), "cfg": cfg}
+              "clocks": clocks.summary(), "cfg": cfg, "tune": tune, "warm_ms": warm_ms, "plain_ms": plain_ms,
+              "l2_gbs": l2_gbs, "hbm_read_gbs": hbm_read_gbs}
     return result, colls, batches
 
 
@@ -362,14 +470,19 @@ def run_serving(args):
     ts = [(7, 10), (4, 5), (9, 10)]
     threads = max(1, min(16, os.cpu_count() or 1))
     pools = []
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t.numpy()
+
+    # request inputs sit in pinned host memory, as a server's receive buffers would
     for p, q in ts:
         pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=threads)
-        pools.append((p, q, pr, co.astype(np.int64), ci))
+        pools.append((p, q, pinned(pr), co.astype(np.int64), pinned(ci)))
     rng = np.random.default_rng(2024)
     n_req = args.requests
 
     def make_requests(arrivals, h):
-        reqs, sizes = [], []
+        picks = []
         for i in range(n_req):
             p, q, pr, co, ci = pools[int(rng.integers(0, len(pools)))]
             want = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e7)))))
@@ -383,7 +496,13 @@ def run_serving(args):
                 a = int(np.searchsorted(co, co[-1] - want, side="right")) - 1
                 a = max(a, 0)
             b = max(b, a + 1)
-            offs = (co[a:b + 1] - co[a]).astype(np.uint64)
+            picks.append((p, q, pr, co, ci, a, b))
+        arena = pinned(np.zeros(sum(b - a + 1 for *_, a, b in picks), dtype=np.uint64))
+        reqs, sizes, at = [], [], 0
+        for i, (p, q, pr, co, ci, a, b) in enumerate(picks):
+            offs = arena[at:at + b - a + 1]
+            at += b - a + 1
+            offs[:] = co[a:b + 1] - co[a]
             cands = ci[int(co[a]):int(co[b])]
             reqs.append((h, h, p, q, pr[a:b], offs, cands, float(arrivals[i]), 0))
             sizes.append(len(cands))
@@ -391,7 +510,7 @@ def run_serving(args):
 
     out = {"workload": "serving", "collection": "1M sets, lognormal(12, 0.6) clip [2,200], Zipf(1.0) over 2e6",
            "requests": n_req, "request_sizes": "log-uniform [1e3, 1e7] pairs, slices of the CPU filter's "
-           "candidates at t in {0.7, 0.8, 0.9}", "runs": []}
+           "candidates at t in {0.7, 0.8, 0.9}, in pinned host memory", "runs": []}
     for budget_gb in (4, 1):
         ctx = ssj.ssj_create(0, mem_budget_bytes=budget_gb << 30, max_inflight=8)
         try:
@@ -488,21 +607,32 @@ def main():
         return
     pairs_step = res["pairs_step"]
     total_s = res["total_ms"] / 1e3
+    input_bytes = (sum(4 * len(c.tokens) + 8 * c.n for c in colls)
+                   + sum(4 * len(b[3]) + 8 * len(b[4]) + 4 * len(b[5]) for b in batches))
     value = pairs_step * args.steps * world / total_s
     peak, peak_kind = measured_hbm_peak()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict(res["cfg"], pairs_per_step=pairs_step, instances_per_launch=len(batches),
-                           l2=(f"flushed before every timed step ({args.l2_flush_mb} MiB write); inputs fit in L2"
+                           l2=(f"flushed before every timed step ({args.l2_flush_mb} MiB write)"
                                if args.l2_flush_mb else "not flushed (profiling run)"),
-                           parallelism=f"replicas x{world}" if world > 1 else "single GPU")}
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                           device_input_bytes=int(input_bytes), inputs_fit_l2=bool(input_bytes < 129e6))}
     sm = sorted(res["step_ms"])
     line["latency_ms"] = {"p50": float(np.percentile(sm, 50)), "p99": float(np.percentile(sm, 99)),
                           "per": "one batched launch (every instance of the step), device time"}
     gm = res["graph_ms"]
     line["graph_replay_ms_per_step"] = float(np.median(gm)) if gm else None
     line["gpu_launches"] = 2 * res["launches"]
+    line["config"]["granularity"] = dict(res["tune"], chosen_by="ssj_multi_autotune (median of 5 launches per setting)")
+    wm = sorted(res["warm_ms"])
+    line["warm_l2"] = {"pairs_per_s": pairs_step / (np.median(wm) / 1e3), "p50_ms": float(np.percentile(wm, 50)),
+                       "p99_ms": float(np.percentile(wm, 99)), "runs": len(wm)}
+    pm = sorted(res["plain_ms"])
+    line["plain_per_batch"] = {"pairs_per_s": pairs_step / (np.median(pm) / 1e3), "p50_ms": float(np.percentile(pm, 50)),
+                               "p99_ms": float(np.percentile(pm, 99)), "runs": len(pm),
+                               "call": "ssj_verify_batch_async per instance (plan + verify each), L2 flushed"}
     line["kernel_ms_per_step"] = {"verify": res["verify_ms"] / args.steps, "plan": res["plan_ms"] / args.steps}
     line["survivors_per_step"] = sum(res["counts"])
     line["e2e"] = {"value": res["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
@@ -523,7 +653,19 @@ def main():
                             "kernel": "verify_kernel", "peak_source": f"{peak_kind} copy bandwidth",
                             "algorithmic_bytes_per_launch": bytes_step}
         line["gbs_vs_hbm_peak"] = {"achieved_gbs": achieved, "frac": achieved / peak}
+        hbm_step = sum(a["hbm_bytes"] for a in acc)
+        l2 = res["l2_gbs"]
+        bound_s = max(hbm_step / (peak * 1e9), bytes_step / (l2 * 1e9))
+        warm_verify_s = np.median(res["warm_ms"]) / 1e3
+        line["l2_aware_roofline"] = {
+            "l2_read_gbs": l2, "hbm_read_gbs_probe": res["hbm_read_gbs"], "hbm_peak_gbs": peak,
+            "A_min": bytes_step, "A_hbm": hbm_step,
+            "frac_cold": bound_s / verify_s_step, "frac_warm_step": bound_s / warm_verify_s,
+            "formula": "max(A_hbm/BW_hbm, A_min/BW_l2) / t; t = verify kernel time (cold: L2 flushed before "
+                       "the step) or whole warm step; BW_l2 from ssj_read_bandwidth over a 32 MiB buffer"}
         line["cpu_baseline"] = cpu_baseline(colls, batches)
+        line["cpu_baseline"]["cpu_model"] = cpu_model()
+        line["cpu_baseline_all_cores"] = cpu_baseline_threads(colls, batches)
     print(json.dumps(line), flush=True)
 
 

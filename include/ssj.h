@@ -139,6 +139,9 @@ ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, ui
 #define SSJ_FORCE_THREAD 0x10u  /* verify every pair with one thread (Alternative A/B style) */
 #define SSJ_FORCE_WARP 0x20u    /* verify every pair with one warp (merge path over 32 lanes) */
 #define SSJ_FORCE_BLOCK 0x40u   /* verify every pair with one thread block (Alternative C) */
+#define SSJ_FORCE_LANE 0x80u    /* verify every pair with one lane, the probe set held in the
+                                   warp's shared memory (Alternative B); probes longer than
+                                   1,020 tokens go to the warp path */
 
 typedef struct {
     ssj_coll R, S;                /* R == S: self-join */
@@ -251,6 +254,30 @@ ssj_status ssj_multi_graph_launch(ssj_ctx* ctx, ssj_multi* m, void* stream);
 /* Free a prepared launch (waits for its work). NULL is ignored. */
 void ssj_multi_destroy(ssj_ctx* ctx, ssj_multi* m);
 
+typedef struct {
+    uint32_t thread_max_key;  /* chosen bins (see ssj_set_granularity); 0xFFFFFFFF */
+    uint32_t lane_max_key;    /*   for warp_max_key sends no probe to the block bin, */
+    uint32_t warp_max_key;    /*   lane_max_key <= thread_max_key means no lane bin */
+    uint32_t block_threads;   /* chosen block size (the block path's window is 8 steps per thread) */
+    uint32_t settings_tried;  /* distinct settings timed */
+    float best_ms;            /* median device time of one launch with the chosen setting */
+    float initial_ms;         /* the same for the setting m had before the call */
+} ssj_tune_result;
+
+/*
+ * Autotune the granularity of a prepared launch on its own inputs: time
+ * (CUDA events on `stream`, NULL: the context's stream; median of reps >= 3
+ * launches after one untimed launch each) settings of the thread, lane and
+ * warp bins' upper keys and of the block size, by coordinate descent
+ * from m's current setting, and keep the fastest in m (later launches, and
+ * graphs captured later, use it).  Every setting computes the same results
+ * (Section 3.3.2 Alternatives A-C differ in speed only, Section 5.4); the
+ * outputs and counts of m hold those of the last timed launch.  Synchronises
+ * the stream.  Errors: SSJ_EINVAL, SSJ_EDEVICE (a launch failed or the
+ * device-side batch checks fired).
+ */
+ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* stream, uint32_t reps, ssj_tune_result* out);
+
 /* Size the workspace for batches of up to n_probes probes and n_cands
  * candidates (device allocation happens here, not in later calls). */
 ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands);
@@ -306,14 +333,28 @@ ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double* plan_ms, d
 
 /* Granularity bins keyed by |r|+|s| (estimated per probe as 2|r|, since the
  * length filter keeps |s| within [t|r|, |r|/t]): a probe whose key is <=
- * thread_max_key is verified one pair per thread, <= warp_max_key one pair
- * per warp, otherwise one pair per thread block (the rule of Section 5.4:
- * per-thread work for small sets, cooperative Intersect Path for large
- * ones).  Defaults 128 and 2048; thread_max_key is capped at 1024.
+ * thread_max_key is verified one pair per thread; <= lane_max_key, with
+ * |r| <= 1,020 and at least 16 candidates, one pair per lane with r held in
+ * the warp's shared memory (Alternative B of Section 3.3.2); <= warp_max_key
+ * one pair per warp; otherwise one pair per thread block (the rule of
+ * Section 5.4: per-thread work for small sets, cooperative Intersect Path
+ * for large ones).  Defaults 128, 2048, 2048; any values are valid (every
+ * granularity verifies pairs of any length), they change the speed only;
+ * lane_max_key <= thread_max_key leaves the lane bin empty.
  * block_threads is 128, 256 or 512 (default 256).  Zero leaves a value
  * unchanged. */
-ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t warp_max_key,
+ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t lane_max_key, uint32_t warp_max_key,
                                uint32_t block_threads);
+
+/* Measurement aid (the paper has no counterpart): device read bandwidth in
+ * GB/s (1e9 bytes/s), streaming a zero-filled device buffer of `bytes`
+ * (rounded down to a multiple of 16; allocated and freed here) `passes` times
+ * in one kernel launch with 128-bit loads cached in L2 only, after one
+ * warm-up pass, timed with CUDA events on the context's stream.  A buffer well below the L2 size
+ * gives the L2 read rate that bounds token reads from a resident collection
+ * (the L2-aware roofline); one well above it the HBM read rate.
+ * Errors: SSJ_EINVAL, SSJ_ENOMEM, SSJ_EDEVICE. */
+ssj_status ssj_read_bandwidth(ssj_ctx* ctx, uint64_t bytes, uint32_t passes, double* gbs);
 
 #ifdef __cplusplus
 }

@@ -35,6 +35,7 @@ SSJ_EMIT_ALL = 0x8
 SSJ_FORCE_THREAD = 0x10
 SSJ_FORCE_WARP = 0x20
 SSJ_FORCE_BLOCK = 0x40
+SSJ_FORCE_LANE = 0x80
 # context flags
 SSJ_CTX_PROFILE = 0x1
 
@@ -61,6 +62,12 @@ class ssj_batch(ctypes.Structure):
 
 class ssj_request(ctypes.Structure):
     _fields_ = [("batch", ssj_batch), ("arrival_s", ctypes.c_double)]
+
+
+class ssj_tune_result(ctypes.Structure):
+    _fields_ = [("thread_max_key", ctypes.c_uint32), ("lane_max_key", ctypes.c_uint32), ("warp_max_key", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32), ("settings_tried", ctypes.c_uint32),
+                ("best_ms", ctypes.c_float), ("initial_ms", ctypes.c_float)]
 
 
 class ssj_serve_stats(ctypes.Structure):
@@ -95,11 +102,13 @@ SIGNATURES = {
     "ssj_multi_launch": (_INT, [_VP, _VP, _VP]),
     "ssj_multi_graph_launch": (_INT, [_VP, _VP, _VP]),
     "ssj_multi_destroy": (None, [_VP, _VP]),
+    "ssj_multi_autotune": (_INT, [_VP, _VP, _VP, _U32, _P(ssj_tune_result)]),
+    "ssj_read_bandwidth": (_INT, [_VP, _U64, _U32, _P(ctypes.c_double)]),
     "ssj_device_error": (_INT, [_VP, _P(_U32)]),
     "ssj_submit": (_INT, [_VP, _P(ssj_batch), _P(_U64)]),
     "ssj_poll": (_INT, [_VP, _U64, _INT, _P(_INT)]),
     "ssj_results": (_INT, [_VP, _U64, _VP, _U64, _P(_U64)]),
-    "ssj_set_granularity": (_INT, [_VP, _U32, _U32, _U32]),
+    "ssj_set_granularity": (_INT, [_VP, _U32, _U32, _U32, _U32]),
     "ssj_profile_read": (_INT, [_VP, _P(_U32), _P(ctypes.c_double), _P(ctypes.c_double)]),
     "ssj_serve_replay": (_INT, [_VP, _P(ssj_request), _U32, _P(ctypes.c_double), _P(ssj_serve_stats)]),
     "ssj_serve_coprocess": (_INT, [_VP, _U32, _VP, _VP, _U32, _U32, _U32, _U32, _U64, _P(ssj_coprocess_stats)]),
@@ -302,6 +311,22 @@ def ssj_multi_destroy(ctx: int, m: int) -> None:
     lib().ssj_multi_destroy(ctx, m)
 
 
+def ssj_multi_autotune(ctx: int, m: int, stream: int | None = None, reps: int = 5) -> dict:
+    """Tune the granularity of a prepared launch; returns the chosen setting and timings."""
+    r = ssj_tune_result()
+    _check(ctx, lib().ssj_multi_autotune(ctx, m, stream, reps, ctypes.byref(r)))
+    return {"thread_max_key": r.thread_max_key, "lane_max_key": r.lane_max_key, "warp_max_key": r.warp_max_key,
+            "block_threads": r.block_threads, "settings_tried": r.settings_tried,
+            "best_ms": r.best_ms, "initial_ms": r.initial_ms}
+
+
+def ssj_read_bandwidth(ctx: int, nbytes: int, passes: int = 20) -> float:
+    """Device read bandwidth (GB/s) over a buffer of nbytes (see ssj.h)."""
+    g = ctypes.c_double()
+    _check(ctx, lib().ssj_read_bandwidth(ctx, nbytes, passes, ctypes.byref(g)))
+    return g.value
+
+
 def ssj_reserve(ctx: int, n_probes: int, n_cands: int) -> None:
     _check(ctx, lib().ssj_reserve(ctx, n_probes, n_cands))
 
@@ -346,8 +371,9 @@ def ssj_results(ctx: int, ticket: int, count_only: bool = False):
     return res[:n.value]
 
 
-def ssj_set_granularity(ctx: int, thread_max_key: int = 0, warp_max_key: int = 0, block_threads: int = 0) -> None:
-    _check(ctx, lib().ssj_set_granularity(ctx, thread_max_key, warp_max_key, block_threads))
+def ssj_set_granularity(ctx: int, thread_max_key: int = 0, lane_max_key: int = 0, warp_max_key: int = 0,
+                        block_threads: int = 0) -> None:
+    _check(ctx, lib().ssj_set_granularity(ctx, thread_max_key, lane_max_key, warp_max_key, block_threads))
 
 
 def ssj_profile_read(ctx: int) -> tuple[int, float, float]:

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -83,6 +84,7 @@ struct Ticket {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t copied = nullptr;   // host-to-device copies of a submission done
     // pinned staging for host inputs
     uint32_t* h_probe = nullptr;
     uint64_t* h_offs = nullptr;
@@ -107,6 +109,7 @@ struct ssj_ctx {
     uint64_t budget = 0;
     uint32_t max_inflight = 0;
     uint32_t thread_max_key = 128;
+    uint32_t lane_max_key = 2048;
     uint32_t warp_max_key = 2048;
     uint32_t block_threads = 256;
     std::string err;
@@ -239,9 +242,9 @@ ssj_status resolve(ssj_ctx* ctx, const ssj_batch* b, Collection** R, Collection*
     if (b->R != b->S && (ir->second.renumbered || is->second.renumbered))
         return fail(ctx, SSJ_EINVAL, "renumbered collections can only be self-joined");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_EMIT_ALL | SSJ_FORCE_THREAD |
-                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK;
+                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE;
     if (b->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown batch flag");
-    const uint32_t forced = b->flags & (SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK);
+    const uint32_t forced = b->flags & (SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE);
     if (forced & (forced - 1)) return fail(ctx, SSJ_EINVAL, "at most one SSJ_FORCE_* flag");
     *R = &ir->second;
     *S = &is->second;
@@ -255,6 +258,7 @@ uint32_t vflags(uint32_t f) {
     if (f & SSJ_FORCE_THREAD) v |= VF_FORCE_THREAD;
     if (f & SSJ_FORCE_WARP) v |= VF_FORCE_WARP;
     if (f & SSJ_FORCE_BLOCK) v |= VF_FORCE_BLOCK;
+    if (f & SSJ_FORCE_LANE) v |= VF_FORCE_LANE;
     return v;
 }
 
@@ -284,6 +288,7 @@ VerifyArgs make_args(ssj_ctx* ctx, const ssj_batch* b, const Collection& R, cons
     a.single = make_instance(b, R, S, n_cands);
     a.table = nullptr;
     a.thread_max_key = ctx->thread_max_key;
+    a.lane_max_key = ctx->lane_max_key;
     a.warp_max_key = ctx->warp_max_key;
     return a;
 }
@@ -345,6 +350,7 @@ extern "C" ssj_status ssj_create(const ssj_config* config, ssj_ctx** out) {
     for (auto& s : ctx->slots) {
         if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) return SSJ_EDEVICE;
         if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) return SSJ_EDEVICE;
+        if (cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming) != cudaSuccess) return SSJ_EDEVICE;
         if (cudaMallocHost(reinterpret_cast<void**>(&s.h_count), sizeof(uint64_t)) != cudaSuccess) return SSJ_EDEVICE;
         if (cudaMallocHost(reinterpret_cast<void**>(&s.h_err), sizeof(uint32_t)) != cudaSuccess) return SSJ_EDEVICE;
     }
@@ -369,6 +375,7 @@ extern "C" void ssj_destroy(ssj_ctx* ctx) {
         cudaStreamSynchronize(s.stream);
         cudaStreamDestroy(s.stream);
         cudaEventDestroy(s.ev);
+        cudaEventDestroy(s.copied);
         cudaFreeHost(s.h_probe);
         cudaFreeHost(s.h_offs);
         cudaFreeHost(s.h_cand);
@@ -400,12 +407,13 @@ extern "C" const char* ssj_last_error(ssj_ctx* ctx) {
     return ctx->err.c_str();
 }
 
-extern "C" ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t warp_max_key,
-                                          uint32_t block_threads) {
+extern "C" ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t lane_max_key,
+                                          uint32_t warp_max_key, uint32_t block_threads) {
     if (!ctx) return SSJ_EINVAL;
     if (block_threads && block_threads != 128 && block_threads != 256 && block_threads != 512)
         return fail(ctx, SSJ_EINVAL, "block_threads must be 128, 256 or 512");
-    if (thread_max_key) ctx->thread_max_key = std::min(thread_max_key, kThreadKeyCap);
+    if (thread_max_key) ctx->thread_max_key = thread_max_key;
+    if (lane_max_key) ctx->lane_max_key = lane_max_key;
     if (warp_max_key) ctx->warp_max_key = warp_max_key;
     if (block_threads) ctx->block_threads = block_threads;
     return SSJ_OK;
@@ -708,6 +716,40 @@ uint64_t batch_device_bytes(uint32_t n_probes, uint64_t n_cands, bool count_only
     return b;
 }
 
+// True if p lies in page-locked host memory (cudaMallocHost, cudaHostAlloc,
+// cudaHostRegister), which the copy engines read directly.
+bool is_pinned(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+// memcpy of pageable input into pinned staging; a large copy is split over a
+// few threads, since one core's copy rate is well below the host-to-device
+// link's.
+void staged_copy(void* dst, const void* src, size_t bytes) {
+    constexpr size_t kPart = size_t(8) << 20;
+    const size_t hw = std::max(2u, std::thread::hardware_concurrency());
+    const size_t parts = std::min<size_t>(std::min<size_t>(bytes / kPart, 8), hw / 2);
+    if (parts <= 1) {
+        memcpy(dst, src, bytes);
+        return;
+    }
+    const size_t step = ((bytes + parts - 1) / parts + 63) & ~size_t(63);
+    std::vector<std::thread> th;
+    for (size_t i = 1; i < parts; ++i) {
+        const size_t b0 = std::min(bytes, i * step), b1 = std::min(bytes, b0 + step);
+        if (b1 > b0)
+            th.emplace_back([=] { memcpy(static_cast<char*>(dst) + b0, static_cast<const char*>(src) + b0, b1 - b0); });
+    }
+    memcpy(dst, src, std::min(bytes, step));
+    for (auto& t : th) t.join();
+}
+
 void completion_loop(ssj_ctx* ctx, int slot) {
     cudaSetDevice(ctx->device);
     Slot& sl = ctx->slots[slot];
@@ -812,31 +854,52 @@ extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t*
     t->bytes = bytes;
     cudaError_t e = cudaMallocFromPoolAsync(&t->d_mem, bytes, ctx->pool, s);
     if (e != cudaSuccess) return unreserve(fail(ctx, SSJ_ENOMEM, "pool allocation: %s", cudaGetErrorString(e)));
+    bool direct_copy = false;
     char* base = static_cast<char*>(t->d_mem);
     size_t off = 0;
     if (!dev) {
-        // copy host inputs to pinned staging, so the caller may reuse them at once
-        if ((st = ensure_pinned(ctx, &sl.h_probe, &sl.h_probe_cap, std::max<uint64_t>(batch->n_probes, 1))) != SSJ_OK ||
-            (st = ensure_pinned(ctx, &sl.h_offs, &sl.h_offs_cap, batch->n_probes + 1ull)) != SSJ_OK ||
-            (st = ensure_pinned(ctx, &sl.h_cand, &sl.h_cand_cap, std::max<uint64_t>(n_cands, 1))) != SSJ_OK) {
+        // Inputs in pinned memory are copied straight from the caller's arrays,
+        // and the call waits for those copies before it returns; pageable
+        // inputs go through this slot's pinned staging.  Either way the caller
+        // may reuse its arrays once ssj_submit returns.
+        const uint64_t offs_n = batch->n_probes ? batch->n_probes + 1ull : 0;
+        const bool pin_probe = batch->n_probes && is_pinned(batch->probe_ids);
+        const bool pin_offs = offs_n && is_pinned(batch->cand_offsets);
+        const bool pin_cand = n_cands && is_pinned(batch->cand_ids);
+        direct_copy = pin_probe || pin_offs || pin_cand;
+        if ((!pin_probe && (st = ensure_pinned(ctx, &sl.h_probe, &sl.h_probe_cap, std::max<uint64_t>(batch->n_probes, 1))) != SSJ_OK) ||
+            (!pin_offs && (st = ensure_pinned(ctx, &sl.h_offs, &sl.h_offs_cap, batch->n_probes + 1ull)) != SSJ_OK) ||
+            (!pin_cand && (st = ensure_pinned(ctx, &sl.h_cand, &sl.h_cand_cap, std::max<uint64_t>(n_cands, 1))) != SSJ_OK)) {
             cudaFreeAsync(t->d_mem, s);
             return unreserve(st);
         }
-        if (batch->n_probes) {
-            memcpy(sl.h_probe, batch->probe_ids, 4ull * batch->n_probes);
-            memcpy(sl.h_offs, batch->cand_offsets, 8ull * (batch->n_probes + 1));
-        } else {
-            sl.h_offs[0] = 0;
+        const void* src_probe = batch->probe_ids;
+        const void* src_offs = batch->cand_offsets;
+        const void* src_cand = batch->cand_ids;
+        if (batch->n_probes && !pin_probe) {
+            staged_copy(sl.h_probe, batch->probe_ids, 4ull * batch->n_probes);
+            src_probe = sl.h_probe;
         }
-        if (n_cands) memcpy(sl.h_cand, batch->cand_ids, 4ull * n_cands);
+        if (offs_n && !pin_offs) {
+            staged_copy(sl.h_offs, batch->cand_offsets, 8ull * offs_n);
+            src_offs = sl.h_offs;
+        }
+        if (n_cands && !pin_cand) {
+            staged_copy(sl.h_cand, batch->cand_ids, 4ull * n_cands);
+            src_cand = sl.h_cand;
+        }
         uint32_t* d_probe = reinterpret_cast<uint32_t*>(base + off); off += align256(4ull * std::max<uint32_t>(batch->n_probes, 1));
         uint64_t* d_offs = reinterpret_cast<uint64_t*>(base + off);  off += align256(8ull * (batch->n_probes + 1));
         uint32_t* d_cand = reinterpret_cast<uint32_t*>(base + off);  off += align256(4ull * std::max<uint64_t>(n_cands, 1));
-        if (batch->n_probes) {
-            cudaMemcpyAsync(d_probe, sl.h_probe, 4ull * batch->n_probes, cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(d_offs, sl.h_offs, 8ull * (batch->n_probes + 1), cudaMemcpyHostToDevice, s);
+        if (batch->n_probes) e = cudaMemcpyAsync(d_probe, src_probe, 4ull * batch->n_probes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && offs_n) e = cudaMemcpyAsync(d_offs, src_offs, 8ull * offs_n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && n_cands) e = cudaMemcpyAsync(d_cand, src_cand, 4ull * n_cands, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && direct_copy) e = cudaEventRecord(sl.copied, s);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(s);  // no copy may still read the caller's arrays
+            cudaFreeAsync(t->d_mem, s);
+            return unreserve(cuda_fail(ctx, e, "submit copy"));
         }
-        if (n_cands) cudaMemcpyAsync(d_cand, sl.h_cand, 4ull * n_cands, cudaMemcpyHostToDevice, s);
         a.single.probe_ids = d_probe;
         a.single.cand_offsets = d_offs;
         a.single.cand_ids = d_cand;
@@ -856,7 +919,9 @@ extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t*
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_count, d_count, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_err, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev, s);
+    if (e == cudaSuccess && direct_copy) e = cudaEventSynchronize(sl.copied);
     if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
         cudaFreeAsync(t->d_mem, s);
         return unreserve(cuda_fail(ctx, e, "submit"));
     }
@@ -976,6 +1041,7 @@ void remember_counters(ssj_ctx* ctx, Counters* c) { ctx->last_ctr = c; }
 struct ssj_multi {
     VerifyArgs a;
     LaunchShape shape;
+    uint32_t block_threads = 256;
     void* ws = nullptr;
     std::vector<ssj_coll> colls;  // collections marked busy
     cudaStream_t capture_stream = nullptr;
@@ -1026,7 +1092,9 @@ extern "C" ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, u
     if (e != cudaSuccess) return fail(ctx, SSJ_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     memset(&m->a, 0, sizeof(m->a));
     m->a.thread_max_key = ctx->thread_max_key;
+    m->a.lane_max_key = ctx->lane_max_key;
     m->a.warp_max_key = ctx->warp_max_key;
+    m->block_threads = ctx->block_threads;
     bind_workspace(m->a, m->ws, sh, ctx->num_sms);
     m->a.table = m->a.table_out;
     m->shape = sh;
@@ -1055,7 +1123,7 @@ extern "C" ssj_status ssj_multi_launch(ssj_ctx* ctx, ssj_multi* m, void* stream)
     DeviceGuard g(ctx->device);
     ctx->last_ctr = m->a.ctr;
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
-    cudaError_t e = launch_verify(m->a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
+    cudaError_t e = launch_verify(m->a, s, ctx->num_sms, m->block_threads, profile_events(ctx));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_verify");
     return SSJ_OK;
 }
@@ -1066,7 +1134,7 @@ extern "C" ssj_status ssj_multi_graph_launch(ssj_ctx* ctx, ssj_multi* m, void* s
     if (!m->exec) {
         CUDA_TRY(ctx, cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
         CUDA_TRY(ctx, cudaStreamBeginCapture(m->capture_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = launch_verify(m->a, m->capture_stream, ctx->num_sms, ctx->block_threads, nullptr);
+        cudaError_t e = launch_verify(m->a, m->capture_stream, ctx->num_sms, m->block_threads, nullptr);
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(m->capture_stream, &graph);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "capture launch_verify");
@@ -1097,4 +1165,165 @@ extern "C" void ssj_multi_destroy(ssj_ctx* ctx, ssj_multi* m) {
     if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
     cudaFree(m->ws);
     delete m;
+}
+
+// ===========================================================================
+// Autotuning of a batched launch
+// ===========================================================================
+
+namespace {
+
+// Median device time (ms) of reps launches of m with the given granularity,
+// after one untimed launch; negative on a CUDA error (*err receives it).
+float time_setting(ssj_ctx* ctx, const ssj_multi* m, uint32_t tmax, uint32_t lmax, uint32_t wmax, uint32_t bt,
+                   uint32_t reps, cudaStream_t s, cudaEvent_t* ev, cudaError_t* err) {
+    VerifyArgs a = m->a;
+    a.thread_max_key = tmax;
+    a.lane_max_key = lmax;
+    a.warp_max_key = wmax;
+    cudaError_t e = prepare_verify(bt);
+    if (e == cudaSuccess) e = launch_verify(a, s, ctx->num_sms, bt, nullptr);
+    std::vector<float> ms;
+    for (uint32_t i = 0; e == cudaSuccess && i < reps; ++i) {
+        e = cudaEventRecord(ev[0], s);
+        if (e == cudaSuccess) e = launch_verify(a, s, ctx->num_sms, bt, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float t = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+        ms.push_back(t);
+    }
+    if (e != cudaSuccess) {
+        *err = e;
+        return -1.0f;
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+}
+
+}  // namespace
+
+extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* stream, uint32_t reps,
+                                         ssj_tune_result* out) {
+    if (!ctx || !m || !out) return fail(ctx, SSJ_EINVAL, "NULL argument");
+    reps = std::max<uint32_t>(reps, 3);
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    CUDA_TRY(ctx, cudaEventCreate(&ev[0]));
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return fail(ctx, SSJ_EDEVICE, "cudaEventCreate");
+    }
+    // Candidate values per coordinate: the thread bin's upper key, the lane
+    // bin's upper key (1: no lane bin), the warp bin's upper key (the largest
+    // value sends no probe to the block bin) and the block size, which also
+    // sets the block path's window (8 merge steps per thread).
+    static const uint32_t kThread[] = {32, 64, 128, 256, 512, 1024, 2048, 4096};
+    static const uint32_t kLane[] = {1, 256, 512, 1024, 2048};
+    static const uint32_t kWarp[] = {256, 512, 1024, 2048, 4096, 0xFFFFFFFFu};
+    static const uint32_t kBlock[] = {128, 256, 512};
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, float> seen;
+    cudaError_t err = cudaSuccess;
+    auto cost = [&](uint32_t t, uint32_t l, uint32_t w, uint32_t b) -> float {
+        auto key = std::make_tuple(t, l, w, b);
+        auto it = seen.find(key);
+        if (it != seen.end()) return it->second;
+        const float v = time_setting(ctx, m, t, l, w, b, reps, s, ev, &err);
+        seen[key] = v;
+        return v;
+    };
+    uint32_t bt = m->a.thread_max_key, bl = m->a.lane_max_key, bw = m->a.warp_max_key, bb = m->block_threads;
+    const float first = cost(bt, bl, bw, bb);
+    float best = first;
+    // coordinate descent: thread bin, lane bin, warp bin, block size; repeated while it improves
+    for (int sweep = 0; sweep < 3 && err == cudaSuccess; ++sweep) {
+        const float before = best;
+        for (uint32_t t : kThread) {
+            if (err != cudaSuccess) break;
+            const uint32_t w = std::max(bw, t);  // a thread bin above the warp bin empties the latter
+            const float v = cost(t, bl, w, bb);
+            if (v < best) best = v, bt = t, bw = w;
+        }
+        for (uint32_t l : kLane) {
+            if (err != cudaSuccess) break;
+            if (l != 1 && l <= bt) continue;  // empty lane bin, same as 1
+            const float v = cost(bt, l, bw, bb);
+            if (v < best) best = v, bl = l;
+        }
+        for (uint32_t w : kWarp) {
+            if (w < bt || err != cudaSuccess) continue;
+            const float v = cost(bt, bl, w, bb);
+            if (v < best) best = v, bw = w;
+        }
+        for (uint32_t b : kBlock) {
+            if (err != cudaSuccess) break;
+            const float v = cost(bt, bl, bw, b);
+            if (v < best) best = v, bb = b;
+        }
+        if (!(best < 0.98f * before)) break;  // no gain worth another sweep
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "autotune launch");
+    uint32_t derr = 0;
+    CUDA_TRY(ctx, cudaMemcpy(&derr, &m->a.ctr->err, sizeof(derr), cudaMemcpyDeviceToHost));
+    if (derr) return fail(ctx, SSJ_EDEVICE, "device checks fired during tuning (code %u)", derr);
+    // The multi keeps the best setting; a captured graph holds the old one.
+    m->a.thread_max_key = bt;
+    m->a.lane_max_key = bl;
+    m->a.warp_max_key = bw;
+    m->block_threads = bb;
+    CUDA_TRY(ctx, prepare_verify(bb));
+    if (m->exec) {
+        cudaGraphExecDestroy(m->exec);
+        m->exec = nullptr;
+    }
+    if (m->graph) {
+        cudaGraphDestroy(m->graph);
+        m->graph = nullptr;
+    }
+    out->thread_max_key = bt;
+    out->lane_max_key = bl;
+    out->warp_max_key = bw;
+    out->block_threads = bb;
+    out->best_ms = best;
+    out->initial_ms = first;
+    out->settings_tried = (uint32_t)seen.size();
+    return SSJ_OK;
+}
+
+// ===========================================================================
+// Read-bandwidth probe
+// ===========================================================================
+
+extern "C" ssj_status ssj_read_bandwidth(ssj_ctx* ctx, uint64_t bytes, uint32_t passes, double* gbs) {
+    if (!ctx || !gbs) return fail(ctx, SSJ_EINVAL, "NULL argument");
+    bytes &= ~uint64_t(15);
+    if (bytes == 0 || passes == 0) return fail(ctx, SSJ_EINVAL, "bytes must be >= 16 and passes > 0");
+    DeviceGuard g(ctx->device);
+    void* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, bytes + 256);
+    if (e != cudaSuccess) return fail(ctx, SSJ_ENOMEM, "cudaMalloc(%llu): %s", (unsigned long long)bytes,
+                                      cudaGetErrorString(e));
+    uint32_t* sink = reinterpret_cast<uint32_t*>(static_cast<char*>(buf) + bytes);
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaMemsetAsync(buf, 0, bytes + 256, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = read_probe(buf, bytes, 1, sink, ctx->num_sms, s);  // warm-up pass
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = read_probe(buf, bytes, passes, sink, ctx->num_sms, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read probe");
+    *gbs = ms > 0 ? (double)bytes * passes / (ms * 1e-3) / 1e9 : 0.0;
+    return SSJ_OK;
 }

@@ -25,6 +25,7 @@ enum : uint32_t {
     VF_FORCE_WARP = 8u,
     VF_FORCE_BLOCK = 16u,
     VF_SELF_JOIN = 32u,
+    VF_FORCE_LANE = 64u,
 };
 
 // One join instance of a launch: its collections, grouped candidate list,
@@ -51,14 +52,16 @@ struct Instance {
     uint32_t pad;
 };
 
-// Work item for warp- or block-per-pair verification: n candidates of probe
-// set r starting at candidate index c0, in instance inst.
+// Work item for warp-, lane- or block-per-pair verification: n candidates of
+// probe set r starting at candidate index c0, in instance inst.  In the warp
+// list, mode 0 is one warp per pair, mode 1 one lane per pair (r in shared
+// memory).
 struct WorkItem {
     uint32_t r;
     uint32_t n;
     uint64_t c0;
     uint32_t inst;
-    uint32_t pad;
+    uint32_t pad;  // mode
 };
 
 // One short pair of the compacted list: probe slot k (index into the
@@ -90,7 +93,8 @@ enum : uint32_t {
 
 constexpr uint32_t kWarpItemCands = 8;   // most candidates per warp work item
 constexpr uint32_t kBlockItemCands = 16; // most candidates per block work item
-constexpr uint32_t kThreadKeyCap = 1024; // largest 2|r| verified one pair per thread
+constexpr uint32_t kLaneItemCands = 128; // most candidates per lane work item
+constexpr uint32_t kLaneMinCands = 16;   // fewest candidates of a probe sent to the lane bin
 
 // Kernel arguments of one launch (passed by value).
 struct VerifyArgs {
@@ -111,7 +115,9 @@ struct VerifyArgs {
     uint64_t pair_cap;
     uint32_t warp_item_cap, block_item_cap;
     uint32_t warp_item_cands, block_item_cands;  // candidates per work item
+    uint32_t lane_item_cands;
     uint32_t thread_max_key;      // 2|r| <= this: one thread per pair
+    uint32_t lane_max_key;        // 2|r| <= this (and r fits, >= kLaneMinCands candidates): one lane per pair
     uint32_t warp_max_key;        // 2|r| <= this: one warp per pair; above: one block
 };
 
@@ -142,5 +148,10 @@ cudaError_t prepare_verify(uint32_t block_threads);
 // verify, and after the verify kernel, on st.
 cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uint32_t block_threads,
                           cudaEvent_t* ev = nullptr);
+
+// One launch of the read-bandwidth probe: `passes` sweeps over bytes (a
+// multiple of 16) at buf, on st; sink is a device word the kernel may write.
+cudaError_t read_probe(const void* buf, uint64_t bytes, uint32_t passes, uint32_t* sink, int num_sms,
+                       cudaStream_t st);
 
 }  // namespace ssj

@@ -315,12 +315,100 @@ struct WarpOut {
     }
 };
 
-__device__ __forceinline__ uint32_t probe_bin(const VerifyArgs& a, uint32_t flags, uint32_t nr) {
+// One lane item (Alternative B): the item's probe r is staged whole in the
+// warp's shared memory (rsm, 16-byte blocks), each lane verifies one of the
+// item's candidates at a time with the block merge, reading r's blocks from
+// shared memory and s's from global memory one block ahead; a lane that
+// finishes takes the item's next candidate.  Survivors are emitted with one
+// atomic per warp step.
+__device__ __noinline__ void lane_item(const Instance& I, const WorkItem& wi, uint32_t nr, const uint4* rsm, int lane,
+                          uint32_t* err) {
+    const uint32_t flags = I.flags;
+    const bool emit_all = (flags & VF_EMIT_ALL) != 0, early = !emit_all;
+    const bool self_join = (flags & VF_SELF_JOIN) != 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t rq = (nr + 3) >> 2;
+    const uint4 zero4 = make_uint4(0, 0, 0, 0);
+    uint32_t cursor = 0;  // next candidate of the item (warp-uniform)
+    bool active = false;
+    uint32_t s_id = 0, ns = 0, req = 0, sq = 0;
+    const uint4* s4 = nullptr;
+    BlockState st;
+    st.qi = st.qj = st.o = 0;
+    st.fin = true;
+    st.rej = false;
+    uint4 rc = zero4, sc = zero4, sn = zero4;
+    for (;;) {
+        const uint32_t idle = __ballot_sync(kFull, !active);
+        if (idle && cursor < wi.n) {
+            const uint32_t my = cursor + __popc(idle & lt_mask);
+            if (!active && my < wi.n) {
+                const uint32_t s = I.cand_ids[wi.c0 + my];
+                if (s >= I.s_n_sets) {
+                    atomicOr(err, ERR_CAND_ID);
+                } else if (!(self_join && s == wi.r)) {
+                    const uint2 ds = I.s_desc[s];
+                    const uint32_t q = required_overlap(I.p, I.den, I.magic, nr, ds.y);
+                    if (emit_all || (nr + ds.y > 0 && q <= min(nr, ds.y))) {  // length filter
+                        active = true;
+                        s_id = s;
+                        ns = ds.y;
+                        req = q;
+                        sq = (ns + 3) >> 2;
+                        s4 = I.s_toks4 + ds.x;
+                        st.qi = st.qj = st.o = 0;
+                        st.rej = false;
+                        st.fin = nr == 0 || ns == 0;
+                        rc = rq ? rsm[0] : zero4;
+                        sc = sq ? __ldg(s4) : zero4;
+                        sn = sq > 1 ? __ldg(s4 + 1) : zero4;
+                    }
+                }
+            }
+            cursor += __popc(idle);
+        }
+        if (!__any_sync(kFull, active)) {
+            if (cursor >= wi.n) break;
+            continue;
+        }
+        if (active && !st.fin) {
+            bool ar, as;
+            block_step(rc, sc, nr, ns, req, early, st, ar, as);
+            if (ar && st.qi < rq) rc = rsm[st.qi];
+            if (as) {
+                sc = sn;
+                if (st.qj + 1 < sq) sn = __ldg(s4 + st.qj + 1);
+            }
+        }
+        const bool done = active && st.fin;
+        const bool pass = done && (emit_all || (!st.rej && st.o >= req));
+        const uint32_t pmask = __ballot_sync(kFull, pass);
+        if (pmask) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(I.count, (unsigned long long)__popc(pmask));
+            if (!(flags & VF_COUNT_ONLY)) {
+                b0 = __shfl_sync(kFull, b0, 0);
+                if (pass) emit_triple(I.out, I.cap, self_join, b0 + __popc(pmask & lt_mask), wi.r, s_id, st.o);
+            }
+        }
+        if (done) active = false;
+    }
+}
+
+// Granularity of a probe with |r| = nr and n candidates: 0 thread per pair,
+// 1 warp per pair, 2 block per pair, 3 lane per pair with r in the warp's
+// shared memory (Alternative B; needs r to fit and enough candidates to
+// occupy the lanes).
+__device__ __forceinline__ uint32_t probe_bin(const VerifyArgs& a, uint32_t flags, uint32_t nr, uint64_t n) {
+    const bool lane_ok = nr + 4 <= kWarpRCap;
     if (flags & VF_FORCE_BLOCK) return 2;
     if (flags & VF_FORCE_WARP) return 1;
     if (flags & VF_FORCE_THREAD) return 0;
+    if (flags & VF_FORCE_LANE) return lane_ok ? 3u : 1u;
     const uint64_t key = 2ull * nr;  // |r|+|s| at |s| = |r|
-    return key <= a.thread_max_key ? 0u : (key <= a.warp_max_key ? 1u : 2u);
+    if (key <= a.thread_max_key) return 0;
+    if (key <= a.lane_max_key && lane_ok && n >= kLaneMinCands) return 3;
+    return key <= a.warp_max_key ? 1u : 2u;
 }
 
 // Reserve `want` slots of a shared counter for every lane of the warp with
@@ -431,7 +519,7 @@ __global__ void plan_kernel(VerifyArgs a) {
                     a.rdesc[slot] = rdesc;
                     a.rid[slot] = r;
                     n = c1 - c0;
-                    bin = probe_bin(a, I.flags, rdesc.y);
+                    bin = probe_bin(a, I.flags, rdesc.y, n);
                 }
             }
         }
@@ -484,9 +572,11 @@ __global__ void plan_kernel(VerifyArgs a) {
                 }
             }
         }
-        // longer probes: work items of up to warp_item_cands / block_item_cands candidates
-        const uint32_t wc = a.warp_item_cands, bc = a.block_item_cands;
-        const unsigned long long wn = (bin == 1) ? (n + wc - 1) / wc : 0;
+        // longer probes: work items of up to warp_item_cands / lane_item_cands /
+        // block_item_cands candidates (lane items share the warp item list,
+        // marked by mode 1)
+        const uint32_t wc = bin == 3 ? a.lane_item_cands : a.warp_item_cands, bc = a.block_item_cands;
+        const unsigned long long wn = (bin == 1 || bin == 3) ? (n + wc - 1) / wc : 0;
         const unsigned long long wbase = warp_reserve(&a.ctr->warp_items, wn, lane);
         for (unsigned long long it = 0; it < wn; ++it) {
             if (wbase + it >= a.warp_item_cap) { atomicOr(&a.ctr->err, ERR_GUARD); break; }
@@ -496,7 +586,7 @@ __global__ void plan_kernel(VerifyArgs a) {
             wi.n = (uint32_t)min((uint64_t)wc, c0 + n - s0);
             wi.c0 = s0;
             wi.inst = inst;
-            wi.pad = 0;
+            wi.pad = bin == 3 ? 1u : 0u;
             a.warp_items[wbase + it] = wi;
         }
         const unsigned long long bn = (bin == 2) ? (n + bc - 1) / bc : 0;
@@ -619,6 +709,11 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
             if (r_staged) {
                 stage<32>(r4, 0, nr, abuf, lane);
                 __syncwarp();
+            }
+            if (wi.pad == 1 && r_staged) {
+                lane_item(I, wi, nr, reinterpret_cast<const uint4*>(abuf), lane, &a.ctr->err);
+                __syncwarp();  // abuf reuse
+                continue;
             }
             for (uint32_t m = 0; m < wi.n; ++m) {
                 const uint32_t s = I.cand_ids[wi.c0 + m];
@@ -825,11 +920,14 @@ static uint64_t item_cap(uint64_t n_probes, uint64_t n_cands, uint32_t per_item)
 // large batches get up to kWarpItemCands / kBlockItemCands to bound the
 // number of dynamic-scheduling atomics.  (Estimates: 32 resident warps and
 // 4 resident CTAs per SM.)
-static void item_sizes(uint64_t n_cands, int num_sms, uint32_t* per_warp_item, uint32_t* per_block_item) {
+static void item_sizes(uint64_t n_cands, int num_sms, uint32_t* per_warp_item, uint32_t* per_block_item,
+                       uint32_t* per_lane_item) {
     const uint64_t warps = 32ull * (uint64_t)num_sms, ctas = 4ull * (uint64_t)num_sms;
-    uint64_t w = n_cands / (64 * warps), b = n_cands / (64 * ctas);
+    uint64_t w = n_cands / (64 * warps), b = n_cands / (64 * ctas), l = n_cands / (8 * warps);
     *per_warp_item = (uint32_t)(w < 1 ? 1 : (w > kWarpItemCands ? kWarpItemCands : w));
     *per_block_item = (uint32_t)(b < 1 ? 1 : (b > kBlockItemCands ? kBlockItemCands : b));
+    l = l < 32 ? 32 : (l > kLaneItemCands ? kLaneItemCands : l);
+    *per_lane_item = (uint32_t)(l & ~31ull);
 }
 
 static uint64_t pair_cap(const LaunchShape& sh) { return sh.total_cands + 32ull * sh.n_tiles + 32; }
@@ -844,8 +942,8 @@ LaunchShape single_shape(uint32_t n_probes, uint64_t n_cands) {
 }
 
 size_t workspace_bytes(const LaunchShape& sh, int num_sms) {
-    uint32_t wc, bc;
-    item_sizes(sh.total_cands, num_sms, &wc, &bc);
+    uint32_t wc, bc, lc;
+    item_sizes(sh.total_cands, num_sms, &wc, &bc, &lc);
     const uint64_t slots = 32ull * sh.n_tiles + 1, pc = pair_cap(sh);
     return align256(sizeof(Counters)) + align256(sizeof(Instance) * ((size_t)sh.n_inst + 1)) +
            align256(sizeof(uint2) * slots) + align256(sizeof(uint32_t) * slots) +
@@ -860,7 +958,7 @@ size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands, int num_sms) {
 
 void bind_workspace(VerifyArgs& a, void* ws, const LaunchShape& sh, int num_sms) {
     char* p = static_cast<char*>(ws);
-    item_sizes(sh.total_cands, num_sms, &a.warp_item_cands, &a.block_item_cands);
+    item_sizes(sh.total_cands, num_sms, &a.warp_item_cands, &a.block_item_cands, &a.lane_item_cands);
     const uint64_t slots = 32ull * sh.n_tiles + 1;
     a.n_inst = sh.n_inst;
     a.n_tiles = sh.n_tiles;

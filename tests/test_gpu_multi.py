@@ -34,9 +34,10 @@ def _dev(b, dev):
             torch.from_numpy(b.cand_ids.astype(np.int32)).to(dev))
 
 
-def _run_multi(ctx, cases, graph_reps=0):
+def _run_multi(ctx, cases, graph_reps=0, tune=None):
     """cases: list of (R, S, p, q, Batch, flags).  Returns per-instance sorted triples for the
-    plain launch and for each graph replay."""
+    plain launch and for each graph replay.  tune: a list that receives the autotuner's report,
+    if the launch is to be autotuned first."""
     import torch
     dev = torch.device("cuda:0")
     keep, dbs, outs, caps = [], [], [], []
@@ -52,6 +53,9 @@ def _run_multi(ctx, cases, graph_reps=0):
     m = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
     results = []
     try:
+        if tune is not None:
+            ssj.ssj_multi_graph_launch(ctx, m)  # a graph captured before tuning is replaced
+            tune.append(ssj.ssj_multi_autotune(ctx, m, reps=3))
         for rep in range(1 + graph_reps):
             for o in outs:
                 o.zero_()
@@ -154,3 +158,63 @@ def test_multi_keeps_collections_loaded(ctx):
     assert ei.value.status == ssj.SSJ_EBUSY
     ssj.ssj_multi_destroy(ctx, m)
     ssj.ssj_unload_collection(ctx, h)
+
+
+def test_autotuned_launch_matches_oracle(ctx):
+    """The autotuner times thread/warp/block bin boundaries and block sizes; whatever it picks,
+    plain and graph launches afterwards return the oracle's join for every instance."""
+    specs = synth.uneven_instances(count=12, seed=77, n_lo=300, n_hi=4000, mean_lo=5, mean_hi=400)
+    cases, wants, handles = [], [], []
+    for ins in specs:
+        ins.coll.plant_frac, ins.coll.plant_edits = 0.1, 1
+        c = synth.collection(ins.coll)
+        h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens, ssj.SSJ_RENUMBER_BY_FREQ)
+        handles.append(h)
+        b = synth.Batch(*ssj.feeder_all(c.offsets, c.tokens, ins.p, ins.q, n_threads=4))
+        cases.append((h, h, ins.p, ins.q, b, 0))
+        wants.append(oracle.sort_triples(oracle.allpairs_self(c.offsets, c.tokens, ins.p, ins.q)[0]))
+    rep = []
+    res = _run_multi(ctx, cases, graph_reps=1, tune=rep)
+    (t,) = rep
+    assert t["block_threads"] in (128, 256, 512)
+    assert t["thread_max_key"] in (32, 64, 128, 256, 512, 1024, 2048, 4096)
+    assert t["warp_max_key"] >= t["thread_max_key"]
+    assert t["settings_tried"] >= 3 and 0 < t["best_ms"] <= t["initial_ms"]
+    for r in res:
+        for i, (got, w) in enumerate(zip(r, wants)):
+            assert np.array_equal(got, w), (i, len(got), len(w))
+    for h in handles:
+        ssj.ssj_unload_collection(ctx, h)
+
+
+def test_read_bandwidth_probe(ctx):
+    l2 = ssj.ssj_read_bandwidth(ctx, 32 << 20, 20)
+    hbm = ssj.ssj_read_bandwidth(ctx, 2 << 30, 3)
+    assert l2 > 100 and hbm > 100
+    with pytest.raises(ssj.SsjError):
+        ssj.ssj_read_bandwidth(ctx, 8, 1)
+
+
+@pytest.mark.parametrize("tmax,lmax,wmax,bt", [(4096, 1, 4096, 256), (32, 1, 256, 128), (32, 1, 256, 512),
+                                               (128, 1, 1024, 128), (512, 1, 0xFFFFFFFF, 512),
+                                               (1 << 30, 1, 1 << 30, 128), (64, 2048, 2048, 256),
+                                               (256, 1024, 4096, 128), (32, 4096, 256, 512)])
+def test_bins_and_block_sizes_match_oracle(ctx, tmax, lmax, wmax, bt):
+    """Every bin boundary and block size the autotuner may pick gives the oracle's result, on
+    sets long enough to reach all three granularities."""
+    spec = synth.long_sets(n=1200)
+    spec.plant_frac, spec.plant_edits = 0.3, 10
+    c = synth.collection(spec)
+    h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens)
+    try:
+        ssj.ssj_set_granularity(ctx, tmax, lmax, wmax, bt)
+        for p, q in ((3, 5), (4, 5)):
+            pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=4)
+            got = ssj.triples_to_array(ssj.ssj_verify_batch(ctx, h, h, p, q, pr, co, ci))
+            want = oracle.sort_triples(oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q,
+                                                           pr, co, ci))
+            assert np.array_equal(got, want), (p, q, len(got), len(want))
+            assert len(want) > 0
+    finally:
+        ssj.ssj_set_granularity(ctx, 128, 2048, 2048, 256)
+        ssj.ssj_unload_collection(ctx, h)

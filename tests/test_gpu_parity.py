@@ -15,7 +15,7 @@ from paper_1812_09141_gb300 import _build
 
 pytestmark = pytest.mark.gpu
 
-GRANULARITIES = [0, ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK]
+GRANULARITIES = [0, ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_LANE, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK]
 T_ALL = [(19, 20), (9, 10), (17, 20), (4, 5), (3, 4), (7, 10), (13, 20), (3, 5)]
 
 

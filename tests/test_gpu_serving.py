@@ -55,3 +55,35 @@ def test_coprocess_finds_the_join():
         assert st["join_s"] > 0 and st["filter_only_s"] > 0
     finally:
         ssj.ssj_destroy(ctx)
+
+
+def test_submit_from_pinned_inputs_then_overwrite():
+    """Pinned inputs are copied straight from the caller's arrays; once ssj_submit returns the
+    caller may overwrite them (here: with ids that would fail the device checks) without
+    changing the result.  Mixed pinned and pageable arrays in one batch take both paths."""
+    import torch
+    _build.build()
+    spec = synth.short_sets(n=20_000)
+    spec.plant_frac, spec.plant_edits = 0.2, 2
+    c = synth.collection(spec)
+    pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, 3, 5, n_threads=4)
+    want = oracle.sort_triples(oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, 3, 5,
+                                                   pr, co, ci))
+
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    ctx = ssj.ssj_create(0, mem_budget_bytes=256 << 20, max_inflight=2)
+    try:
+        h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens)
+        for mask in range(8):  # which of probe_ids / cand_offsets / cand_ids are pinned
+            arrs = [pinned(a) if mask >> i & 1 else a.copy() for i, a in enumerate((pr, co, ci))]
+            t = ssj.ssj_submit(ctx, h, h, 3, 5, *arrs)
+            assert t is not None
+            for a in arrs:
+                a[:] = np.iinfo(a.dtype).max
+            assert ssj.ssj_poll(ctx, t, timeout_ms=-1)
+            got = ssj.ssj_results(ctx, t)
+            np.testing.assert_array_equal(ssj.triples_to_array(got), want)
+    finally:
+        ssj.ssj_destroy(ctx)
