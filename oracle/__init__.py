@@ -11,9 +11,11 @@ returns results as (r, s, overlap) uint32 triples.
 
 Functions and the passages they follow:
 
-* ``required_overlap`` / ``jaccard_pass`` - Table "Similarity Functions"
-  (Section 2.2.2), Jaccard with t = p/q in exact integer form.
-* ``length_ok`` - the length filter of Section 2.2.3.
+* ``required_overlap`` / ``jaccard_pass`` / ``sim_pass`` - Table "Similarity
+  Functions" (Section 2.2.2): Jaccard, Dice, Cosine (and the plain overlap
+  threshold) with t = p/q in exact integer form (``sim`` selects the
+  function; Jaccard by default).
+* ``length_ok`` - the length filter of Section 2.2.3, per function.
 * ``overlap`` - intersection count by a sorted-list merge (Section 4.2.2).
 * ``verify_pair`` - the verification loop of Section 3.1 with the
   positional stopping rule of Section 2.2.3.
@@ -45,6 +47,9 @@ _lib = None
 
 EARLY = 1
 EMIT_ALL = 2
+
+# similarity functions (Table "Similarity Functions"), threshold t = p/q
+JACCARD, DICE, COSINE, OVERLAP = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -85,6 +90,24 @@ def _load():
             lib.oracle_renumber.argtypes = [u64p, u32p, u32, u32p]
             lib.oracle_allpairs_self.restype = i64
             lib.oracle_allpairs_self.argtypes = [u64p, u32p, u32, u64, u64, u32p, u64, u64p]
+            c_int = ctypes.c_int
+            lib.oracle_sim_pass.restype = c_int
+            lib.oracle_sim_pass.argtypes = [c_int, u64, u64, u64, u64, u64]
+            lib.oracle_required_overlap_sim.restype = u64
+            lib.oracle_required_overlap_sim.argtypes = [c_int, u64, u64, u64, u64]
+            lib.oracle_length_ok_sim.restype = c_int
+            lib.oracle_length_ok_sim.argtypes = [c_int, u64, u64, u64, u64]
+            lib.oracle_verify_pair_sim.restype = c_int
+            lib.oracle_verify_pair_sim.argtypes = [c_int, u32p, u32, u32p, u32, u64, u64, c_int, u32p, u32p, u32p]
+            lib.oracle_bruteforce_self_sim.restype = i64
+            lib.oracle_bruteforce_self_sim.argtypes = [c_int, u64p, u32p, u32, u64, u64, u32p, u64]
+            lib.oracle_bruteforce_rs_sim.restype = i64
+            lib.oracle_bruteforce_rs_sim.argtypes = [c_int, u64p, u32p, u32, u64p, u32p, u32, u64, u64, u32p, u64]
+            lib.oracle_verify_batch_sim.restype = i64
+            lib.oracle_verify_batch_sim.argtypes = [c_int, u64p, u32p, u32, u64p, u32p, u32, c_int, u64, u64,
+                                                    u32, u32p, u64p, u32p, c_int, u32p, u64, u32p, u32p]
+            lib.oracle_allpairs_self_sim.restype = i64
+            lib.oracle_allpairs_self_sim.argtypes = [c_int, u64p, u32p, u32, u64, u64, u32p, u64, u64p]
             _lib = lib
     return _lib
 
@@ -124,16 +147,24 @@ def _triples(fn, cap_hint=1024):
         cap = k
 
 
-def required_overlap(nr: int, ns: int, p: int, q: int) -> int:
-    return int(_load().oracle_required_overlap(nr, ns, p, q))
+def required_overlap(nr: int, ns: int, p: int, q: int, sim: int = JACCARD) -> int:
+    if sim == JACCARD:
+        return int(_load().oracle_required_overlap(nr, ns, p, q))
+    return int(_load().oracle_required_overlap_sim(sim, nr, ns, p, q))
 
 
 def jaccard_pass(o: int, nr: int, ns: int, p: int, q: int) -> bool:
     return bool(_load().oracle_jaccard_pass(o, nr, ns, p, q))
 
 
-def length_ok(nr: int, ns: int, p: int, q: int) -> bool:
-    return bool(_load().oracle_length_ok(nr, ns, p, q))
+def sim_pass(o: int, nr: int, ns: int, p: int, q: int, sim: int = JACCARD) -> bool:
+    return bool(_load().oracle_sim_pass(sim, o, nr, ns, p, q))
+
+
+def length_ok(nr: int, ns: int, p: int, q: int, sim: int = JACCARD) -> bool:
+    if sim == JACCARD:
+        return bool(_load().oracle_length_ok(nr, ns, p, q))
+    return bool(_load().oracle_length_ok_sim(sim, nr, ns, p, q))
 
 
 def overlap(a, b) -> int:
@@ -143,31 +174,44 @@ def overlap(a, b) -> int:
     return int(_load().oracle_overlap(_p32(a), la, _p32(b), lb))
 
 
-def verify_pair(r, s, p: int, q: int, early: bool = True):
+def verify_pair(r, s, p: int, q: int, early: bool = True, sim: int = JACCARD):
     """Returns (passes, overlap, consumed_r, consumed_s)."""
     lr, ls = len(r), len(s)
     r, s = _u32(r), _u32(s)
     o, ci, cj = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
-    ok = _load().oracle_verify_pair(_p32(r), lr, _p32(s), ls, p, q, int(early),
-                                    ctypes.byref(o), ctypes.byref(ci), ctypes.byref(cj))
+    lib = _load()
+    refs = (ctypes.byref(o), ctypes.byref(ci), ctypes.byref(cj))
+    if sim == JACCARD:
+        ok = lib.oracle_verify_pair(_p32(r), lr, _p32(s), ls, p, q, int(early), *refs)
+    else:
+        ok = lib.oracle_verify_pair_sim(sim, _p32(r), lr, _p32(s), ls, p, q, int(early), *refs)
     return bool(ok), o.value, ci.value, cj.value
 
 
-def bruteforce_self(offsets, tokens, p: int, q: int) -> np.ndarray:
+def bruteforce_self(offsets, tokens, p: int, q: int, sim: int = JACCARD) -> np.ndarray:
     offs, toks = _u64(offsets), _u32(tokens)
     n = len(offsets) - 1
-    return _triples(lambda out, cap: _load().oracle_bruteforce_self(_p64(offs), _p32(toks), n, p, q, _p32(out), cap))
+    lib = _load()
+    if sim == JACCARD:
+        return _triples(lambda out, cap: lib.oracle_bruteforce_self(_p64(offs), _p32(toks), n, p, q, _p32(out), cap))
+    return _triples(lambda out, cap: lib.oracle_bruteforce_self_sim(sim, _p64(offs), _p32(toks), n, p, q,
+                                                                    _p32(out), cap))
 
 
-def bruteforce_rs(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int) -> np.ndarray:
+def bruteforce_rs(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, sim: int = JACCARD) -> np.ndarray:
     ro, rt, so, st = _u64(r_offsets), _u32(r_tokens), _u64(s_offsets), _u32(s_tokens)
     nr, ns = len(r_offsets) - 1, len(s_offsets) - 1
-    return _triples(lambda out, cap: _load().oracle_bruteforce_rs(_p64(ro), _p32(rt), nr, _p64(so), _p32(st), ns,
+    lib = _load()
+    if sim == JACCARD:
+        return _triples(lambda out, cap: lib.oracle_bruteforce_rs(_p64(ro), _p32(rt), nr, _p64(so), _p32(st), ns,
                                                                   p, q, _p32(out), cap))
+    return _triples(lambda out, cap: lib.oracle_bruteforce_rs_sim(sim, _p64(ro), _p32(rt), nr, _p64(so), _p32(st),
+                                                                  ns, p, q, _p32(out), cap))
 
 
 def verify_batch(r_offsets, r_tokens, s_offsets, s_tokens, self_join: bool, p: int, q: int,
-                 probe_ids, cand_offsets, cand_ids, flags: int = EARLY, consumed: bool = False):
+                 probe_ids, cand_offsets, cand_ids, flags: int = EARLY, consumed: bool = False,
+                 sim: int = JACCARD):
     """Verify a grouped candidate batch.  Returns triples, or (triples, consumed_r, consumed_s)."""
     ro, rt, so, st = _u64(r_offsets), _u32(r_tokens), _u64(s_offsets), _u32(s_tokens)
     nr, ns = len(r_offsets) - 1, len(s_offsets) - 1
@@ -179,9 +223,12 @@ def verify_batch(r_offsets, r_tokens, s_offsets, s_tokens, self_join: bool, p: i
     lib = _load()
 
     def call(out, cap):
-        return lib.oracle_verify_batch(_p64(ro), _p32(rt), nr, _p64(so), _p32(st), ns, int(self_join), p, q,
-                                       n_probes, _p32(pr), _p64(co), _p32(ci), flags, _p32(out), cap,
-                                       _p32(cr) if consumed else None, _p32(cs) if consumed else None)
+        args = (_p64(ro), _p32(rt), nr, _p64(so), _p32(st), ns, int(self_join), p, q,
+                n_probes, _p32(pr), _p64(co), _p32(ci), flags, _p32(out), cap,
+                _p32(cr) if consumed else None, _p32(cs) if consumed else None)
+        if sim == JACCARD:
+            return lib.oracle_verify_batch(*args)
+        return lib.oracle_verify_batch_sim(sim, *args)
     tr = _triples(call, cap_hint=max(n_cands, 1))
     if consumed:
         return tr, cr[:n_cands], cs[:n_cands]
@@ -199,14 +246,19 @@ def renumber(offsets, tokens):
     return out[:len(tokens)], int(u)
 
 
-def allpairs_self(offsets, tokens, p: int, q: int):
+def allpairs_self(offsets, tokens, p: int, q: int, sim: int = JACCARD):
     """AllPairs self-join.  Returns (triples, n_candidates)."""
     offs, toks = _u64(offsets), _u32(tokens)
     n = len(offsets) - 1
     nc = ctypes.c_uint64()
     lib = _load()
-    tr = _triples(lambda out, cap: lib.oracle_allpairs_self(_p64(offs), _p32(toks), n, p, q, _p32(out), cap,
-                                                            ctypes.byref(nc)), cap_hint=1 << 16)
+    if sim == JACCARD:
+        fn = lambda out, cap: lib.oracle_allpairs_self(_p64(offs), _p32(toks), n, p, q, _p32(out), cap,
+                                                       ctypes.byref(nc))
+    else:
+        fn = lambda out, cap: lib.oracle_allpairs_self_sim(sim, _p64(offs), _p32(toks), n, p, q, _p32(out), cap,
+                                                           ctypes.byref(nc))
+    tr = _triples(fn, cap_hint=1 << 16)
     return tr, int(nc.value)
 
 
