@@ -6,19 +6,25 @@ short sets (sizes lognormal mean 20, sigma 0.6, clipped 2..200; Zipf(1.0)
 tokens over a 1,000,000 vocabulary), at Jaccard t in {0.9, 0.8, 0.7, 0.6}.
 The CPU feeder produces the four candidate batches once (untimed); one
 step verifies all four on the GPU in one batched launch (one plan and one
-verify kernel over the four instances).  Synthetic, seeded data.  Other
-workloads: long_sets, serving_collection, uneven_instances (256 joins).
+verify kernel over the four instances), with the granularity chosen by the
+library's autotuner beforehand.  Synthetic, seeded data.  Other workloads:
+tiny (all 499,500 pairs of 1,000 sets), long_sets, serving_collection,
+uneven_instances (256 joins in one launch), serving (continuous batching:
+latency percentiles and the filter/verify co-process).
 
 value   pairs/s with inputs resident in HBM; L2 is flushed (512 MiB write)
-        before every timed step because the inputs fit in L2; CUDA events on
-        the launching stream; max over ranks.
+        before every timed step; CUDA events on the launching stream; max
+        over ranks.
 e2e     the same metric through the public synchronous call with pinned
         host buffers: host->device copies, kernels and the result readback
         in the timed region.
 roofline  algorithmic bytes of the verify kernel (candidate stream, set
         descriptors, the tokens the positional filter lets the merge read,
         results) over its own event-timed duration, against the measured HBM
-        copy bandwidth.
+        copy bandwidth; l2_aware_roofline adds the L2 read rate measured by
+        the library's probe.
+warm_l2 / plain_per_batch  the same launch without the flush, and one
+        plan + verify call per instance instead of one batched launch.
 cpu_baseline / --impl reference  the CPU oracle as it stands, on host cores.
 """
 from __future__ import annotations
@@ -64,6 +70,12 @@ def workload(name: str):
                "instances": len(inst), "n_sets": int(sum(c.n for c in colls)),
                "n_tokens": int(sum(len(c.tokens) for c in colls)), "seed": 1004}
         return cfg, colls, inst
+    if name == "tiny":
+        c = synth.collection(synth.tiny_self_join())
+        cfg = {"workload": name, "description": "brute-force self-join: all 499,500 pairs of 1,000 sets "
+               "(sizes uniform 5..50, Zipf(1.0) over 1e4 tokens), t = 4/5", "n_sets": c.n,
+               "n_tokens": int(len(c.tokens)), "seed": 1001, "thresholds": ["4/5"], "candidates": "all pairs"}
+        return cfg, [c], [(0, 4, 5)]
     if name == "short_sets":
         spec = synth.short_sets()
         ts = [(9, 10), (4, 5), (7, 10), (3, 5)]
@@ -86,14 +98,20 @@ def workload(name: str):
     return cfg, [c], [(0, p, q) for p, q in ts]
 
 
-def make_batches(colls, inst):
-    """CPU feeder (AllPairs prefix filter) candidates for every instance: (ci, p, q, probes, offsets, cands)."""
+def make_batches(colls, inst, all_pairs: bool = False):
+    """CPU feeder (AllPairs prefix filter) candidates for every instance, or every pair r < s
+    (brute force) when all_pairs: (ci, p, q, probes, offsets, cands)."""
     import paper_1812_09141_gb300 as ssj
     threads = max(1, min(16, os.cpu_count() or 1))
+    import synth
     out = []
     for ci, p, q in inst:
         c = colls[ci]
-        pr, co, cands = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=threads)
+        if all_pairs:
+            b = synth.all_pairs_batch(c.n)
+            pr, co, cands = b.probe_ids, b.cand_offsets, b.cand_ids
+        else:
+            pr, co, cands = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=threads)
         out.append((ci, p, q, pr, co, cands))
     return out
 
@@ -301,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     cfg, colls, inst = workload(args.workload)
-    batches = make_batches(colls, inst)
+    batches = make_batches(colls, inst, all_pairs=args.workload == "tiny")
     pairs_step = sum(len(b[5]) for b in batches)
 
     stream = torch.cuda.Stream(device=dev)
@@ -322,11 +340,20 @@ def run_ours(args, rank, world, local_rank):
     counts = torch.zeros(len(batches), dtype=torch.int64, device=dev)
     flush = torch.empty(max(args.l2_flush_mb << 18, 1), dtype=torch.int32, device=dev)
     torch.cuda.synchronize(dev)
-    multi = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
-    # granularity and block size chosen by the library's autotuner on this launch (untimed)
-    tune = ssj.ssj_multi_autotune(ctx, multi, stream.cuda_stream, reps=5)
-    ssj.ssj_set_granularity(ctx, tune["thread_max_key"], tune["lane_max_key"], min(tune["warp_max_key"], 1 << 30),
-                            tune["block_threads"])
+    if args.granularity:
+        # a fixed setting (profiling runs: no tuning launches before the timed ones)
+        t, l, w, b = (int(x) for x in args.granularity.split(","))
+        ssj.ssj_set_granularity(ctx, t, l, w, b)
+        multi = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
+        tune = {"thread_max_key": t, "lane_max_key": l, "warp_max_key": w, "block_threads": b,
+                "chosen_by": "--granularity"}
+    else:
+        multi = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
+        # granularity and block size chosen by the library's autotuner on this launch (untimed)
+        tune = ssj.ssj_multi_autotune(ctx, multi, stream.cuda_stream, reps=5)
+        tune["chosen_by"] = "ssj_multi_autotune (median of 5 launches per setting)"
+        ssj.ssj_set_granularity(ctx, tune["thread_max_key"], tune["lane_max_key"],
+                                min(tune["warp_max_key"], 1 << 30), tune["block_threads"])
 
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -558,6 +585,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--out-cap", type=int, default=1 << 26, help="most result triples kept per instance")
     ap.add_argument("--requests", type=int, default=1000, help="requests of the serving workload")
+    ap.add_argument("--granularity", default="", help="thread,lane,warp,block_threads: fixed setting instead of "
+                    "the autotuner's (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
@@ -574,7 +603,7 @@ def main():
         if rank != 0:
             return
         cfg, colls, inst = workload(args.workload)
-        batches = make_batches(colls, inst)
+        batches = make_batches(colls, inst, all_pairs=args.workload == "tiny")
         import oracle
         pairs_step = sum(len(b[5]) for b in batches)
 
@@ -625,7 +654,7 @@ def main():
     gm = res["graph_ms"]
     line["graph_replay_ms_per_step"] = float(np.median(gm)) if gm else None
     line["gpu_launches"] = 2 * res["launches"]
-    line["config"]["granularity"] = dict(res["tune"], chosen_by="ssj_multi_autotune (median of 5 launches per setting)")
+    line["config"]["granularity"] = res["tune"]
     wm = sorted(res["warm_ms"])
     line["warm_l2"] = {"pairs_per_s": pairs_step / (np.median(wm) / 1e3), "p50_ms": float(np.percentile(wm, 50)),
                        "p99_ms": float(np.percentile(wm, 99)), "runs": len(wm)}

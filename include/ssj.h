@@ -143,9 +143,24 @@ ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, ui
                                    warp's shared memory (Alternative B); probes longer than
                                    1,020 tokens go to the warp path */
 
+/* Similarity function (Table "Similarity Functions", Section 2.2.2), in the
+ * flags' bits 8-9; t = p/q.  Each pair is kept iff its overlap o reaches the
+ * function's equivalent overlap, tested exactly in integers:
+ *   Jaccard  o / (|r|+|s|-o) >= t   <=>  o (p+q) >= p (|r|+|s|)    (default)
+ *   Dice     2o / (|r|+|s|) >= t    <=>  2 q o >= p (|r|+|s|)
+ *   Cosine   o / sqrt(|r||s|) >= t  <=>  (q o)^2 >= p^2 |r| |s|
+ *   Overlap  o >= t                 <=>  q o >= p   (p may exceed q)
+ * The positional early termination uses the same equivalent overlap. */
+#define SSJ_SIM_JACCARD 0x000u
+#define SSJ_SIM_DICE 0x100u
+#define SSJ_SIM_COSINE 0x200u
+#define SSJ_SIM_OVERLAP 0x300u
+#define SSJ_SIM_MASK 0x300u
+
 typedef struct {
     ssj_coll R, S;                /* R == S: self-join */
-    uint32_t p, q;                /* Jaccard threshold t = p/q, 0 < p <= q < 2^31 */
+    uint32_t p, q;                /* threshold t = p/q, 0 < p <= q < 2^31 (SSJ_SIM_OVERLAP:
+                                     0 < p, q < 2^31); Jaccard unless flags select another function */
     uint32_t n_probes;
     const uint32_t* probe_ids;    /* n_probes ids into R */
     const uint64_t* cand_offsets; /* n_probes+1 nondecreasing offsets, cand_offsets[0] = 0 */
@@ -154,7 +169,7 @@ typedef struct {
     uint64_t n_cands;             /* cand_offsets[n_probes].  Required with SSJ_DEVICE_PTRS (the
                                      host does not read device offsets; the device checks it);
                                      with host pointers 0 means "take it from cand_offsets" */
-    uint32_t flags;               /* SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | ... */
+    uint32_t flags;               /* SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | ... | SSJ_SIM_* */
 } ssj_batch;
 
 /*

@@ -1,5 +1,6 @@
 /*
- * ssj_feeder.h - CPU candidate generation for a Jaccard self-join, the
+ * ssj_feeder.h - CPU candidate generation for a self-join or an R x S join
+ * (Jaccard, Dice, Cosine or a plain overlap threshold), the
  * filtering half of the paper's filter-verification framework (thread H0 of
  * Section 3.2) that feeds the GPU verification in include/ssj.h.
  *
@@ -40,6 +41,40 @@ typedef struct ssj_feeder ssj_feeder;
  * SSJ_ENOMEM. */
 ssj_status ssj_feeder_create(const uint64_t* offsets, const uint32_t* tokens, uint32_t n_sets, uint32_t p,
                              uint32_t q, uint32_t n_threads, ssj_feeder** out);
+
+#define SSJ_FEEDER_PPJOIN 0x1u  /* PPJoin's positional filter at candidate time: a candidate
+                                   is dropped once the prefix matches found so far plus
+                                   1 + min(|r|-i-1, |s|-j-1) (i, j: positions of the current
+                                   common prefix token) fall below the pair's equivalent
+                                   overlap; fewer candidates, the same join */
+
+typedef struct {
+    uint32_t sim;        /* 0 Jaccard, 1 Dice, 2 Cosine, 3 plain overlap (SSJ_SIM_* >> 8) */
+    uint32_t p, q;       /* threshold t = p/q, as for ssj_batch */
+    uint32_t flags;      /* SSJ_FEEDER_PPJOIN */
+    uint32_t n_threads;  /* worker threads (results identical to one) */
+} ssj_feeder_opts;
+
+/* General form.  s_offsets == NULL: self-join of R, as ssj_feeder_create.
+ * Otherwise an R x S join: every set of S is indexed (prefixes as below,
+ * one token order for both collections, renumbered by their joint
+ * frequency), and each set r of R, in id order, is probed against it with
+ * the two-sided length filter (a partner's size lies where the threshold is
+ * reachable) and the prefix filter; probe ids are ids of R, candidate ids
+ * ids of S.  Errors: SSJ_EINVAL, SSJ_ENOMEM. */
+ssj_status ssj_feeder_create_ex(const uint64_t* r_offsets, const uint32_t* r_tokens, uint32_t n_r,
+                                const uint64_t* s_offsets, const uint32_t* s_tokens, uint32_t n_s,
+                                const ssj_feeder_opts* opts, ssj_feeder** out);
+
+/* The same for another similarity function of Table "Similarity Functions"
+ * (sim: 0 Jaccard, 1 Dice, 2 Cosine, 3 plain overlap o >= p/q; the values
+ * of SSJ_SIM_* shifted right by 8).  The prefix of a set x is its first
+ * |x| - a + 1 tokens, where a is the least overlap x shares with any
+ * partner that can reach t (t|x|, t|x|/(2-t), t^2|x| or t, rounded up),
+ * and a probe r keeps indexed sets of at least a(|r|) tokens (the length
+ * filter).  Thresholds as for ssj_batch. */
+ssj_status ssj_feeder_create_sim(const uint64_t* offsets, const uint32_t* tokens, uint32_t n_sets, uint32_t sim,
+                                 uint32_t p, uint32_t q, uint32_t n_threads, ssj_feeder** out);
 
 /* Fill the next chunk: at most max_probes entries in probe_ids (and
  * max_probes+1 in cand_offsets) and at most max_cands candidate ids

@@ -36,6 +36,12 @@ SSJ_FORCE_THREAD = 0x10
 SSJ_FORCE_WARP = 0x20
 SSJ_FORCE_BLOCK = 0x40
 SSJ_FORCE_LANE = 0x80
+SSJ_SIM_JACCARD = 0x000
+SSJ_SIM_DICE = 0x100
+SSJ_SIM_COSINE = 0x200
+SSJ_SIM_OVERLAP = 0x300
+SSJ_SIM_MASK = 0x300
+SSJ_FEEDER_PPJOIN = 0x1
 # context flags
 SSJ_CTX_PROFILE = 0x1
 
@@ -68,6 +74,11 @@ class ssj_tune_result(ctypes.Structure):
     _fields_ = [("thread_max_key", ctypes.c_uint32), ("lane_max_key", ctypes.c_uint32), ("warp_max_key", ctypes.c_uint32),
                 ("block_threads", ctypes.c_uint32), ("settings_tried", ctypes.c_uint32),
                 ("best_ms", ctypes.c_float), ("initial_ms", ctypes.c_float)]
+
+
+class ssj_feeder_opts(ctypes.Structure):
+    _fields_ = [("sim", ctypes.c_uint32), ("p", ctypes.c_uint32), ("q", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("n_threads", ctypes.c_uint32)]
 
 
 class ssj_serve_stats(ctypes.Structure):
@@ -113,6 +124,8 @@ SIGNATURES = {
     "ssj_serve_replay": (_INT, [_VP, _P(ssj_request), _U32, _P(ctypes.c_double), _P(ssj_serve_stats)]),
     "ssj_serve_coprocess": (_INT, [_VP, _U32, _VP, _VP, _U32, _U32, _U32, _U32, _U64, _P(ssj_coprocess_stats)]),
     "ssj_feeder_create": (_INT, [_VP, _VP, _U32, _U32, _U32, _U32, _P(_VP)]),
+    "ssj_feeder_create_sim": (_INT, [_VP, _VP, _U32, _U32, _U32, _U32, _U32, _P(_VP)]),
+    "ssj_feeder_create_ex": (_INT, [_VP, _VP, _U32, _VP, _VP, _U32, _P(ssj_feeder_opts), _P(_VP)]),
     "ssj_feeder_next": (_INT, [_VP, _U32, _U64, _VP, _VP, _VP, _P(_U32), _P(_U64), _P(_INT)]),
     "ssj_feeder_progress": (_INT, [_VP, _P(_U64), _P(_U32), _P(_U32)]),
     "ssj_feeder_destroy": (None, [_VP]),
@@ -425,6 +438,15 @@ def ssj_feeder_create(offsets, tokens, p: int, q: int, n_threads: int = 1) -> in
     return out.value
 
 
+def ssj_feeder_create_sim(offsets, tokens, sim: int, p: int, q: int, n_threads: int = 1) -> int:
+    """sim: 0 Jaccard, 1 Dice, 2 Cosine, 3 plain overlap (SSJ_SIM_* >> 8)."""
+    offs, po = _host(offsets, np.uint64)
+    toks, pt = _host(tokens, np.uint32)
+    out = ctypes.c_void_p()
+    _check(None, lib().ssj_feeder_create_sim(po, pt, len(offs) - 1, sim, p, q, n_threads, ctypes.byref(out)))
+    return out.value
+
+
 def ssj_feeder_next(f: int, max_probes: int, max_cands: int):
     """Next chunk as (probe_ids, cand_offsets, cand_ids, done)."""
     pr = np.empty(max_probes, dtype=np.uint32)
@@ -447,9 +469,33 @@ def ssj_feeder_destroy(f: int) -> None:
     lib().ssj_feeder_destroy(f)
 
 
-def feeder_all(offsets, tokens, p: int, q: int, n_threads: int = 1, chunk: int = 1 << 22):
-    """Run the feeder to completion; returns one concatenated batch (probe_ids, offsets, cands)."""
-    f = ssj_feeder_create(offsets, tokens, p, q, n_threads)
+def ssj_feeder_create_ex(r_offsets, r_tokens, s_offsets=None, s_tokens=None, sim: int = 0, p: int = 1,
+                         q: int = 1, flags: int = 0, n_threads: int = 1) -> int:
+    """Self-join of R (s_offsets None) or R x S join feeder; flags: SSJ_FEEDER_PPJOIN."""
+    ro, rpo = _host(r_offsets, np.uint64)
+    rt, rpt = _host(r_tokens, np.uint32)
+    n_s, spo, spt = 0, None, None
+    if s_offsets is not None:
+        so, spo = _host(s_offsets, np.uint64)
+        st, spt = _host(s_tokens, np.uint32)
+        n_s = len(so) - 1
+    o = ssj_feeder_opts(sim, p, q, flags, n_threads)
+    out = ctypes.c_void_p()
+    _check(None, lib().ssj_feeder_create_ex(rpo, rpt, len(ro) - 1, spo, spt, n_s, ctypes.byref(o),
+                                            ctypes.byref(out)))
+    return out.value
+
+
+def feeder_all(offsets, tokens, p: int, q: int, n_threads: int = 1, chunk: int = 1 << 22, sim: int = 0,
+               s_offsets=None, s_tokens=None, flags: int = 0):
+    """Run the feeder to completion; returns one concatenated batch (probe_ids, offsets, cands).
+    sim selects the similarity function (SSJ_SIM_* >> 8; Jaccard by default); s_offsets /
+    s_tokens make it an R x S join of (offsets, tokens) against them; flags: SSJ_FEEDER_PPJOIN."""
+    if s_offsets is None and flags == 0:
+        f = (ssj_feeder_create(offsets, tokens, p, q, n_threads) if sim == 0 else
+             ssj_feeder_create_sim(offsets, tokens, sim, p, q, n_threads))
+    else:
+        f = ssj_feeder_create_ex(offsets, tokens, s_offsets, s_tokens, sim, p, q, flags, n_threads)
     try:
         probes, offs, cands = [], [np.zeros(1, dtype=np.uint64)], []
         base = 0

@@ -235,14 +235,20 @@ ssj_status validate_host_batch(ssj_ctx* ctx, const ssj_batch* b, uint64_t* n_can
 
 ssj_status resolve(ssj_ctx* ctx, const ssj_batch* b, Collection** R, Collection** S) {
     if (!ctx || !b) return fail(ctx, SSJ_EINVAL, "NULL argument");
-    if (b->p == 0 || b->p > b->q || b->q >= (1u << 31)) return fail(ctx, SSJ_EINVAL, "threshold must be 0 < p <= q < 2^31");
+    const uint32_t sim = (b->flags & SSJ_SIM_MASK) >> 8;
+    if (sim == SIM_OVERLAP) {
+        if (b->p == 0 || b->q == 0 || b->p >= (1u << 31) || b->q >= (1u << 31))
+            return fail(ctx, SSJ_EINVAL, "overlap threshold must be 0 < p, q < 2^31");
+    } else if (b->p == 0 || b->p > b->q || b->q >= (1u << 31)) {
+        return fail(ctx, SSJ_EINVAL, "threshold must be 0 < p <= q < 2^31");
+    }
     auto ir = ctx->colls.find(b->R);
     auto is = ctx->colls.find(b->S);
     if (ir == ctx->colls.end() || is == ctx->colls.end()) return fail(ctx, SSJ_ENOTFOUND, "unknown collection");
     if (b->R != b->S && (ir->second.renumbered || is->second.renumbered))
         return fail(ctx, SSJ_EINVAL, "renumbered collections can only be self-joined");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_EMIT_ALL | SSJ_FORCE_THREAD |
-                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE;
+                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_SIM_MASK;
     if (b->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown batch flag");
     const uint32_t forced = b->flags & (SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE);
     if (forced & (forced - 1)) return fail(ctx, SSJ_EINVAL, "at most one SSJ_FORCE_* flag");
@@ -273,8 +279,14 @@ Instance make_instance(const ssj_batch* b, const Collection& R, const Collection
     I.s_desc = S.d_desc;
     I.s_n_sets = S.n_sets;
     I.p = b->p;
-    I.den = b->p + b->q;
-    I.magic = div_magic(I.den);
+    I.sim = (b->flags & SSJ_SIM_MASK) >> 8;
+    switch (I.sim) {
+        case SIM_DICE: I.den = 2 * b->q; break;
+        case SIM_COSINE: I.den = b->q; break;
+        case SIM_OVERLAP: I.den = (uint32_t)(((uint64_t)b->p + b->q - 1) / b->q); break;
+        default: I.den = b->p + b->q; break;
+    }
+    I.magic = (I.sim == SIM_JACCARD || I.sim == SIM_DICE) ? div_magic(I.den) : 0;
     I.flags = vflags(b->flags) | (b->R == b->S ? VF_SELF_JOIN : 0u);
     I.n_probes = b->n_probes;
     I.n_cands = n_cands;

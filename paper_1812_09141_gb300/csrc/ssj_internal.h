@@ -41,15 +41,23 @@ struct Instance {
     const uint32_t* cand_ids;
     ssj_triple* out;
     unsigned long long* count;  // result pairs of this instance (may exceed cap)
-    uint64_t magic;             // div_magic(p + q)
+    uint64_t magic;             // div_magic(den) for Jaccard and Dice
     uint64_t n_cands;
     uint64_t cap;
     uint32_t r_n_sets, s_n_sets;
-    uint32_t p, den;            // t = p / q, den = p + q
+    uint32_t p, den;            // t = p / q; den: see SIM_*
     uint32_t n_probes;
     uint32_t tile_base;         // first plan tile (32 probes) of this instance
     uint32_t flags;             // VF_*
-    uint32_t pad;
+    uint32_t sim;               // SIM_*
+};
+
+// Similarity function of an instance, and what den / magic hold for it.
+enum : uint32_t {
+    SIM_JACCARD = 0,  // den = p + q, magic = div_magic(den)
+    SIM_DICE = 1,     // den = 2q, magic = div_magic(den)
+    SIM_COSINE = 2,   // den = q
+    SIM_OVERLAP = 3,  // den = ceil(p / q), the required overlap itself
 };
 
 // Work item for warp-, lane- or block-per-pair verification: n candidates of

@@ -60,12 +60,13 @@ constexpr uint32_t kBlockRCap = 4096;              // r kept whole in shared mem
 constexpr uint32_t kFlatGrab = 4;                  // 32-pair chunks taken per dynamic grab in phase 3
 constexpr uint32_t kCont = 64;                     // parked pairs per warp in phase 3
 
-// A pair parked after pass 1 with its merge state.
+// A parked pair with its merge state.
 struct ContEntry {
-    uint4 m0;  // r id, s id, r start chunk, s start chunk
-    uint4 m1;  // |r|, |s|, required overlap, overlap so far
-    uint4 m2;  // r block index, s block index, unused, unused
+    uint4 m0;  // r id, s id, current 16-byte block of r, of s (indices into the token arrays)
+    uint4 m1;  // tokens of r and of s from the current blocks on, required overlap, overlap so far
+    uint4 m2;  // instance, unused, unused, unused
 };
+constexpr uint32_t kDrainMinLive = 16;             // pass 2 re-parks a warp's pairs below this many live lanes
 constexpr uint32_t kTableBytes = kCont * sizeof(ContEntry);
 
 // Phases 2 and 3 run per warp and the warps of a CTA change phase at
@@ -129,10 +130,15 @@ __device__ __forceinline__ void block_step(const uint4& rc, const uint4& sc, uin
     st.fin = (4 * st.qi >= nr || 4 * st.qj >= ns);
 }
 
-// ceil(p*(nr+ns)/(p+q)): Jaccard's equivalent overlap with t = p/q, by the
-// instance's precomputed reciprocal of p+q (exact; see arith.h).
-__device__ __forceinline__ uint32_t required_overlap(uint32_t p, uint32_t den, uint64_t magic, uint32_t nr,
-                                                     uint32_t ns) {
+// Equivalent overlap of the instance's similarity function with t = p/q
+// (Table "Similarity Functions"; exact, see arith.h): Jaccard and Dice
+// divide p(|r|+|s|) by den = p+q or 2q with the precomputed reciprocal,
+// Cosine takes the exact ceil(t sqrt(|r||s|)) (den = q), the plain overlap
+// threshold is den itself.
+__device__ __forceinline__ uint32_t required_overlap(uint32_t sim, uint32_t p, uint32_t den, uint64_t magic,
+                                                     uint32_t nr, uint32_t ns) {
+    if (sim == SIM_COSINE) return required_overlap_cosine(p, den, nr, ns);
+    if (sim == SIM_OVERLAP) return den;
     return required_overlap_magic(nr, ns, p, den, magic);
 }
 
@@ -295,6 +301,120 @@ __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const
     return o;
 }
 
+// 1 if x equals one of the four tokens of s (distinct within a block).
+__device__ __forceinline__ uint32_t match4(uint32_t x, const uint4& s) {
+    return (x == s.x) | (x == s.y) | (x == s.z) | (x == s.w);
+}
+
+// Block step of pass 2 on a (block cursor, tokens remaining) state; the same
+// step as block_step: positional bound, 16 compares between the current
+// blocks (masked by position at a set's end), then the block with the
+// smaller last valid token advances (both on a tie).  rn / sn hold the next
+// block of each side, loaded one step ahead.
+__device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4& sn, const uint4* rb,
+                                          const uint4* sb, uint32_t& rcur, uint32_t& scur, uint32_t& remr,
+                                          uint32_t& rems, uint32_t& o, uint32_t req, bool early, bool& fin,
+                                          bool& rej) {
+    const uint32_t m = min(remr, rems);
+    if (early && o + m < req) {
+        rej = true;
+        fin = true;
+        return;
+    }
+    uint32_t rmax, smax;
+    if (m >= 4) {
+        o += match4(rc.x, sc) + match4(rc.y, sc) + match4(rc.z, sc) + match4(rc.w, sc);
+        rmax = rc.w;
+        smax = sc.w;
+    } else {
+        const uint32_t nvr = min(remr, 4u), nvs = min(rems, 4u);
+        const uint32_t ra[4] = {rc.x, rc.y, rc.z, rc.w};
+        const uint32_t sv[4] = {sc.x, sc.y, sc.z, sc.w};
+        uint32_t c = 0;
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) c += ((uint32_t)x < nvr && (uint32_t)y < nvs && ra[x] == sv[y]) ? 1u : 0u;
+        o += c;
+        rmax = sel4(rc, nvr - 1);
+        smax = sel4(sc, nvs - 1);
+    }
+    const bool ar = rmax <= smax, as = smax <= rmax;
+    if (ar) {
+        rc = rn;
+        ++rcur;
+        remr = remr > 4 ? remr - 4 : 0;
+        if (remr > 4) rn = __ldg(rb + rcur + 1);
+    }
+    if (as) {
+        sc = sn;
+        ++scur;
+        rems = rems > 4 ? rems - 4 : 0;
+        if (rems > 4) sn = __ldg(sb + scur + 1);
+    }
+    fin = remr == 0 || rems == 0;
+}
+
+// Pass 2 of the short-pair phase: the parked pairs [n_cont - m, n_cont) are
+// taken one per lane (lanes may belong to different instances) and merged
+// while at least min_live lanes are still undecided; decided pairs are
+// emitted, undecided ones parked again, compacted, so that lanes are refilled
+// from later pairs instead of idling behind the longest merge of the warp.
+// min_live = 1 finishes every pair.  Returns the new number of parked pairs.
+__device__ __noinline__ uint32_t drain_parked(ContEntry* cont, uint32_t n_cont, uint32_t m, uint32_t min_live,
+                                              const Instance* table, int lane) {
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint4 zero4 = make_uint4(0, 0, 0, 0);
+    const uint32_t base = n_cont - m;
+    const bool have = (uint32_t)lane < m;
+    uint32_t rid = 0, sid = 0, rcur = 0, scur = 0, remr = 0, rems = 0, req = 0, o = 0, inst = 0;
+    const uint4* rb = nullptr;
+    const uint4* sb = nullptr;
+    bool early = true, fin = true, rej = false;
+    uint4 rc = zero4, rn = zero4, sc = zero4, sn = zero4;
+    if (have) {
+        const ContEntry* ce = cont + base + lane;
+        const uint4 m0 = ce->m0, m1 = ce->m1, m2 = ce->m2;
+        rid = m0.x;
+        sid = m0.y;
+        rcur = m0.z;
+        scur = m0.w;
+        remr = m1.x;
+        rems = m1.y;
+        req = m1.z;
+        o = m1.w;
+        inst = m2.x;
+        const Instance& I = table[inst];
+        rb = I.r_toks4;
+        sb = I.s_toks4;
+        early = !(I.flags & VF_EMIT_ALL);
+        fin = remr == 0 || rems == 0;
+        rc = __ldg(rb + rcur);
+        if (remr > 4) rn = __ldg(rb + rcur + 1);
+        sc = __ldg(sb + scur);
+        if (rems > 4) sn = __ldg(sb + scur + 1);
+    }
+    __syncwarp();  // every entry is read before any is written again
+    while ((uint32_t)__popc(__ballot_sync(kFull, !fin)) >= min_live) {
+        if (!fin) lean_step(rc, rn, sc, sn, rb, sb, rcur, scur, remr, rems, o, req, early, fin, rej);
+    }
+    if (have && fin && (!early || (!rej && o >= req))) {
+        const Instance& I = table[inst];
+        const unsigned long long idx = atomicAdd(I.count, 1ull);
+        if (!(I.flags & VF_COUNT_ONLY)) emit_triple(I.out, I.cap, (I.flags & VF_SELF_JOIN) != 0, idx, rid, sid, o);
+    }
+    const bool again = have && !fin;
+    const uint32_t amask = __ballot_sync(kFull, again);
+    if (again) {
+        ContEntry* ce = cont + base + __popc(amask & lt_mask);
+        ce->m0 = make_uint4(rid, sid, rcur, scur);
+        ce->m1 = make_uint4(remr, rems, req, o);
+        ce->m2 = make_uint4(inst, 0u, 0u, 0u);
+    }
+    __syncwarp();
+    return base + __popc(amask);
+}
+
 // Warp-local survivor buffer for pairs decided by the whole warp (one work
 // item, so one instance): lane k holds the k-th buffered triple; flushed
 // with one atomic per 32 and at the end of every item.
@@ -348,7 +468,7 @@ __device__ __noinline__ void lane_item(const Instance& I, const WorkItem& wi, ui
                     atomicOr(err, ERR_CAND_ID);
                 } else if (!(self_join && s == wi.r)) {
                     const uint2 ds = I.s_desc[s];
-                    const uint32_t q = required_overlap(I.p, I.den, I.magic, nr, ds.y);
+                    const uint32_t q = required_overlap(I.sim, I.p, I.den, I.magic, nr, ds.y);
                     if (emit_all || (nr + ds.y > 0 && q <= min(nr, ds.y))) {  // length filter
                         active = true;
                         s_id = s;
@@ -669,7 +789,7 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
                 if (self_join && s == bi.r) continue;
                 const uint2 ds = I.s_desc[s];
                 const uint32_t ns = ds.y;
-                const uint32_t req = required_overlap(I.p, I.den, I.magic, nr, ns);
+                const uint32_t req = required_overlap(I.sim, I.p, I.den, I.magic, nr, ns);
                 if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
                 bool rej;
                 const uint32_t o = block_merge<BT>(r4, nr, I.s_toks4 + ds.x, ns, req, early, rbuf, r_staged, wr, ws,
@@ -724,7 +844,7 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
                 if (self_join && s == wi.r) continue;
                 const uint2 ds = I.s_desc[s];
                 const uint32_t ns = ds.y;
-                const uint32_t req = required_overlap(I.p, I.den, I.magic, nr, ns);
+                const uint32_t req = required_overlap(I.sim, I.p, I.den, I.magic, nr, ns);
                 if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
                 bool rej;
                 const uint32_t o =
@@ -752,58 +872,10 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
         const unsigned lt_mask = (1u << lane) - 1u;
         const uint4 zero4 = make_uint4(0, 0, 0, 0);
 
-        // Pass 2: finish the parked pairs [n_cont - m, n_cont), one per lane
-        // (lanes may belong to different instances).
-        auto drain = [&](uint32_t m) {
-            uint32_t pr_id = 0, ps_id = 0, rs = 0, ss = 0, nr = 0, ns = 0, req = 0, inst = 0;
-            BlockState st;
-            st.qi = st.qj = st.o = 0;
-            st.fin = true;
-            st.rej = false;
-            uint4 rc = zero4, rn = zero4, sc = zero4, sn = zero4;
-            const uint4* rt = nullptr;
-            const uint4* stk = nullptr;
-            bool early = true;
-            if ((uint32_t)lane < m) {
-                const ContEntry* ce = cont + (n_cont - m) + lane;
-                const uint4 m0 = ce->m0, m1 = ce->m1, m2 = ce->m2;
-                pr_id = m0.x; ps_id = m0.y; rs = m0.z; ss = m0.w;
-                nr = m1.x; ns = m1.y; req = m1.z;
-                st.o = m1.w; st.qi = m2.x; st.qj = m2.y; inst = m2.z;
-                st.fin = false;
-                const Instance& I = table[inst];
-                rt = I.r_toks4 + rs;
-                stk = I.s_toks4 + ss;
-                early = !(I.flags & VF_EMIT_ALL);
-                const uint32_t rq = (nr + 3) >> 2, sq = (ns + 3) >> 2;
-                rc = __ldg(rt + st.qi);
-                if (st.qi + 1 < rq) rn = __ldg(rt + st.qi + 1);
-                sc = __ldg(stk + st.qj);
-                if (st.qj + 1 < sq) sn = __ldg(stk + st.qj + 1);
-            }
-            const bool have = (uint32_t)lane < m;
-            while (!st.fin) {
-                bool ar, as;
-                block_step(rc, sc, nr, ns, req, early, st, ar, as);
-                if (ar) {
-                    rc = rn;
-                    if (st.qi + 1 < ((nr + 3) >> 2)) rn = __ldg(rt + st.qi + 1);
-                }
-                if (as) {
-                    sc = sn;
-                    if (st.qj + 1 < ((ns + 3) >> 2)) sn = __ldg(stk + st.qj + 1);
-                }
-            }
-            if (have) {
-                const Instance& I = table[inst];
-                if (!early || (!st.rej && st.o >= req)) {
-                    const unsigned long long idx = atomicAdd(I.count, 1ull);
-                    if (!(I.flags & VF_COUNT_ONLY))
-                        emit_triple(I.out, I.cap, (I.flags & VF_SELF_JOIN) != 0, idx, pr_id, ps_id, st.o);
-                }
-            }
-            n_cont -= m;
-            __syncwarp();  // the parked entries may be overwritten from here on
+        // Pass 2 (drain_parked): the last m parked pairs, one per lane, merged
+        // while at least min_live lanes still work; the rest are parked again.
+        auto drain = [&](uint32_t m, uint32_t min_live) {
+            n_cont = drain_parked(cont, n_cont, m, min_live, table, lane);
         };
 
         for (uint32_t round = 0;; ++round) {
@@ -823,7 +895,7 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
                 const uint32_t flags = I.flags;
                 const bool emit_all = (flags & VF_EMIT_ALL) != 0, early = !emit_all;
                 const bool self_join = (flags & VF_SELF_JOIN) != 0;
-                const uint32_t s_n_sets = I.s_n_sets, p = I.p, den = I.den;
+                const uint32_t s_n_sets = I.s_n_sets, p = I.p, den = I.den, sim = I.sim;
                 const uint64_t magic = I.magic;
                 const uint4* r_toks4 = I.r_toks4;
                 const uint4* s_toks4 = I.s_toks4;
@@ -844,7 +916,7 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
                             nr = dr.y;
                             ns = ds.y;
                             if (!(self_join && pr_id == ps_id)) {
-                                req = required_overlap(p, den, magic, nr, ns);
+                                req = required_overlap(sim, p, den, magic, nr, ns);
                                 live = emit_all || (nr + ns > 0 && req <= min(nr, ns));  // length filter
                             }
                         }
@@ -887,20 +959,21 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
                 const bool park = live && !st.fin;
                 const uint32_t kmask = __ballot_sync(kFull, park);
                 if (kmask) {
-                    if (n_cont + 32 > kCont) drain(32);  // room for a full warp of parked pairs
+                    while (n_cont + 32 > kCont) drain(32, kDrainMinLive);  // room for a full warp of parked pairs
                     if (park) {
                         ContEntry* ce = cont + n_cont + __popc(kmask & lt_mask);
-                        ce->m0 = make_uint4(pr_id, ps_id, dr.x, ds.x);
-                        ce->m1 = make_uint4(nr, ns, req, st.o);
-                        ce->m2 = make_uint4(st.qi, st.qj, inst, 0u);
+                        ce->m0 = make_uint4(pr_id, ps_id, dr.x + st.qi, ds.x + st.qj);
+                        ce->m1 = make_uint4(nr - 4 * st.qi, ns - 4 * st.qj, req, st.o);
+                        ce->m2 = make_uint4(inst, 0u, 0u, 0u);
                     }
                     n_cont += __popc(kmask);
                     __syncwarp();
-                    if (n_cont >= 32) drain(32);
+                    if (n_cont >= 32) drain(32, kDrainMinLive);
                 }
             }
         }
-        while (n_cont) drain(min(n_cont, 32u));
+        // the tail: keep refilling lanes while more than a warp is parked, then finish
+        while (n_cont) drain(min(n_cont, 32u), n_cont > 32 ? kDrainMinLive : 1u);
     }
 }
 

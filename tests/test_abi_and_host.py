@@ -90,6 +90,76 @@ def test_feeder_candidates_cover_every_result(pq):
     assert np.array_equal(oracle.sort_triples(tr), oracle.sort_triples(bf))
 
 
+@pytest.mark.parametrize("sim,pq", [(oracle.DICE, (4, 5)), (oracle.DICE, (3, 5)), (oracle.COSINE, (9, 10)),
+                                    (oracle.COSINE, (3, 5)), (oracle.OVERLAP, (6, 1)), (oracle.OVERLAP, (23, 2))])
+def test_feeder_other_similarity_functions(sim, pq):
+    """The feeder's prefix and length filters for Dice, Cosine and the plain overlap threshold
+    produce exactly the oracle AllPairs candidates, which cover every brute-force result."""
+    rng = np.random.default_rng(5 + sim)
+    lists = [sorted(rng.choice(40, size=int(rng.integers(1, 30)), replace=False).tolist()) for _ in range(400)]
+    for c in (_planted(), synth.from_lists(lists)):
+        pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, *pq, n_threads=3, chunk=1013, sim=sim)
+        pairs = {(min(int(r), int(s)), max(int(r), int(s)))
+                 for r, k0, k1 in zip(pr, co[:-1], co[1:]) for s in ci[k0:k1]}
+        assert len(pairs) == len(ci)
+        bf = oracle.bruteforce_self(c.offsets, c.tokens, *pq, sim=sim)
+        assert {(int(r), int(s)) for r, s, _ in bf} <= pairs
+        _, n_cands = oracle.allpairs_self(c.offsets, c.tokens, *pq, sim=sim)
+        assert n_cands == len(ci)
+        tr = oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, *pq, pr, co, ci, sim=sim)
+        assert np.array_equal(oracle.sort_triples(tr), oracle.sort_triples(bf))
+
+
+def _pairs(pr, co, ci, self_join=True):
+    out = set()
+    for r, k0, k1 in zip(pr, co[:-1], co[1:]):
+        for s in ci[k0:k1]:
+            out.add((min(int(r), int(s)), max(int(r), int(s))) if self_join else (int(r), int(s)))
+    return out
+
+
+@pytest.mark.parametrize("sim,pq", [(oracle.JACCARD, (4, 5)), (oracle.JACCARD, (3, 5)), (oracle.DICE, (7, 10)),
+                                    (oracle.COSINE, (4, 5)), (oracle.OVERLAP, (5, 1))])
+def test_feeder_rs_join_covers_every_result(sim, pq):
+    """R x S: every brute-force result pair of R against S is a candidate, once."""
+    rng = np.random.default_rng(31 + sim)
+    R = [sorted(rng.choice(60, size=int(rng.integers(1, 30)), replace=False).tolist()) for _ in range(300)]
+    S = [sorted(rng.choice(60, size=int(rng.integers(1, 30)), replace=False).tolist()) for _ in range(250)]
+    S += [sorted(set(R[i]) | {59}) for i in range(0, 300, 7)]  # near-copies of some sets of R
+    cr, cs = synth.from_lists(R), synth.from_lists(S)
+    for ppjoin in (0, ssj.SSJ_FEEDER_PPJOIN):
+        pr, co, ci = ssj.feeder_all(cr.offsets, cr.tokens, *pq, n_threads=3, chunk=501, sim=sim,
+                                    s_offsets=cs.offsets, s_tokens=cs.tokens, flags=ppjoin)
+        pairs = _pairs(pr, co, ci, self_join=False)
+        assert len(pairs) == len(ci)
+        bf = oracle.bruteforce_rs(cr.offsets, cr.tokens, cs.offsets, cs.tokens, *pq, sim=sim)
+        assert len(bf) > 0
+        assert {(int(r), int(s)) for r, s, _ in bf} <= pairs
+        tr = oracle.verify_batch(cr.offsets, cr.tokens, cs.offsets, cs.tokens, False, *pq, pr, co, ci, sim=sim)
+        assert np.array_equal(oracle.sort_triples(tr), oracle.sort_triples(bf))
+
+
+@pytest.mark.parametrize("sim,pq", [(oracle.JACCARD, (4, 5)), (oracle.JACCARD, (3, 5)), (oracle.DICE, (4, 5)),
+                                    (oracle.COSINE, (7, 10)), (oracle.OVERLAP, (8, 1))])
+def test_feeder_ppjoin_prunes_without_losing_results(sim, pq):
+    """PPJoin's positional filter: candidates are a subset of AllPairs' and still cover every
+    result (self-join)."""
+    pruned = 0
+    for c in (_planted(n=700), synth.from_lists(
+            [sorted(np.random.default_rng(9).choice(40, size=k, replace=False).tolist())
+             for k in np.random.default_rng(10).integers(1, 30, size=400)])):
+        allp = ssj.feeder_all(c.offsets, c.tokens, *pq, n_threads=2, sim=sim)
+        ppj = ssj.feeder_all(c.offsets, c.tokens, *pq, n_threads=2, sim=sim, flags=ssj.SSJ_FEEDER_PPJOIN)
+        a, b = _pairs(*allp), _pairs(*ppj)
+        assert b <= a and len(b) == len(ppj[2])
+        bf = oracle.bruteforce_self(c.offsets, c.tokens, *pq, sim=sim)
+        assert {(int(r), int(s)) for r, s, _ in bf} <= b
+        pruned += len(a) - len(b)
+    # with a plain overlap threshold k every prefix position leaves k tokens on both sides, so
+    # the positional bound never falls below k; the normalized functions do prune
+    assert pruned == 0 if sim == oracle.OVERLAP else pruned > 0
+
+
 def test_feeder_threads_and_chunking_do_not_change_candidates():
     c = _planted(n=800)
     ref = ssj.feeder_all(c.offsets, c.tokens, 3, 5, n_threads=1, chunk=1 << 20)
