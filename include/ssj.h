@@ -191,6 +191,21 @@ ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* ou
                             uint64_t* n_out);
 
 /*
+ * Verify n_batches host batches (independent joins: own collections,
+ * thresholds, functions) synchronously in ONE batched launch: all inputs
+ * are copied to the device together (from pinned memory at the copy
+ * engines' rate), one plan and one verify kernel cover every batch, then
+ * the counts and results come back.  outs[i] / caps[i]: host room for
+ * batch i's triples; n_outs[i] receives its result count.  Host pointers
+ * only (SSJ_DEVICE_PTRS is rejected; see ssj_multi_create for device
+ * batches).  Flags per batch as for ssj_verify_batch.  If a count exceeds
+ * its cap, the first caps[i] triples are written and SSJ_ENOMEM is returned
+ * after every batch is done.  Errors as for ssj_verify_batch.
+ */
+ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches, uint32_t n_batches, ssj_triple* const* outs,
+                              const uint64_t* caps, uint64_t* n_outs);
+
+/*
  * Enqueue the verification of a batch on `stream` (a cudaStream_t, or NULL
  * for the context's stream) and return without waiting.  All batch arrays,
  * d_out (cap triples) and d_count (one uint64, receives the number of

@@ -113,6 +113,7 @@ SIGNATURES = {
     "ssj_multi_launch": (_INT, [_VP, _VP, _VP]),
     "ssj_multi_graph_launch": (_INT, [_VP, _VP, _VP]),
     "ssj_multi_destroy": (None, [_VP, _VP]),
+    "ssj_verify_batches": (_INT, [_VP, _P(ssj_batch), _U32, _P(_VP), _P(_U64), _P(_U64)]),
     "ssj_multi_autotune": (_INT, [_VP, _VP, _VP, _U32, _P(ssj_tune_result)]),
     "ssj_read_bandwidth": (_INT, [_VP, _U64, _U32, _P(ctypes.c_double)]),
     "ssj_device_error": (_INT, [_VP, _P(_U32)]),
@@ -263,6 +264,23 @@ def ssj_verify_batch(ctx: int, R: int, S: int, p: int, q: int, probe_ids, cand_o
     st = lib().ssj_verify_batch(ctx, ctypes.byref(hb.batch), res.ctypes.data, cap, ctypes.byref(n_out))
     _check(ctx, st)
     return res[:n_out.value]
+
+
+def ssj_verify_batches(ctx: int, batches: list, caps: list | None = None):
+    """Several host batches in one batched launch.  batches: list of (R, S, p, q, probe_ids,
+    cand_offsets, cand_ids, flags).  Returns a list with, per batch, its structured triples (or
+    its count with SSJ_COUNT_ONLY)."""
+    n = len(batches)
+    hbs = [_make_batch(R, S, p, q, pr, co, ci, fl) for R, S, p, q, pr, co, ci, fl in batches]
+    arr = (ssj_batch * max(n, 1))(*[h.batch for h in hbs])
+    if caps is None:
+        caps = [max(int(h.keep[1][-1]) if len(h.keep[1]) else 0, 1) for h in hbs]
+    res = [np.empty(max(int(c), 1), dtype=TRIPLE_DTYPE) for c in caps]
+    outp = (ctypes.c_void_p * max(n, 1))(*[r.ctypes.data for r in res])
+    capa = (ctypes.c_uint64 * max(n, 1))(*[int(c) for c in caps])
+    nout = (ctypes.c_uint64 * max(n, 1))()
+    _check(ctx, lib().ssj_verify_batches(ctx, arr, n, outp, capa, nout))
+    return [int(nout[i]) if batches[i][7] & SSJ_COUNT_ONLY else res[i][:nout[i]] for i in range(n)]
 
 
 def ssj_verify_batch_async(ctx: int, R: int, S: int, p: int, q: int, probe_ids, cand_offsets, cand_ids, n_cands: int,

@@ -709,6 +709,104 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
     return SSJ_OK;
 }
 
+extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches, uint32_t n_batches,
+                                         ssj_triple* const* outs, const uint64_t* caps, uint64_t* n_outs) {
+    if (!ctx || (n_batches && (!batches || !outs || !caps || !n_outs))) return fail(ctx, SSJ_EINVAL, "NULL argument");
+    if (n_batches == 0) return SSJ_OK;
+    std::vector<Instance> table(n_batches);
+    std::vector<uint64_t> n_cands(n_batches), io_off(n_batches);
+    LaunchShape sh;
+    sh.n_inst = n_batches;
+    sh.n_tiles = 0;
+    sh.total_probes = 0;
+    sh.total_cands = 0;
+    size_t off = align256(sizeof(uint64_t) * n_batches);  // counts first
+    for (uint32_t i = 0; i < n_batches; ++i) {
+        const ssj_batch* b = &batches[i];
+        if (b->flags & SSJ_DEVICE_PTRS) return fail(ctx, SSJ_EINVAL, "batch %u: host pointers expected", i);
+        Collection *R, *S;
+        ssj_status st = resolve(ctx, b, &R, &S);
+        if (st != SSJ_OK) return st;
+        st = validate_host_batch(ctx, b, &n_cands[i]);
+        if (st != SSJ_OK) return st;
+        if (caps[i] && !outs[i] && !(b->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "batch %u: NULL output", i);
+        table[i] = make_instance(b, *R, *S, n_cands[i]);
+        table[i].tile_base = sh.n_tiles;
+        const uint64_t tiles = ((uint64_t)b->n_probes + 31) / 32;
+        if ((uint64_t)sh.n_tiles + tiles > 0x7FFFFFFull) return fail(ctx, SSJ_EINVAL, "too many probes in one call");
+        sh.n_tiles += (uint32_t)tiles;
+        sh.total_probes += b->n_probes;
+        sh.total_cands += n_cands[i];
+        // device staging of this batch: probe ids, offsets, candidate ids, output
+        io_off[i] = off;
+        off += align256(4ull * std::max<uint32_t>(b->n_probes, 1)) + align256(8ull * (b->n_probes + 1)) +
+               align256(4ull * std::max<uint64_t>(n_cands[i], 1));
+        const uint64_t cap = (b->flags & SSJ_COUNT_ONLY) ? 0 : std::min(caps[i], n_cands[i]);
+        off += align256(sizeof(ssj_triple) * std::max<uint64_t>(cap, 1));
+    }
+    DeviceGuard g(ctx->device);
+    ssj_status st = ensure_device_buffer(ctx, &ctx->io, &ctx->io_bytes, off);
+    if (st != SSJ_OK) return st;
+    st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(sh, ctx->num_sms));
+    if (st != SSJ_OK) return st;
+    cudaStream_t s = ctx->stream;
+    char* base = static_cast<char*>(ctx->io);
+    uint64_t* d_counts = reinterpret_cast<uint64_t*>(base);
+    for (uint32_t i = 0; i < n_batches; ++i) {
+        const ssj_batch* b = &batches[i];
+        char* p = base + io_off[i];
+        uint32_t* d_probe = reinterpret_cast<uint32_t*>(p); p += align256(4ull * std::max<uint32_t>(b->n_probes, 1));
+        uint64_t* d_offs = reinterpret_cast<uint64_t*>(p);  p += align256(8ull * (b->n_probes + 1));
+        uint32_t* d_cand = reinterpret_cast<uint32_t*>(p);  p += align256(4ull * std::max<uint64_t>(n_cands[i], 1));
+        if (b->n_probes) {
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_probe, b->probe_ids, 4ull * b->n_probes, cudaMemcpyHostToDevice, s));
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_offs, b->cand_offsets, 8ull * (b->n_probes + 1), cudaMemcpyHostToDevice, s));
+        }
+        if (n_cands[i])
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_cand, b->cand_ids, 4ull * n_cands[i], cudaMemcpyHostToDevice, s));
+        Instance& I = table[i];
+        I.probe_ids = d_probe;
+        I.cand_offsets = d_offs;
+        I.cand_ids = d_cand;
+        I.out = reinterpret_cast<ssj_triple*>(p);
+        I.cap = (b->flags & SSJ_COUNT_ONLY) ? 0 : std::min(caps[i], n_cands[i]);
+        I.count = reinterpret_cast<unsigned long long*>(d_counts + i);
+    }
+    VerifyArgs a;
+    memset(&a, 0, sizeof(a));
+    a.thread_max_key = ctx->thread_max_key;
+    a.lane_max_key = ctx->lane_max_key;
+    a.warp_max_key = ctx->warp_max_key;
+    bind_workspace(a, ctx->ws, sh, ctx->num_sms);
+    a.table = a.table_out;
+    CUDA_TRY(ctx, cudaMemcpyAsync(a.table_out, table.data(), sizeof(Instance) * n_batches, cudaMemcpyHostToDevice, s));
+    ctx->last_ctr = a.ctr;
+    cudaError_t e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_verify");
+    std::vector<uint64_t> counts(n_batches);
+    CUDA_TRY(ctx, cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint64_t) * n_batches, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_err, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const uint32_t derr = *ctx->h_err;
+    if (derr & ERR_GUARD) return fail(ctx, SSJ_EDEVICE, "internal loop bound reached on the device (code %u)", derr);
+    if (derr) return fail(ctx, SSJ_EINVAL, "batch rejected by the device checks (code %u)", derr);
+    bool short_cap = false;
+    for (uint32_t i = 0; i < n_batches; ++i) {
+        n_outs[i] = counts[i];
+        if (batches[i].flags & SSJ_COUNT_ONLY) continue;
+        const uint64_t n_copy = std::min(counts[i], caps[i]);
+        if (n_copy)
+            CUDA_TRY(ctx, cudaMemcpyAsync(outs[i], table[i].out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost, s));
+        short_cap |= counts[i] > caps[i];
+    }
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    for (uint32_t i = 0; i < n_batches; ++i)
+        if ((batches[i].flags & SSJ_SORTED) && !(batches[i].flags & SSJ_COUNT_ONLY))
+            std::sort(outs[i], outs[i] + std::min(counts[i], caps[i]), triple_less);
+    if (short_cap) return fail(ctx, SSJ_ENOMEM, "a batch has more result pairs than its capacity (see n_outs)");
+    return SSJ_OK;
+}
+
 // ===========================================================================
 // Serving: continuous batching
 // ===========================================================================

@@ -218,3 +218,40 @@ def test_bins_and_block_sizes_match_oracle(ctx, tmax, lmax, wmax, bt):
     finally:
         ssj.ssj_set_granularity(ctx, 128, 2048, 2048, 256)
         ssj.ssj_unload_collection(ctx, h)
+
+
+def test_verify_batches_host_equals_single_calls(ctx):
+    """ssj_verify_batches (host batches, one launch) returns for every batch what the single
+    synchronous call returns; a too-small capacity answers SSJ_ENOMEM with the true counts."""
+    spec = synth.tiny_self_join(seed=31, n=600)
+    spec.plant_frac, spec.plant_edits = 0.2, 2
+    c = synth.collection(spec)
+    short = synth.collection(synth.short_sets(n=10_000))
+    cR = synth.collection(synth.tiny_self_join(seed=32, n=300))
+    h, hs, hR = (ssj.ssj_load_collection(ctx, x.offsets, x.tokens) for x in (c, short, cR))
+    ap = synth.all_pairs_batch(c.n)
+    fb = synth.Batch(*ssj.feeder_all(short.offsets, short.tokens, 3, 5, n_threads=4))
+    rb = synth.random_batch(5, cR.n, c.n, 200, 40)
+    empty = synth.Batch(np.zeros(0, np.uint32), np.zeros(1, np.uint64), np.zeros(0, np.uint32))
+    batches = [(h, h, 4, 5, *ap, 0), (h, h, 3, 5, *ap, ssj.SSJ_SIM_COSINE | ssj.SSJ_SORTED),
+               (hs, hs, 3, 5, *fb, 0), (hR, h, 1, 3, *rb, 0), (h, h, 1, 2, *ap, ssj.SSJ_COUNT_ONLY),
+               (h, h, 1, 2, *empty, 0), (h, h, 7, 1, *ap, ssj.SSJ_SIM_OVERLAP)]
+    try:
+        got = ssj.ssj_verify_batches(ctx, batches)
+        for i, (R, S, p, q, pr, co, ci, fl) in enumerate(batches):
+            want = ssj.ssj_verify_batch(ctx, R, S, p, q, pr, co, ci, flags=fl)
+            if fl & ssj.SSJ_COUNT_ONLY:
+                assert got[i] == want, i
+            else:
+                assert np.array_equal(ssj.triples_to_array(got[i]), ssj.triples_to_array(want)), i
+                if fl & ssj.SSJ_SORTED:
+                    assert np.array_equal(ssj.triples_to_array(got[i]),
+                                          np.stack([got[i]["r"], got[i]["s"], got[i]["overlap"]], 1)), i
+        n0 = len(got[0])
+        assert n0 > 1
+        with pytest.raises(ssj.SsjError) as ei:
+            ssj.ssj_verify_batches(ctx, batches[:1], caps=[n0 - 1])
+        assert ei.value.status == ssj.SSJ_ENOMEM
+    finally:
+        for x in (h, hs, hR):
+            ssj.ssj_unload_collection(ctx, x)
