@@ -42,6 +42,7 @@ import subprocess
 import sys
 import threading
 import time
+import types
 
 import numpy as np
 
@@ -50,6 +51,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "candidate pairs verified/sec and GB/s vs HBM peak; p50/p99 batch latency"
+SIM = 0                   # similarity function of every instance (0 Jaccard, 1 Dice, 2 Cosine, 3 overlap)
+SIM_NAMES = {"jaccard": 0, "dice": 1, "cosine": 2, "overlap": 3}
+OVERLAP_THRESHOLDS = [(6, 1), (8, 1), (10, 1), (12, 1)]
+REF_STEP_PAIRS = 3_000_000  # candidates per step of the reference (CPU oracle) arm
 UNIT = "pairs/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
@@ -76,6 +81,24 @@ def workload(name: str):
                "(sizes uniform 5..50, Zipf(1.0) over 1e4 tokens), t = 4/5", "n_sets": c.n,
                "n_tokens": int(len(c.tokens)), "seed": 1001, "thresholds": ["4/5"], "candidates": "all pairs"}
         return cfg, [c], [(0, 4, 5)]
+    if name == "rs_short":
+        # one seeded collection with planted near-duplicates, split into R (first 100k sets) and
+        # S (the other 150k), so that S holds edited copies of sets of R
+        spec = synth.short_sets(seed=1006, n=250_000)
+        spec.plant_frac, spec.plant_edits = 0.3, 2
+        c = synth.collection(spec)
+        cut = int(c.offsets[100_000])
+        cr = types.SimpleNamespace(n=100_000, offsets=c.offsets[:100_001].copy(), tokens=c.tokens[:cut].copy())
+        cs = types.SimpleNamespace(n=150_000, offsets=(c.offsets[100_000:] - c.offsets[100_000]).astype(np.uint64),
+                                   tokens=c.tokens[cut:].copy())
+        ts = [(4, 5), (7, 10), (3, 5), (1, 2)] if SIM != 3 else OVERLAP_THRESHOLDS
+        cfg = {"workload": name, "description": "R x S join: one seeded collection of 250k short sets "
+               "(lognormal(20, 0.6) clip [2,200], Zipf(1.0) over 1e6, seed 1006, 30% planted near-duplicates "
+               "with 2 edits) split into R = the first 100k and S = the other 150k; feeder candidates of R "
+               "against S",
+               "n_sets": cr.n + cs.n, "n_tokens": int(len(cr.tokens) + len(cs.tokens)),
+               "thresholds": [f"{p}/{q}" for p, q in ts]}
+        return cfg, [cr, cs], [((0, 1), p, q) for p, q in ts]
     if name == "short_sets":
         spec = synth.short_sets()
         ts = [(9, 10), (4, 5), (7, 10), (3, 5)]
@@ -90,6 +113,8 @@ def workload(name: str):
         label = "prefix-filter self-join, 1M sets mean 12, t in {0.7,0.8,0.9}"
     else:
         raise SystemExit(f"unknown workload {name}")
+    if SIM == 3:
+        ts = OVERLAP_THRESHOLDS
     c = synth.collection(spec)
     cfg = {"workload": name, "description": label, "n_sets": c.n, "n_tokens": int(len(c.tokens)),
            "size_law": f"{'lognormal' if spec.size_kind else 'uniform'}({spec.a},{spec.b}) clip [{spec.lo},{spec.hi}]",
@@ -98,7 +123,15 @@ def workload(name: str):
     return cfg, [c], [(0, p, q) for p, q in ts]
 
 
-def make_batches(colls, inst, all_pairs: bool = False):
+def coll_pair(colls, k):
+    """(R collection, S collection, self-join?) of an instance's collection index k, which is an
+    int for a self-join or a pair (r, s) for an R x S join."""
+    if isinstance(k, tuple):
+        return colls[k[0]], colls[k[1]], False
+    return colls[k], colls[k], True
+
+
+def make_batches(colls, inst, all_pairs: bool = False, ppjoin: bool = False):
     """CPU feeder (AllPairs prefix filter) candidates for every instance, or every pair r < s
     (brute force) when all_pairs: (ci, p, q, probes, offsets, cands)."""
     import paper_1812_09141_gb300 as ssj
@@ -106,12 +139,15 @@ def make_batches(colls, inst, all_pairs: bool = False):
     import synth
     out = []
     for ci, p, q in inst:
-        c = colls[ci]
+        cR, cS, selfj = coll_pair(colls, ci)
         if all_pairs:
-            b = synth.all_pairs_batch(c.n)
+            b = synth.all_pairs_batch(cR.n)
             pr, co, cands = b.probe_ids, b.cand_offsets, b.cand_ids
         else:
-            pr, co, cands = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=threads)
+            pr, co, cands = ssj.feeder_all(cR.offsets, cR.tokens, p, q, n_threads=threads, sim=SIM,
+                                           s_offsets=None if selfj else cS.offsets,
+                                           s_tokens=None if selfj else cS.tokens,
+                                           flags=ssj.SSJ_FEEDER_PPJOIN if ppjoin else 0)
         out.append((ci, p, q, pr, co, cands))
     return out
 
@@ -129,9 +165,9 @@ def oracle_accounting(colls, batches):
 
     def one(b):
         k, p, q, pr, co, ci = b
-        c = colls[k]
-        tr, cr, cs = oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci,
-                                         consumed=True)
+        cR, cS, selfj = coll_pair(colls, k)
+        tr, cr, cs = oracle.verify_batch(cR.offsets, cR.tokens, cS.offsets, cS.tokens, selfj, p, q, pr, co, ci,
+                                         consumed=True, sim=SIM)
         counts = np.diff(co.astype(np.int64))
         pr_max = np.zeros(len(pr), dtype=np.int64)
         if len(ci):
@@ -167,9 +203,9 @@ def cpu_baseline(colls, batches, min_seconds=10.0, max_seconds=30.0, max_call_pa
     pairs, total_t, reps = 0, 0.0, 0
     while total_t < min_seconds and reps < 1000:
         for k, p, q, pr, co, ci in calls:
-            c = colls[k]
+            cR, cS, selfj = coll_pair(colls, k)
             t0 = time.perf_counter()
-            oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci)
+            oracle.verify_batch(cR.offsets, cR.tokens, cS.offsets, cS.tokens, selfj, p, q, pr, co, ci, sim=SIM)
             total_t += time.perf_counter() - t0
             pairs += len(ci)
             if total_t > max_seconds:
@@ -212,8 +248,8 @@ def cpu_baseline_threads(colls, batches, min_seconds=5.0):
 
     def run(job):
         k, p, q, pr, co, ci = job
-        c = colls[k]
-        oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci)
+        cR, cS, selfj = coll_pair(colls, k)
+        oracle.verify_batch(cR.offsets, cR.tokens, cS.offsets, cS.tokens, selfj, p, q, pr, co, ci, sim=SIM)
 
     steps, t = 0, 0.0
     with cf.ThreadPoolExecutor(n_thr) as ex:
@@ -319,21 +355,28 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     cfg, colls, inst = workload(args.workload)
-    batches = make_batches(colls, inst, all_pairs=args.workload == "tiny")
+    batches = make_batches(colls, inst, all_pairs=args.workload == "tiny", ppjoin=args.ppjoin)
     pairs_step = sum(len(b[5]) for b in batches)
+    sim_flags = SIM << 8
 
     stream = torch.cuda.Stream(device=dev)
     ctx = ssj.ssj_create(local_rank, flags=ssj.SSJ_CTX_PROFILE, stream=stream.cuda_stream)
-    handles = [ssj.ssj_load_collection(ctx, c.offsets, c.tokens, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
-               for c in colls]
+    # renumbering by frequency is for self-joins; an R x S join keeps the raw token order
+    rs_join = any(isinstance(k, tuple) for k, _, _ in inst)
+    load_flags = ssj.SSJ_VALIDATE | (0 if rs_join else ssj.SSJ_RENUMBER_BY_FREQ)
+    handles = [ssj.ssj_load_collection(ctx, c.offsets, c.tokens, load_flags) for c in colls]
+
+    def hpair(k):
+        return (handles[k[0]], handles[k[1]]) if isinstance(k, tuple) else (handles[k], handles[k])
+
     dbs, outs, caps, keep = [], [], [], []
     for ci, p, q, pr, co, cands in batches:
         t_pr = torch.from_numpy(pr.astype(np.int32)).to(dev)
         t_co = torch.from_numpy(co.astype(np.int64)).to(dev)
         t_ci = torch.from_numpy(cands.astype(np.int32)).to(dev)
         keep.append((t_pr, t_co, t_ci))
-        h = handles[ci]
-        dbs.append(ssj.DeviceBatch(h, h, p, q, t_pr, t_co, t_ci, len(cands), n_probes=len(pr)))
+        hR, hS = hpair(ci)
+        dbs.append(ssj.DeviceBatch(hR, hS, p, q, t_pr, t_co, t_ci, len(cands), flags=sim_flags, n_probes=len(pr)))
         cap = max(min(len(cands), args.out_cap), 1)
         outs.append(torch.empty(cap * 3, dtype=torch.int32, device=dev))
         caps.append(cap)
@@ -450,13 +493,13 @@ def run_ours(args, rank, world, local_rank):
         tp = torch.from_numpy(pr.astype(np.uint32).view(np.int32)).pin_memory()
         tc = torch.from_numpy(co.astype(np.uint64).view(np.int64)).pin_memory()
         ti = torch.from_numpy(cands.astype(np.uint32).view(np.int32)).pin_memory()
-        pinned.append((handles[ci], p, q, tp.numpy().view(np.uint32), tc.numpy().view(np.uint64),
+        pinned.append((hpair(ci), p, q, tp.numpy().view(np.uint32), tc.numpy().view(np.uint64),
                        ti.numpy().view(np.uint32), (tp, tc, ti)))
     e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 20))
     e2e_t = e2e_single_t = 0.0
     h2d = sum(4 * len(b[3]) + 8 * (len(b[3]) + 1) + 4 * len(b[5]) for b in pinned)
     d2h = 0
-    step_batches = [(h, h, p, q, pr, co, ci, 0) for h, p, q, pr, co, ci, _keep in pinned]
+    step_batches = [(hr, hs, p, q, pr, co, ci, sim_flags) for (hr, hs), p, q, pr, co, ci, _keep in pinned]
     with torch.cuda.stream(stream):
         for it in range(e2e_steps + 1 if e2e_steps else 0):
             # one call for every instance of the step (one batched launch)
@@ -470,8 +513,8 @@ def run_ours(args, rank, world, local_rank):
             flush.fill_(1)
             stream.synchronize()
             t0 = time.perf_counter()
-            for h, p, q, pr, co, ci, _keep in pinned:
-                ssj.ssj_verify_batch(ctx, h, h, p, q, pr, co, ci)
+            for (hr, hs), p, q, pr, co, ci, _keep in pinned:
+                ssj.ssj_verify_batch(ctx, hr, hs, p, q, pr, co, ci, flags=sim_flags)
             dt_single = time.perf_counter() - t0
             if it > 0:  # the first pass sizes the staging buffers
                 e2e_t += dt
@@ -581,6 +624,54 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+def run_candgen(args):
+    """Self-join with candidate generation on the device (ssj_self_join) against the CPU feeder
+    (16 threads) followed by the same GPU verification, on the short-set and long-set
+    collections; CUDA events and wall clock; results must agree."""
+    import torch
+    import synth
+    import paper_1812_09141_gb300 as ssj
+    from paper_1812_09141_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    threads = max(1, min(16, os.cpu_count() or 1))
+    ctx = ssj.ssj_create(0)
+    out = {"workload": "candgen", "runs": []}
+    try:
+        for name, spec, ts in (("short_sets", synth.short_sets(), [(9, 10), (4, 5), (7, 10), (3, 5)]),
+                               ("long_sets", synth.long_sets(), [(9, 10), (4, 5)])):
+            c = synth.collection(spec)
+            h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens, ssj.SSJ_RENUMBER_BY_FREQ)
+            for p, q in ts:
+                row = {"collection": name, "t": f"{p}/{q}"}
+                for label, fl in (("device", 0), ("device_positional", ssj.SSJ_JOIN_POSITIONAL)):
+                    ssj.ssj_self_join(ctx, h, p, q, fl | ssj.SSJ_COUNT_ONLY)  # warm-up
+                    times = []
+                    for _ in range(3):
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        cnt, nc = ssj.ssj_self_join(ctx, h, p, q, fl | ssj.SSJ_COUNT_ONLY)
+                        times.append(time.perf_counter() - t0)
+                    row[label] = {"s": float(np.median(times)), "candidates": nc, "results": cnt,
+                                  "candidates_per_s": nc / float(np.median(times))}
+                t0 = time.perf_counter()
+                pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=threads)
+                t_feed = time.perf_counter() - t0
+                t0 = time.perf_counter()
+                cnt_cpu = ssj.ssj_verify_batch(ctx, h, h, p, q, pr, co, ci, flags=ssj.SSJ_COUNT_ONLY)
+                t_ver = time.perf_counter() - t0
+                row["cpu_feeder_then_gpu"] = {"feeder_s": t_feed, "verify_s": t_ver, "candidates": len(ci),
+                                              "results": cnt_cpu, "feeder_threads": threads}
+                if cnt_cpu != row["device"]["results"] or len(ci) != row["device"]["candidates"]:
+                    row["mismatch"] = True
+                out["runs"].append(row)
+            ssj.ssj_unload_collection(ctx, h)
+    finally:
+        ssj.ssj_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -594,9 +685,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--out-cap", type=int, default=1 << 26, help="most result triples kept per instance")
     ap.add_argument("--requests", type=int, default=1000, help="requests of the serving workload")
+    ap.add_argument("--sim", default="jaccard", choices=sorted(SIM_NAMES),
+                    help="similarity function of every instance (overlap uses thresholds 6, 8, 10, 12)")
+    ap.add_argument("--ppjoin", action="store_true", help="PPJoin positional filter in the CPU feeder")
     ap.add_argument("--granularity", default="", help="thread,lane,warp,block_threads: fixed setting instead of "
                     "the autotuner's (profiling runs)")
     args = ap.parse_args()
+    global SIM
+    SIM = SIM_NAMES[args.sim]
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
 
@@ -607,32 +703,54 @@ def main():
         if rank == 0:
             run_serving(args)
         return
+    if args.workload == "candgen" and args.impl == "ours":
+        if rank == 0:
+            run_candgen(args)
+        return
 
     if args.impl == "reference":
         if rank != 0:
             return
         cfg, colls, inst = workload(args.workload)
-        batches = make_batches(colls, inst, all_pairs=args.workload == "tiny")
+        batches = make_batches(colls, inst, all_pairs=args.workload == "tiny", ppjoin=args.ppjoin)
         import oracle
         pairs_step = sum(len(b[5]) for b in batches)
 
+        # each step verifies a bounded sample: a probe-prefix slice of every batch, about
+        # REF_STEP_PAIRS candidates in all, split in proportion to the batches' sizes
+        sample = []
+        for k, p, q, pr, co, ci in batches:
+            co64 = co.astype(np.int64)
+            want = max(1000, REF_STEP_PAIRS * len(ci) // max(pairs_step, 1))
+            b = len(pr) if co64[-1] <= want else max(1, int(np.searchsorted(co64, want, side="right")) - 1)
+            sample.append((k, p, q, pr[:b], co64[:b + 1].astype(np.uint64), ci[:int(co64[b])]))
+        sample_pairs = sum(len(x[5]) for x in sample)
+
         def one_step():
-            for k, p, q, pr, co, ci in batches:
-                c = colls[k]
-                oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q, pr, co, ci)
+            for k, p, q, pr, co, ci in sample:
+                cR, cS, selfj = coll_pair(colls, k)
+                oracle.verify_batch(cR.offsets, cR.tokens, cS.offsets, cS.tokens, selfj, p, q, pr, co, ci, sim=SIM)
         one_step()  # warm-up
         t0 = time.perf_counter()
         for _ in range(args.steps):
             one_step()
         dt = time.perf_counter() - t0
-        v = pairs_step * args.steps / dt
+        v = sample_pairs * args.steps / dt
+        whole = sample_pairs == pairs_step
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-                "data": "synthetic", "config": cfg,
+                "data": "synthetic",
+                "config": dict(cfg, pairs_per_step=pairs_step, instances_per_launch=len(batches),
+                               similarity=args.sim,
+                               candidates="AllPairs prefix filter" + (" + PPJoin" if args.ppjoin else "")
+                               if args.workload != "tiny" else "all pairs"),
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"{args.steps} full steps of the workload ({pairs_step} pairs each), "
-                                           f"after one warm-up step"},
+                                 "sample": (f"{args.steps} full steps of the workload ({pairs_step} pairs each)"
+                                            if whole else
+                                            f"{args.steps} steps of a fixed sample of {sample_pairs} of the "
+                                            f"{pairs_step} candidate pairs of a step (a probe-prefix slice of each "
+                                            f"of the {len(batches)} batches)") + ", after one warm-up step"},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -653,6 +771,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict(res["cfg"], pairs_per_step=pairs_step, instances_per_launch=len(batches),
+                           similarity=args.sim, candidates="AllPairs prefix filter" + (" + PPJoin" if args.ppjoin else "")
+                           if args.workload != "tiny" else "all pairs",
                            l2=(f"flushed before every timed step ({args.l2_flush_mb} MiB write)"
                                if args.l2_flush_mb else "not flushed (profiling run)"),
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU",

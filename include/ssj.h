@@ -156,6 +156,9 @@ ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, ui
 #define SSJ_SIM_COSINE 0x200u
 #define SSJ_SIM_OVERLAP 0x300u
 #define SSJ_SIM_MASK 0x300u
+#define SSJ_JOIN_POSITIONAL 0x400u  /* ssj_self_join: drop a candidate at a matching prefix token
+                                       when min(i, j) + 1 + min(|r|-i-1, |s|-j-1) (i, j: the token's
+                                       positions) is below the pair's equivalent overlap */
 
 typedef struct {
     ssj_coll R, S;                /* R == S: self-join */
@@ -245,6 +248,35 @@ ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batch, ssj_trip
  */
 ssj_status ssj_verify_batch_noalloc(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* d_out, uint64_t cap,
                                     uint64_t* d_count, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Self-join with candidate generation on the device (the paper's future
+ * work, Section 6: the filtering phase on the GPU as well)
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Join a loaded collection with itself at threshold t = p/q (flags may
+ * select the similarity function, SSJ_SIM_*): the prefix filter and
+ * inverted-index probing of algorithm ALL (Sections 2.2.3, 2.2.4, 3.1) run
+ * on the device (sets ordered by size; each set's prefix indexed; each
+ * probe matched against the earlier sets' prefix entries that pass the
+ * length filter, SSJ_JOIN_POSITIONAL adding the positional bound;
+ * candidates deduplicated), then the candidates are verified by the same
+ * launch as ssj_verify_batch, without a host round trip.  The candidates
+ * are those of the CPU feeder (ssj_feeder.h) for the same function and
+ * threshold.  Results as for ssj_verify_batch of a self-join: (min id, max
+ * id, overlap) triples in the caller's ids, to out (host memory, or device
+ * memory with SSJ_DEVICE_PTRS), at most cap; *n_out receives the count
+ * (SSJ_ENOMEM if it exceeds cap), *n_candidates (may be NULL) the number
+ * of candidates verified.  Flags: SSJ_SIM_*, SSJ_JOIN_POSITIONAL,
+ * SSJ_COUNT_ONLY, SSJ_SORTED, SSJ_DEVICE_PTRS, SSJ_FORCE_*.  Token values
+ * must stay below 2^30 (load with SSJ_RENUMBER_BY_FREQ, which the prefix
+ * filter wants anyway).  Allocates its scratch (the prefix index, a hash
+ * set of candidate pairs and the candidate list) for the call.
+ * Errors: SSJ_EINVAL, SSJ_ENOTFOUND, SSJ_ENOMEM, SSJ_EDEVICE.
+ */
+ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uint32_t q, uint32_t flags, ssj_triple* out,
+                         uint64_t cap, uint64_t* n_out, uint64_t* n_candidates);
 
 /* ------------------------------------------------------------------------
  * Batched instances: many independent joins in one launch

@@ -42,6 +42,7 @@ SSJ_SIM_COSINE = 0x200
 SSJ_SIM_OVERLAP = 0x300
 SSJ_SIM_MASK = 0x300
 SSJ_FEEDER_PPJOIN = 0x1
+SSJ_JOIN_POSITIONAL = 0x400
 # context flags
 SSJ_CTX_PROFILE = 0x1
 
@@ -113,6 +114,7 @@ SIGNATURES = {
     "ssj_multi_launch": (_INT, [_VP, _VP, _VP]),
     "ssj_multi_graph_launch": (_INT, [_VP, _VP, _VP]),
     "ssj_multi_destroy": (None, [_VP, _VP]),
+    "ssj_self_join": (_INT, [_VP, _U32, _U32, _U32, _U32, _VP, _U64, _P(_U64), _P(_U64)]),
     "ssj_verify_batches": (_INT, [_VP, _P(ssj_batch), _U32, _P(_VP), _P(_U64), _P(_U64)]),
     "ssj_multi_autotune": (_INT, [_VP, _VP, _VP, _U32, _P(ssj_tune_result)]),
     "ssj_read_bandwidth": (_INT, [_VP, _U64, _U32, _P(ctypes.c_double)]),
@@ -264,6 +266,28 @@ def ssj_verify_batch(ctx: int, R: int, S: int, p: int, q: int, probe_ids, cand_o
     st = lib().ssj_verify_batch(ctx, ctypes.byref(hb.batch), res.ctypes.data, cap, ctypes.byref(n_out))
     _check(ctx, st)
     return res[:n_out.value]
+
+
+def ssj_self_join(ctx: int, coll: int, p: int, q: int, flags: int = 0, cap: int | None = None, out=None):
+    """Self-join with device candidate generation.  Host mode: returns (structured triples,
+    n_candidates), or (count, n_candidates) with SSJ_COUNT_ONLY.  With SSJ_DEVICE_PTRS, `out` is a
+    device tensor/address of `cap` triples and (count, n_candidates) is returned."""
+    n_out, n_c = ctypes.c_uint64(), ctypes.c_uint64()
+    if flags & SSJ_COUNT_ONLY:
+        _check(ctx, lib().ssj_self_join(ctx, coll, p, q, flags, None, 0, ctypes.byref(n_out), ctypes.byref(n_c)))
+        return n_out.value, n_c.value
+    if flags & SSJ_DEVICE_PTRS:
+        _check(ctx, lib().ssj_self_join(ctx, coll, p, q, flags, _devptr(out), int(cap), ctypes.byref(n_out),
+                                        ctypes.byref(n_c)))
+        return n_out.value, n_c.value
+    if cap is None:
+        # ask for the count first (a COUNT_ONLY pass), then fetch
+        cnt, _ = ssj_self_join(ctx, coll, p, q, flags | SSJ_COUNT_ONLY)
+        cap = max(cnt, 1)
+    res = np.empty(max(int(cap), 1), dtype=TRIPLE_DTYPE)
+    _check(ctx, lib().ssj_self_join(ctx, coll, p, q, flags, res.ctypes.data, int(cap), ctypes.byref(n_out),
+                                    ctypes.byref(n_c)))
+    return res[:n_out.value], n_c.value
 
 
 def ssj_verify_batches(ctx: int, batches: list, caps: list | None = None):

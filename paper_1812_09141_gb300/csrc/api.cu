@@ -50,6 +50,8 @@ struct Collection {
     uint32_t* d_toks = nullptr;  // n_chunks * 4 tokens
     uint2* d_desc = nullptr;
     bool renumbered = false;
+    uint32_t max_len = 0;        // longest set
+    uint32_t vocab = 0;          // largest token on the device + 1
     uint32_t busy = 0;           // submitted batches not yet collected
     DevColl dev() const {
         DevColl d;
@@ -467,6 +469,9 @@ extern "C" ssj_status ssj_load_collection(ssj_ctx* ctx, const uint64_t* offsets,
     c.n_sets = n_sets;
     c.n_tokens = total;
     c.renumbered = (flags & SSJ_RENUMBER_BY_FREQ) != 0;
+    for (uint32_t i = 0; i < n_sets; ++i)
+        c.max_len = std::max<uint32_t>(c.max_len, (uint32_t)std::min<uint64_t>(offsets[i + 1] - offsets[i], 0xFFFFFFFFu));
+    for (uint64_t t = 0; t < total; ++t) c.vocab = std::max<uint32_t>(c.vocab, src[t] == 0xFFFFFFFFu ? src[t] : src[t] + 1);
     auto cleanup = [&]() {
         cudaFree(d_offs);
         cudaFree(d_raw);
@@ -804,6 +809,190 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
         if ((batches[i].flags & SSJ_SORTED) && !(batches[i].flags & SSJ_COUNT_ONLY))
             std::sort(outs[i], outs[i] + std::min(counts[i], caps[i]), triple_less);
     if (short_cap) return fail(ctx, SSJ_ENOMEM, "a batch has more result pairs than its capacity (see n_outs)");
+    return SSJ_OK;
+}
+
+// ===========================================================================
+// Self-join with candidates generated on the device
+// ===========================================================================
+
+extern "C" ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uint32_t q, uint32_t flags,
+                                    ssj_triple* out, uint64_t cap, uint64_t* n_out, uint64_t* n_candidates) {
+    if (!ctx || !n_out) return fail(ctx, SSJ_EINVAL, "NULL argument");
+    const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_SIM_MASK | SSJ_JOIN_POSITIONAL |
+                           SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE;
+    if (flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown flag");
+    if (cap && !out && !(flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output with cap > 0");
+    // threshold and collection checks through the batch path's resolve()
+    ssj_batch probe_b;
+    memset(&probe_b, 0, sizeof(probe_b));
+    probe_b.R = probe_b.S = coll;
+    probe_b.p = p;
+    probe_b.q = q;
+    probe_b.flags = flags & (SSJ_SIM_MASK | SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE);
+    Collection *R, *S;
+    ssj_status st = resolve(ctx, &probe_b, &R, &S);
+    if (st != SSJ_OK) return st;
+    const Collection& C = *R;
+    if (C.vocab > (1u << 30)) return fail(ctx, SSJ_EINVAL, "token values above 2^30: load with SSJ_RENUMBER_BY_FREQ");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const uint32_t n = C.n_sets;
+    std::vector<void*> mem;
+    auto release = [&]() {
+        for (void* m : mem) cudaFree(m);
+        mem.clear();
+    };
+    auto alloc = [&](size_t bytes) -> void* {
+        void* m = nullptr;
+        if (cudaMalloc(&m, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        mem.push_back(m);
+        return m;
+    };
+    CandgenIndex ix;
+    const uint64_t scan_n = std::max<uint64_t>((uint64_t)C.max_len + 2, (uint64_t)C.vocab + 1);
+    ix.size_hist = static_cast<uint64_t*>(alloc(8ull * (C.max_len + 2)));
+    ix.order = static_cast<uint32_t*>(alloc(4ull * n));
+    ix.rank = static_cast<uint32_t*>(alloc(4ull * n));
+    ix.tcnt = static_cast<uint64_t*>(alloc(8ull * (C.vocab + 1)));
+    ix.toff = static_cast<uint64_t*>(alloc(8ull * (C.vocab + 1)));
+    ix.scan_scratch = static_cast<uint64_t*>(alloc(8ull * scan_scratch_words(scan_n)));
+    ix.total = static_cast<uint64_t*>(alloc(8));
+    ix.post = nullptr;
+    uint32_t* d_err = static_cast<uint32_t*>(alloc(4));
+    if (!ix.size_hist || !ix.order || !ix.rank || !ix.tcnt || !ix.toff || !ix.scan_scratch || !ix.total || !d_err) {
+        release();
+        return fail(ctx, SSJ_ENOMEM, "candidate generation index");
+    }
+    CandgenInput in;
+    memset(&in, 0, sizeof(in));
+    in.toks4 = reinterpret_cast<const uint4*>(C.d_toks);
+    in.desc = C.d_desc;
+    in.n = n;
+    in.max_len = C.max_len;
+    in.vocab = C.vocab;
+    in.sim = (flags & SSJ_SIM_MASK) >> 8;
+    in.p = p;
+    in.q = q;
+    in.positional = (flags & SSJ_JOIN_POSITIONAL) ? 1u : 0u;
+    cudaError_t e = cudaMemsetAsync(d_err, 0, 4, s);
+    in.stage = 0;
+    if (e == cudaSuccess) e = candgen_run(in, s, ctx->num_sms, &ix, ctx->h_count);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(ctx, e, "candidate generation (index)");
+    }
+    const uint64_t entries = *ctx->h_count;
+    ix.post = static_cast<uint4*>(alloc(16ull * entries));
+    if (!ix.post) {
+        release();
+        return fail(ctx, SSJ_ENOMEM, "prefix index of %llu entries", (unsigned long long)entries);
+    }
+    in.stage = 1;
+    e = candgen_run(in, s, ctx->num_sms, &ix, ctx->h_count);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(ctx, e, "candidate generation (count)");
+    }
+    const uint64_t bound = *ctx->h_count;  // entries that can yield a candidate
+    uint64_t tsize = 1024;
+    while (tsize < 2 * bound) tsize <<= 1;
+    const uint64_t group_cap = (uint64_t)n + bound / 224 + 1;
+    in.table = static_cast<unsigned long long*>(alloc(8ull * tsize));
+    in.table_mask = tsize - 1;
+    in.out.probe_ids = static_cast<uint32_t*>(alloc(4ull * group_cap));
+    in.out.cand_offsets = static_cast<uint64_t*>(alloc(8ull * (group_cap + 1)));
+    in.out.cand_ids = static_cast<uint32_t*>(alloc(4ull * std::max<uint64_t>(bound, 1)));
+    in.out.packed = static_cast<unsigned long long*>(alloc(8));
+    in.out.group_cap = group_cap;
+    in.out.cand_cap = bound;
+    in.out.err = d_err;
+    if (!in.table || !in.out.probe_ids || !in.out.cand_offsets || !in.out.cand_ids || !in.out.packed) {
+        release();
+        return fail(ctx, SSJ_ENOMEM, "candidate generation output (%llu entries)", (unsigned long long)bound);
+    }
+    in.stage = 2;
+    e = candgen_run(in, s, ctx->num_sms, &ix, ctx->h_count);
+    uint32_t derr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&derr, d_err, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(ctx, e, "candidate generation (probe)");
+    }
+    if (derr) {
+        release();
+        return fail(ctx, SSJ_EDEVICE, "candidate generation: an output capacity was exceeded (code %u)", derr);
+    }
+    const uint64_t packed = *ctx->h_count;
+    const uint64_t groups = packed >> 40, total = packed & ((1ull << 40) - 1);
+    if (n_candidates) *n_candidates = total;
+    e = cudaMemcpy(in.out.cand_offsets + groups, &total, 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(ctx, e, "candidate offsets");
+    }
+    // index and hash table are no longer needed; verify the generated batch
+    ssj_batch b;
+    memset(&b, 0, sizeof(b));
+    b.R = b.S = coll;
+    b.p = p;
+    b.q = q;
+    b.n_probes = (uint32_t)groups;
+    b.probe_ids = in.out.probe_ids;
+    b.cand_offsets = in.out.cand_offsets;
+    b.cand_ids = in.out.cand_ids;
+    b.n_cands = total;
+    b.flags = (flags & ~(SSJ_JOIN_POSITIONAL | SSJ_DEVICE_PTRS | SSJ_SORTED)) | SSJ_DEVICE_PTRS;
+    if (groups > 0xFFFFFFFFull) {
+        release();
+        return fail(ctx, SSJ_EINVAL, "too many candidate groups");
+    }
+    const bool count_only = (flags & SSJ_COUNT_ONLY) != 0;
+    const bool dev_out = (flags & SSJ_DEVICE_PTRS) != 0;
+    ssj_triple* d_out = nullptr;
+    uint64_t d_cap = 0;
+    if (!count_only) {
+        if (dev_out) {
+            d_out = out;
+            d_cap = cap;
+        } else {
+            d_cap = std::min<uint64_t>(cap, total);
+            d_out = static_cast<ssj_triple*>(alloc(sizeof(ssj_triple) * std::max<uint64_t>(d_cap, 1)));
+            if (!d_out) {
+                release();
+                return fail(ctx, SSJ_ENOMEM, "join output");
+            }
+        }
+    }
+    uint64_t count = 0;
+    st = ssj_verify_batch(ctx, &b, d_out, d_cap, &count);
+    *n_out = count;
+    if (st != SSJ_OK && st != SSJ_ENOMEM) {
+        release();
+        return st;
+    }
+    if (!count_only) {
+        const uint64_t n_copy = std::min(count, cap);
+        if (dev_out) {
+            if ((flags & SSJ_SORTED) && n_copy) {
+                std::vector<ssj_triple> h(n_copy);
+                e = cudaMemcpy(h.data(), out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost);
+                std::sort(h.begin(), h.end(), triple_less);
+                if (e == cudaSuccess) e = cudaMemcpy(out, h.data(), sizeof(ssj_triple) * n_copy, cudaMemcpyHostToDevice);
+            }
+        } else if (n_copy) {
+            e = cudaMemcpy(out, d_out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && (flags & SSJ_SORTED)) std::sort(out, out + n_copy, triple_less);
+        }
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(ctx, e, "join results");
+        }
+    }
+    release();
+    if (count > cap && !count_only)
+        return fail(ctx, SSJ_ENOMEM, "%llu result pairs, room for %llu", (unsigned long long)count,
+                    (unsigned long long)cap);
     return SSJ_OK;
 }
 

@@ -159,4 +159,15 @@ size_t layout_scratch_words(uint32_t n) {
     return (size_t)n + 1 + (n + kScanBlock - 1) / kScanBlock + 1;
 }
 
+size_t scan_scratch_words(uint64_t n) { return (n + kScanBlock - 1) / kScanBlock + 1; }
+
+cudaError_t exclusive_scan_u64(uint64_t* data, uint64_t n, uint64_t* scratch, uint64_t* total, cudaStream_t st) {
+    if (n == 0) return cudaMemsetAsync(total, 0, sizeof(uint64_t), st);
+    const uint64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    scan_blocks<<<(unsigned)nb, kScanBlock, 0, st>>>(data, n, scratch);
+    scan_sums<<<1, kScanBlock, 0, st>>>(scratch, nb, total);
+    scan_add<<<(unsigned)nb, kScanBlock, 0, st>>>(data, n, scratch);
+    return cudaGetLastError();
+}
+
 }  // namespace ssj

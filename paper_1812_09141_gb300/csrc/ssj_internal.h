@@ -157,6 +157,54 @@ cudaError_t prepare_verify(uint32_t block_threads);
 cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uint32_t block_threads,
                           cudaEvent_t* ev = nullptr);
 
+// Exclusive prefix sum of n 64-bit values in place on st; *total (device)
+// receives the sum.  scratch holds scan_scratch_words(n) values.
+size_t scan_scratch_words(uint64_t n);
+cudaError_t exclusive_scan_u64(uint64_t* data, uint64_t n, uint64_t* scratch, uint64_t* total, cudaStream_t st);
+
+// Device candidate generation of a self-join (candgen.cu).  Scratch of the
+// prefix index, sized by the caller: size_hist max_len + 2 words, order and
+// rank n each, tcnt and toff vocab + 1 words each, scan_scratch
+// scan_scratch_words(max(max_len + 2, vocab + 1)), total 1 word, post one
+// uint4 per index entry (known after stage 0).
+struct CandgenIndex {
+    uint64_t* size_hist;
+    uint32_t* order;
+    uint32_t* rank;
+    uint64_t* tcnt;
+    uint64_t* toff;
+    uint64_t* scan_scratch;
+    uint64_t* total;
+    uint4* post;
+};
+
+struct CandgenOutput {
+    uint32_t* probe_ids;          // group -> probe set id
+    uint64_t* cand_offsets;       // group -> first candidate
+    uint32_t* cand_ids;
+    unsigned long long* packed;   // groups << 40 | candidates
+    uint64_t group_cap, cand_cap;
+    uint32_t* err;                // ERR_GUARD if a capacity was exceeded
+};
+
+struct CandgenInput {
+    const uint4* toks4;
+    const uint2* desc;
+    uint32_t n, max_len, vocab;   // vocab: largest token + 1
+    uint32_t sim, p, q;           // SIM_*, t = p/q
+    uint32_t positional;          // positional bound at the matching prefix token
+    int stage;                    // 0: order + token counts; 1: lists + filtered count; 2: probe and emit
+    unsigned long long* table;    // stage 2: hash set of (probe position, candidate position)
+    uint64_t table_mask;          // its size - 1 (a power of two minus one)
+    CandgenOutput out;
+};
+
+// Run one stage on st and wait for it; *host_word (pinned) receives stage
+// 0: index entries, stage 1: entries passing the filters (an upper bound of
+// the candidates), stage 2: the packed group / candidate counter.
+cudaError_t candgen_run(const CandgenInput& in, cudaStream_t st, int num_sms, CandgenIndex* ix,
+                        uint64_t* host_word);
+
 // One launch of the read-bandwidth probe: `passes` sweeps over bytes (a
 // multiple of 16) at buf, on st; sink is a device word the kernel may write.
 cudaError_t read_probe(const void* buf, uint64_t bytes, uint32_t passes, uint32_t* sink, int num_sms,

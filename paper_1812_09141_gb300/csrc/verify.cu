@@ -59,6 +59,7 @@ constexpr int kBlockD = 8;                         // merge steps per thread per
 constexpr uint32_t kBlockRCap = 4096;              // r kept whole in shared memory up to this
 constexpr uint32_t kFlatGrab = 4;                  // 32-pair chunks taken per dynamic grab in phase 3
 constexpr uint32_t kCont = 64;                     // parked pairs per warp in phase 3
+constexpr int kPlanThreads = 256;                  // plan kernel block size
 
 // A parked pair with its merge state.
 struct ContEntry {
@@ -531,23 +532,6 @@ __device__ __forceinline__ uint32_t probe_bin(const VerifyArgs& a, uint32_t flag
     return key <= a.warp_max_key ? 1u : 2u;
 }
 
-// Reserve `want` slots of a shared counter for every lane of the warp with
-// one atomic (all 32 lanes call this); returns this lane's first slot.
-__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* counter, unsigned long long want,
-                                                           int lane) {
-    unsigned long long incl = want;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const unsigned long long y = __shfl_up_sync(kFull, incl, off);
-        if (lane >= off) incl += y;
-    }
-    const unsigned long long total = __shfl_sync(kFull, incl, 31);
-    unsigned long long base = 0;
-    if (lane == 31 && total) base = atomicAdd(counter, total);
-    base = __shfl_sync(kFull, base, 31);
-    return base + incl - want;
-}
-
 // Instance fields read by the plan kernel (from the kernel parameters for a
 // one-batch launch, else from the device table).
 struct PlanInst {
@@ -597,16 +581,26 @@ __device__ __forceinline__ PlanInst plan_inst(const VerifyArgs& a, uint32_t i) {
 // the compacted list (a warp's range is padded to whole 32-slot chunks, so
 // a chunk never mixes instances), longer probes become work items.
 // -------------------------------------------------------------------------
-__global__ void plan_kernel(VerifyArgs a) {
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
+    constexpr int kPlanWarps = kPlanThreads / 32;
+    // per-warp list sizes and the CTA's list bases, double-buffered by round
+    // parity so that a warp one round ahead never overwrites what others read
+    __shared__ unsigned long long s_tot[2][3][kPlanWarps];
+    __shared__ unsigned long long s_base[2][3];
     const int lane = threadIdx.x & 31;
-    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int warp = threadIdx.x >> 5;
     if (blockIdx.x == 0) {
         if (!a.table && threadIdx.x == 0) a.table_out[0] = a.single;
         for (uint32_t i = threadIdx.x; i < a.n_inst; i += blockDim.x)
             *(a.table ? a.table[i].count : a.single.count) = 0ull;
     }
-    for (uint32_t g = gw; g < a.n_tiles; g += n_warps) {
+    // Rounds are uniform over the CTA: warp w of the CTA takes tile g0 + w.
+    // The three lists (short pairs, warp/lane items, block items) are
+    // reserved with one atomic per CTA and round, not per warp.
+    uint32_t par = 0;
+    for (uint32_t g0 = blockIdx.x * kPlanWarps; g0 < a.n_tiles; g0 += gridDim.x * kPlanWarps, par ^= 1u) {
+        const uint32_t g = g0 + (uint32_t)warp;
+        const bool tile_ok = g < a.n_tiles;
         // instance owning tile g: the last one whose tile_base <= g
         uint32_t inst = 0;
         if (a.table) {
@@ -625,7 +619,7 @@ __global__ void plan_kernel(VerifyArgs a) {
         uint64_t c0 = 0, n = 0;
         uint32_t r = 0, bin = 0;
         uint2 rdesc = make_uint2(0, 0);
-        if (k < I.n_probes) {
+        if (tile_ok && k < I.n_probes) {
             c0 = I.cand_offsets[k];
             const uint64_t c1 = I.cand_offsets[k + 1];
             if ((k == 0 && c0 != 0) || (k + 1 == I.n_probes && c1 != I.n_cands) || c1 < c0 || c1 > I.n_cands) {
@@ -655,9 +649,40 @@ __global__ void plan_kernel(VerifyArgs a) {
         }
         const unsigned long long ttotal = __shfl_sync(kFull, tincl, 31);
         const unsigned long long tpadded = (ttotal + 31) & ~31ull;
-        unsigned long long tbase0 = 0;
-        if (lane == 31 && tpadded) tbase0 = atomicAdd(&a.ctr->thread_pairs, tpadded);
-        tbase0 = __shfl_sync(kFull, tbase0, 31);
+        // work item counts (lane items share the warp item list, marked by mode 1)
+        const uint32_t wc = bin == 3 ? a.lane_item_cands : a.warp_item_cands, bc = a.block_item_cands;
+        const unsigned long long wn = (bin == 1 || bin == 3) ? (n + wc - 1) / wc : 0;
+        const unsigned long long bn = (bin == 2) ? (n + bc - 1) / bc : 0;
+        unsigned long long wincl = wn, bincl = bn;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long yw = __shfl_up_sync(kFull, wincl, off);
+            const unsigned long long yb = __shfl_up_sync(kFull, bincl, off);
+            if (lane >= off) { wincl += yw; bincl += yb; }
+        }
+        if (lane == 31) {
+            s_tot[par][0][warp] = tpadded;
+            s_tot[par][1][warp] = wincl;
+            s_tot[par][2][warp] = bincl;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            unsigned long long sum = 0;
+#pragma unroll
+            for (int w = 0; w < kPlanWarps; ++w) sum += s_tot[par][threadIdx.x][w];
+            unsigned long long* ctr = threadIdx.x == 0 ? &a.ctr->thread_pairs
+                                                       : (threadIdx.x == 1 ? &a.ctr->warp_items : &a.ctr->block_items);
+            s_base[par][threadIdx.x] = sum ? atomicAdd(ctr, sum) : 0ull;
+        }
+        __syncthreads();
+        unsigned long long tbase0 = s_base[par][0], wbase = s_base[par][1], bbase = s_base[par][2];
+        for (int w = 0; w < warp; ++w) {
+            tbase0 += s_tot[par][0][w];
+            wbase += s_tot[par][1][w];
+            bbase += s_tot[par][2][w];
+        }
+        wbase += wincl - wn;  // this lane's first item
+        bbase += bincl - bn;
         if (tbase0 + tpadded > a.pair_cap) {  // cannot happen with a sized workspace
             if (lane == 0 && tpadded) atomicOr(&a.ctr->err, ERR_GUARD);
         } else {
@@ -693,11 +718,7 @@ __global__ void plan_kernel(VerifyArgs a) {
             }
         }
         // longer probes: work items of up to warp_item_cands / lane_item_cands /
-        // block_item_cands candidates (lane items share the warp item list,
-        // marked by mode 1)
-        const uint32_t wc = bin == 3 ? a.lane_item_cands : a.warp_item_cands, bc = a.block_item_cands;
-        const unsigned long long wn = (bin == 1 || bin == 3) ? (n + wc - 1) / wc : 0;
-        const unsigned long long wbase = warp_reserve(&a.ctr->warp_items, wn, lane);
+        // block_item_cands candidates
         for (unsigned long long it = 0; it < wn; ++it) {
             if (wbase + it >= a.warp_item_cap) { atomicOr(&a.ctr->err, ERR_GUARD); break; }
             const uint64_t s0 = c0 + it * wc;
@@ -709,8 +730,6 @@ __global__ void plan_kernel(VerifyArgs a) {
             wi.pad = bin == 3 ? 1u : 0u;
             a.warp_items[wbase + it] = wi;
         }
-        const unsigned long long bn = (bin == 2) ? (n + bc - 1) / bc : 0;
-        const unsigned long long bbase = warp_reserve(&a.ctr->block_items, bn, lane);
         for (unsigned long long it = 0; it < bn; ++it) {
             if (bbase + it >= a.block_item_cap) { atomicOr(&a.ctr->err, ERR_GUARD); break; }
             const uint64_t s0 = c0 + it * bc;
@@ -1126,9 +1145,10 @@ cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uin
     }
     // the plan kernel also runs for empty batches: it clears the instances' counts
     {
-        const int threads = 256;
+        // one round of tiles per CTA and round (kPlanThreads / 32 tiles), one wave of CTAs
+        const int threads = kPlanThreads;
         uint64_t blocks = ((uint64_t)a.n_tiles * 32 + threads - 1) / threads;
-        const uint64_t max_blocks = (uint64_t)num_sms * 8;
+        const uint64_t max_blocks = (uint64_t)num_sms * 4;
         if (blocks > max_blocks) blocks = max_blocks;
         if (blocks < 1) blocks = 1;
         plan_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);

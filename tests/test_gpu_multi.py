@@ -233,9 +233,11 @@ def test_verify_batches_host_equals_single_calls(ctx):
     fb = synth.Batch(*ssj.feeder_all(short.offsets, short.tokens, 3, 5, n_threads=4))
     rb = synth.random_batch(5, cR.n, c.n, 200, 40)
     empty = synth.Batch(np.zeros(0, np.uint32), np.zeros(1, np.uint64), np.zeros(0, np.uint32))
-    batches = [(h, h, 4, 5, *ap, 0), (h, h, 3, 5, *ap, ssj.SSJ_SIM_COSINE | ssj.SSJ_SORTED),
-               (hs, hs, 3, 5, *fb, 0), (hR, h, 1, 3, *rb, 0), (h, h, 1, 2, *ap, ssj.SSJ_COUNT_ONLY),
-               (h, h, 1, 2, *empty, 0), (h, h, 7, 1, *ap, ssj.SSJ_SIM_OVERLAP)]
+    arrs = lambda b: (b.probe_ids, b.cand_offsets, b.cand_ids)
+    batches = [(h, h, 4, 5, *arrs(ap), 0), (h, h, 3, 5, *arrs(ap), ssj.SSJ_SIM_COSINE | ssj.SSJ_SORTED),
+               (hs, hs, 3, 5, *arrs(fb), 0), (hR, h, 1, 3, *arrs(rb), 0),
+               (h, h, 1, 2, *arrs(ap), ssj.SSJ_COUNT_ONLY), (h, h, 1, 2, *arrs(empty), 0),
+               (h, h, 7, 1, *arrs(ap), ssj.SSJ_SIM_OVERLAP)]
     try:
         got = ssj.ssj_verify_batches(ctx, batches)
         for i, (R, S, p, q, pr, co, ci, fl) in enumerate(batches):
