@@ -583,13 +583,15 @@ def run_serving(args):
             at += b - a + 1
             offs[:] = co[a:b + 1] - co[a]
             cands = ci[int(co[a]):int(co[b])]
-            reqs.append((h, h, p, q, pr[a:b], offs, cands, float(arrivals[i]), 0))
+            # request buffers stay untouched until the replay has collected every result
+            reqs.append((h, h, p, q, pr[a:b], offs, cands, float(arrivals[i]), ssj.SSJ_KEEP_INPUTS))
             sizes.append(len(cands))
         return reqs, np.array(sizes)
 
     out = {"workload": "serving", "collection": "1M sets, lognormal(12, 0.6) clip [2,200], Zipf(1.0) over 2e6",
            "requests": n_req, "request_sizes": "log-uniform [1e3, 1e7] pairs, slices of the CPU filter's "
-           "candidates at t in {0.7, 0.8, 0.9}, in pinned host memory", "runs": []}
+           "candidates at t in {0.7, 0.8, 0.9}, in pinned host memory kept until collected (SSJ_KEEP_INPUTS)",
+           "runs": []}
     for budget_gb in (4, 1):
         ctx = ssj.ssj_create(0, mem_budget_bytes=budget_gb << 30, max_inflight=8)
         try:

@@ -156,6 +156,9 @@ ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, ui
 #define SSJ_SIM_COSINE 0x200u
 #define SSJ_SIM_OVERLAP 0x300u
 #define SSJ_SIM_MASK 0x300u
+#define SSJ_KEEP_INPUTS 0x800u      /* ssj_submit: the caller keeps pinned host inputs unchanged
+                                       until the ticket is done, so the call does not wait for
+                                       their host-to-device copies (ignored for pageable inputs) */
 #define SSJ_JOIN_POSITIONAL 0x400u  /* ssj_self_join: drop a candidate at a matching prefix token
                                        when min(i, j) + 1 + min(|r|-i-1, |s|-j-1) (i, j: the token's
                                        positions) is below the pair's equivalent overlap */
@@ -359,9 +362,13 @@ ssj_status ssj_device_error(ssj_ctx* ctx, uint32_t* code);
  * ------------------------------------------------------------------------ */
 
 /*
- * Admit a batch.  Host inputs are copied into a library slot before the
- * call returns, so the caller may reuse its arrays at once (with
- * SSJ_DEVICE_PTRS the caller keeps them alive until ssj_poll reports done).
+ * Admit a batch.  Host inputs are copied to the device before the call
+ * returns (pinned arrays straight from the caller's memory, pageable ones
+ * through the slot's pinned staging), so the caller may reuse its arrays at
+ * once; with SSJ_KEEP_INPUTS the caller instead keeps pinned arrays
+ * unchanged until the ticket is done and the call does not wait for their
+ * copies (with SSJ_DEVICE_PTRS the caller keeps the arrays alive until
+ * ssj_poll reports done).
  * The batch runs on its own stream, overlapping with other admitted
  * batches.  Returns SSJ_EAGAIN when every slot is busy or the batch does not
  * fit the remaining memory budget; SSJ_EINVAL when it could never fit.

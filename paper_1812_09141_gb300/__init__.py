@@ -43,6 +43,7 @@ SSJ_SIM_OVERLAP = 0x300
 SSJ_SIM_MASK = 0x300
 SSJ_FEEDER_PPJOIN = 0x1
 SSJ_JOIN_POSITIONAL = 0x400
+SSJ_KEEP_INPUTS = 0x800
 # context flags
 SSJ_CTX_PROFILE = 0x1
 

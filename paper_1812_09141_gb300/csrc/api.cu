@@ -250,7 +250,7 @@ ssj_status resolve(ssj_ctx* ctx, const ssj_batch* b, Collection** R, Collection*
     if (b->R != b->S && (ir->second.renumbered || is->second.renumbered))
         return fail(ctx, SSJ_EINVAL, "renumbered collections can only be self-joined");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_EMIT_ALL | SSJ_FORCE_THREAD |
-                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_SIM_MASK;
+                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_SIM_MASK | SSJ_KEEP_INPUTS;
     if (b->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown batch flag");
     const uint32_t forced = b->flags & (SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE);
     if (forced & (forced - 1)) return fail(ctx, SSJ_EINVAL, "at most one SSJ_FORCE_* flag");
@@ -1218,7 +1218,8 @@ extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t*
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_count, d_count, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.h_err, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev, s);
-    if (e == cudaSuccess && direct_copy) e = cudaEventSynchronize(sl.copied);
+    // pinned inputs: wait for their copies unless the caller keeps them until the ticket is done
+    if (e == cudaSuccess && direct_copy && !(batch->flags & SSJ_KEEP_INPUTS)) e = cudaEventSynchronize(sl.copied);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
         cudaFreeAsync(t->d_mem, s);

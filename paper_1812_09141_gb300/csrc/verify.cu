@@ -82,6 +82,11 @@ __device__ __forceinline__ uint32_t sel4(const uint4& v, uint32_t k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
+// 1 if x equals one of the four tokens of s (distinct within a block).
+__device__ __forceinline__ uint32_t match4(uint32_t x, const uint4& s) {
+    return (x == s.x) | (x == s.y) | (x == s.z) | (x == s.w);
+}
+
 // Merge state of one pair compared block by block.
 struct BlockState {
     uint32_t qi, qj, o;  // current block of r and of s, overlap so far
@@ -111,10 +116,7 @@ __device__ __forceinline__ void block_step(const uint4& rc, const uint4& sc, uin
     const uint32_t sb[4] = {sc.x, sc.y, sc.z, sc.w};
     uint32_t c = 0;
     if (nvr == 4 && nvs == 4) {
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) c += (ra[x] == sb[y]) ? 1u : 0u;
+        c = match4(rc.x, sc) + match4(rc.y, sc) + match4(rc.z, sc) + match4(rc.w, sc);
     } else {
 #pragma unroll
         for (int x = 0; x < 4; ++x)
@@ -300,11 +302,6 @@ __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const
     }
     *rejected = rej;
     return o;
-}
-
-// 1 if x equals one of the four tokens of s (distinct within a block).
-__device__ __forceinline__ uint32_t match4(uint32_t x, const uint4& s) {
-    return (x == s.x) | (x == s.y) | (x == s.z) | (x == s.w);
 }
 
 // Block step of pass 2 on a (block cursor, tokens remaining) state; the same
@@ -587,6 +584,12 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
     // parity so that a warp one round ahead never overwrites what others read
     __shared__ unsigned long long s_tot[2][3][kPlanWarps];
     __shared__ unsigned long long s_base[2][3];
+    // each warp's tile, for the copy of the short pairs by the whole CTA
+    __shared__ unsigned long long s_incl[2][kPlanWarps][32];  // inclusive prefix of the lanes' short pairs
+    __shared__ unsigned long long s_c0[2][kPlanWarps][32];    // the lanes' first candidates
+    __shared__ uint32_t s_slot[2][kPlanWarps][32];            // the lanes' probe slots
+    __shared__ unsigned long long s_pre[2][kPlanWarps + 1];   // exclusive prefix of the tiles' padded ranges
+    __shared__ const uint32_t* s_cand[2][kPlanWarps];         // the tiles' candidate arrays
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     if (blockIdx.x == 0) {
@@ -597,10 +600,14 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
     // Rounds are uniform over the CTA: warp w of the CTA takes tile g0 + w.
     // The three lists (short pairs, warp/lane items, block items) are
     // reserved with one atomic per CTA and round, not per warp.
+    // With few tiles a CTA takes fewer than one per warp, so that more CTAs
+    // share the copying.
+    const uint32_t per_round =
+        a.n_tiles >= gridDim.x * (uint32_t)kPlanWarps ? kPlanWarps : max(1u, (a.n_tiles + gridDim.x - 1) / gridDim.x);
     uint32_t par = 0;
-    for (uint32_t g0 = blockIdx.x * kPlanWarps; g0 < a.n_tiles; g0 += gridDim.x * kPlanWarps, par ^= 1u) {
+    for (uint32_t g0 = blockIdx.x * per_round; g0 < a.n_tiles; g0 += gridDim.x * per_round, par ^= 1u) {
         const uint32_t g = g0 + (uint32_t)warp;
-        const bool tile_ok = g < a.n_tiles;
+        const bool tile_ok = (uint32_t)warp < per_round && g < a.n_tiles;
         // instance owning tile g: the last one whose tile_base <= g
         uint32_t inst = 0;
         if (a.table) {
@@ -683,36 +690,66 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
         }
         wbase += wincl - wn;  // this lane's first item
         bbase += bincl - bn;
-        if (tbase0 + tpadded > a.pair_cap) {  // cannot happen with a sized workspace
-            if (lane == 0 && tpadded) atomicOr(&a.ctr->err, ERR_GUARD);
+        // short pairs: the CTA's tiles have one contiguous, chunk-aligned range of
+        // the list (warp order); all its threads copy it flat and coalesced, each
+        // slot finding its tile by the prefix of the tiles' ranges and its probe
+        // by a search over that tile's lane prefix sums
+        s_incl[par][warp][lane] = tincl;
+        s_c0[par][warp][lane] = c0;
+        s_slot[par][warp][lane] = slot;
+        if (lane == 0) s_cand[par][warp] = I.cand_ids;
+        if (threadIdx.x == 0) {
+            unsigned long long acc = 0;
+            for (int w = 0; w < kPlanWarps; ++w) {
+                s_pre[par][w] = acc;
+                acc += s_tot[par][0][w];
+            }
+            s_pre[par][kPlanWarps] = acc;
+        }
+        if (tpadded && tbase0 + tpadded > a.pair_cap) {  // cannot happen with a sized workspace
+            if (lane == 0) atomicOr(&a.ctr->err, ERR_GUARD);
         } else {
-            const unsigned long long texcl = tincl - tn;
             for (unsigned long long c = lane; c < tpadded / 32; c += 32) a.chunk_inst[tbase0 / 32 + c] = inst;
-            for (unsigned long long f0 = 0; f0 < tpadded; f0 += 4 * 32) {
-                uint32_t v[4], kk[4];
+        }
+        __syncthreads();
+        {
+            const unsigned long long cta_base = s_base[par][0], cta_total = s_pre[par][kPlanWarps];
+            if (cta_base + cta_total <= a.pair_cap) {
+                for (unsigned long long f0 = 0; f0 < cta_total; f0 += 4 * kPlanThreads) {
+                    uint32_t v[4], kk[4];
+                    unsigned long long fa[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const unsigned long long f = f0 + u * 32 + lane;
-                    uint32_t pos = 0;
+                    for (int u = 0; u < 4; ++u) {
+                        const unsigned long long f = f0 + u * kPlanThreads + threadIdx.x;
+                        fa[u] = f;
+                        v[u] = 0u;
+                        kk[u] = kNoProbe;
+                        if (f < cta_total) {
+                            int w = 0;
 #pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const unsigned long long w = __shfl_sync(kFull, tincl, pos + step - 1);
-                        if (w <= f) pos += step;
+                            for (int step = kPlanWarps / 2; step >= 1; step >>= 1)
+                                if (s_pre[par][w + step] <= f) w += step;
+                            const unsigned long long fl = f - s_pre[par][w];
+                            const unsigned long long tt = s_incl[par][w][31];
+                            if (fl < tt) {
+                                uint32_t pos = 0;
+#pragma unroll
+                                for (int step = 16; step >= 1; step >>= 1)
+                                    if (s_incl[par][w][pos + step - 1] <= fl) pos += step;
+                                const unsigned long long ex = pos ? s_incl[par][w][pos - 1] : 0ull;
+                                kk[u] = s_slot[par][w][pos];
+                                v[u] = s_cand[par][w][s_c0[par][w][pos] + (fl - ex)];
+                            }
+                        }
                     }
-                    pos = min(pos, 31u);
-                    const unsigned long long oc0 = __shfl_sync(kFull, c0, pos);
-                    const unsigned long long oex = __shfl_sync(kFull, texcl, pos);
-                    kk[u] = __shfl_sync(kFull, slot, pos);
-                    v[u] = (f < ttotal) ? I.cand_ids[oc0 + (f - oex)] : 0u;
-                }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const unsigned long long f = f0 + u * 32 + lane;
-                    if (f < tpadded) {
-                        PairRef pr;
-                        pr.k = (f < ttotal) ? kk[u] : kNoProbe;
-                        pr.s = v[u];
-                        a.pairs[tbase0 + f] = pr;
+                    for (int u = 0; u < 4; ++u) {
+                        if (fa[u] < cta_total) {
+                            PairRef pr;
+                            pr.k = kk[u];
+                            pr.s = v[u];
+                            a.pairs[cta_base + fa[u]] = pr;
+                        }
                     }
                 }
             }
@@ -1148,7 +1185,7 @@ cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uin
         // one round of tiles per CTA and round (kPlanThreads / 32 tiles), one wave of CTAs
         const int threads = kPlanThreads;
         uint64_t blocks = ((uint64_t)a.n_tiles * 32 + threads - 1) / threads;
-        const uint64_t max_blocks = (uint64_t)num_sms * 4;
+        const uint64_t max_blocks = (uint64_t)num_sms * 6;
         if (blocks > max_blocks) blocks = max_blocks;
         if (blocks < 1) blocks = 1;
         plan_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);

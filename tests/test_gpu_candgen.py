@@ -58,10 +58,13 @@ def test_self_join_matches_oracle_allpairs(ctx, sim, pq):
 
 def test_self_join_raw_tokens_count_only_device_and_sorted(ctx):
     import torch
-    spec = synth.tiny_self_join(seed=77, n=600)
-    spec.plant_frac, spec.plant_edits = 0.2, 1
-    c = synth.collection(spec)
+    # raw (not renumbered) token values, small enough for the device prefix index
+    rng = np.random.default_rng(77)
+    lists = [sorted(rng.choice(300, size=int(rng.integers(1, 40)), replace=False).tolist()) for _ in range(500)]
+    lists += [sorted(set(x) | {299 - i % 7}) for i, x in enumerate(lists[:100])]
+    c = synth.from_lists(lists)
     want = oracle.sort_triples(oracle.bruteforce_self(c.offsets, c.tokens, 3, 5))
+    assert len(want) > 10
     h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens)  # raw token order
     try:
         got, _ = ssj.ssj_self_join(ctx, h, 3, 5, ssj.SSJ_SORTED)

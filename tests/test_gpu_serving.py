@@ -87,3 +87,31 @@ def test_submit_from_pinned_inputs_then_overwrite():
             np.testing.assert_array_equal(ssj.triples_to_array(got), want)
     finally:
         ssj.ssj_destroy(ctx)
+
+
+def test_keep_inputs_submissions_match_single_batches():
+    """SSJ_KEEP_INPUTS: the call does not wait for the copies of pinned inputs; with the inputs kept
+    until the tickets are done, every result equals the synchronous call's."""
+    import torch
+    _build.build()
+    spec = synth.short_sets(n=20_000)
+    spec.plant_frac, spec.plant_edits = 0.2, 2
+    c = synth.collection(spec)
+    ctx = ssj.ssj_create(0, mem_budget_bytes=256 << 20, max_inflight=4)
+    try:
+        h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens)
+        pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        jobs = []
+        for p, q in [(3, 5), (7, 10), (4, 5), (9, 10)]:
+            pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=4)
+            arrs = (pinned(pr), pinned(co), pinned(ci))
+            want = ssj.triples_to_array(ssj.ssj_verify_batch(ctx, h, h, p, q, *arrs))
+            t = None
+            while t is None:
+                t = ssj.ssj_submit(ctx, h, h, p, q, *arrs, flags=ssj.SSJ_KEEP_INPUTS)
+            jobs.append((t, want, arrs))
+        for t, want, _arrs in jobs:
+            assert ssj.ssj_poll(ctx, t, timeout_ms=-1)
+            np.testing.assert_array_equal(ssj.triples_to_array(ssj.ssj_results(ctx, t)), want)
+    finally:
+        ssj.ssj_destroy(ctx)
