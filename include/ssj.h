@@ -159,6 +159,10 @@ ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, ui
 #define SSJ_KEEP_INPUTS 0x800u      /* ssj_submit: the caller keeps pinned host inputs unchanged
                                        until the ticket is done, so the call does not wait for
                                        their host-to-device copies (ignored for pageable inputs) */
+#define SSJ_HOST_DIRECT 0x1000u     /* ssj_verify_batches: host arrays in pinned memory that the
+                                       device can address are read by the kernels directly over
+                                       the host link (NVLink-C2C on Grace systems) instead of
+                                       being copied first; other arrays are copied */
 #define SSJ_JOIN_POSITIONAL 0x400u  /* ssj_self_join: drop a candidate at a matching prefix token
                                        when min(i, j) + 1 + min(|r|-i-1, |s|-j-1) (i, j: the token's
                                        positions) is below the pair's equivalent overlap */
@@ -324,6 +328,8 @@ typedef struct {
     uint32_t lane_max_key;    /*   for warp_max_key sends no probe to the block bin, */
     uint32_t warp_max_key;    /*   lane_max_key <= thread_max_key means no lane bin */
     uint32_t block_threads;   /* chosen block size (the block path's window is 8 steps per thread) */
+    uint32_t drain_min_live;  /* short pairs still merging that keep a warp on them before the rest
+                                 are parked again and lanes refilled (8 .. 24) */
     uint32_t settings_tried;  /* distinct settings timed */
     float best_ms;            /* median device time of one launch with the chosen setting */
     float initial_ms;         /* the same for the setting m had before the call */
@@ -333,7 +339,8 @@ typedef struct {
  * Autotune the granularity of a prepared launch on its own inputs: time
  * (CUDA events on `stream`, NULL: the context's stream; median of reps >= 3
  * launches after one untimed launch each) settings of the thread, lane and
- * warp bins' upper keys and of the block size, by coordinate descent
+ * warp bins' upper keys, of the block size and of the short-pair refill
+ * threshold (drain_min_live), by coordinate descent
  * from m's current setting, and keep the fastest in m (later launches, and
  * graphs captured later, use it).  Every setting computes the same results
  * (Section 3.3.2 Alternatives A-C differ in speed only, Section 5.4); the

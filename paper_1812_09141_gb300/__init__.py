@@ -44,6 +44,7 @@ SSJ_SIM_MASK = 0x300
 SSJ_FEEDER_PPJOIN = 0x1
 SSJ_JOIN_POSITIONAL = 0x400
 SSJ_KEEP_INPUTS = 0x800
+SSJ_HOST_DIRECT = 0x1000
 # context flags
 SSJ_CTX_PROFILE = 0x1
 
@@ -74,7 +75,8 @@ class ssj_request(ctypes.Structure):
 
 class ssj_tune_result(ctypes.Structure):
     _fields_ = [("thread_max_key", ctypes.c_uint32), ("lane_max_key", ctypes.c_uint32), ("warp_max_key", ctypes.c_uint32),
-                ("block_threads", ctypes.c_uint32), ("settings_tried", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32), ("drain_min_live", ctypes.c_uint32),
+                ("settings_tried", ctypes.c_uint32),
                 ("best_ms", ctypes.c_float), ("initial_ms", ctypes.c_float)]
 
 
@@ -372,7 +374,8 @@ def ssj_multi_autotune(ctx: int, m: int, stream: int | None = None, reps: int = 
     r = ssj_tune_result()
     _check(ctx, lib().ssj_multi_autotune(ctx, m, stream, reps, ctypes.byref(r)))
     return {"thread_max_key": r.thread_max_key, "lane_max_key": r.lane_max_key, "warp_max_key": r.warp_max_key,
-            "block_threads": r.block_threads, "settings_tried": r.settings_tried,
+            "block_threads": r.block_threads, "drain_min_live": r.drain_min_live,
+            "settings_tried": r.settings_tried,
             "best_ms": r.best_ms, "initial_ms": r.initial_ms}
 
 

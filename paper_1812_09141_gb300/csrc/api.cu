@@ -217,6 +217,18 @@ ssj_status ensure_pinned(ssj_ctx* ctx, T** buf, uint64_t* have, uint64_t need) {
     return SSJ_OK;
 }
 
+// Device address of pinned host memory the device can read directly, or
+// NULL (pageable memory, or no mapping).
+const void* device_view(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Host-side checks of a host batch.  Only what the host needs is read here
 // (the first and last offsets); ids and the monotonicity of the offsets are
 // checked on the device by the plan and verify kernels, which report
@@ -250,7 +262,8 @@ ssj_status resolve(ssj_ctx* ctx, const ssj_batch* b, Collection** R, Collection*
     if (b->R != b->S && (ir->second.renumbered || is->second.renumbered))
         return fail(ctx, SSJ_EINVAL, "renumbered collections can only be self-joined");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_EMIT_ALL | SSJ_FORCE_THREAD |
-                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_SIM_MASK | SSJ_KEEP_INPUTS;
+                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_SIM_MASK | SSJ_KEEP_INPUTS |
+                           SSJ_HOST_DIRECT;
     if (b->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown batch flag");
     const uint32_t forced = b->flags & (SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE);
     if (forced & (forced - 1)) return fail(ctx, SSJ_EINVAL, "at most one SSJ_FORCE_* flag");
@@ -763,16 +776,21 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
         uint32_t* d_probe = reinterpret_cast<uint32_t*>(p); p += align256(4ull * std::max<uint32_t>(b->n_probes, 1));
         uint64_t* d_offs = reinterpret_cast<uint64_t*>(p);  p += align256(8ull * (b->n_probes + 1));
         uint32_t* d_cand = reinterpret_cast<uint32_t*>(p);  p += align256(4ull * std::max<uint64_t>(n_cands[i], 1));
-        if (b->n_probes) {
+        // SSJ_HOST_DIRECT: pinned arrays the device can address are read by the kernels
+        // themselves (over the host link), with no staging copy
+        const void* dv_probe = (b->flags & SSJ_HOST_DIRECT) ? device_view(b->probe_ids) : nullptr;
+        const void* dv_offs = (b->flags & SSJ_HOST_DIRECT) ? device_view(b->cand_offsets) : nullptr;
+        const void* dv_cand = (b->flags & SSJ_HOST_DIRECT) ? device_view(b->cand_ids) : nullptr;
+        if (b->n_probes && !dv_probe)
             CUDA_TRY(ctx, cudaMemcpyAsync(d_probe, b->probe_ids, 4ull * b->n_probes, cudaMemcpyHostToDevice, s));
+        if (b->n_probes && !dv_offs)
             CUDA_TRY(ctx, cudaMemcpyAsync(d_offs, b->cand_offsets, 8ull * (b->n_probes + 1), cudaMemcpyHostToDevice, s));
-        }
-        if (n_cands[i])
+        if (n_cands[i] && !dv_cand)
             CUDA_TRY(ctx, cudaMemcpyAsync(d_cand, b->cand_ids, 4ull * n_cands[i], cudaMemcpyHostToDevice, s));
         Instance& I = table[i];
-        I.probe_ids = d_probe;
-        I.cand_offsets = d_offs;
-        I.cand_ids = d_cand;
+        I.probe_ids = dv_probe ? static_cast<const uint32_t*>(dv_probe) : d_probe;
+        I.cand_offsets = dv_offs ? static_cast<const uint64_t*>(dv_offs) : d_offs;
+        I.cand_ids = dv_cand ? static_cast<const uint32_t*>(dv_cand) : d_cand;
         I.out = reinterpret_cast<ssj_triple*>(p);
         I.cap = (b->flags & SSJ_COUNT_ONLY) ? 0 : std::min(caps[i], n_cands[i]);
         I.count = reinterpret_cast<unsigned long long*>(d_counts + i);
@@ -1476,11 +1494,12 @@ namespace {
 // Median device time (ms) of reps launches of m with the given granularity,
 // after one untimed launch; negative on a CUDA error (*err receives it).
 float time_setting(ssj_ctx* ctx, const ssj_multi* m, uint32_t tmax, uint32_t lmax, uint32_t wmax, uint32_t bt,
-                   uint32_t reps, cudaStream_t s, cudaEvent_t* ev, cudaError_t* err) {
+                   uint32_t dml, uint32_t reps, cudaStream_t s, cudaEvent_t* ev, cudaError_t* err) {
     VerifyArgs a = m->a;
     a.thread_max_key = tmax;
     a.lane_max_key = lmax;
     a.warp_max_key = wmax;
+    a.drain_min_live = dml;
     cudaError_t e = prepare_verify(bt);
     if (e == cudaSuccess) e = launch_verify(a, s, ctx->num_sms, bt, nullptr);
     std::vector<float> ms;
@@ -1523,13 +1542,15 @@ extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* strea
     static const uint32_t kLane[] = {1, 256, 512, 1024, 2048};
     static const uint32_t kWarp[] = {256, 512, 1024, 2048, 4096, 0xFFFFFFFFu};
     static const uint32_t kBlock[] = {128, 256, 512};
-    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, float> seen;
+    static const uint32_t kMinLive[] = {8, 12, 16, 20, 24};
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, uint32_t>, float> seen;
     cudaError_t err = cudaSuccess;
+    uint32_t bd = m->a.drain_min_live ? m->a.drain_min_live : 16;
     auto cost = [&](uint32_t t, uint32_t l, uint32_t w, uint32_t b) -> float {
-        auto key = std::make_tuple(t, l, w, b);
+        auto key = std::make_tuple(t, l, w, b, bd);
         auto it = seen.find(key);
         if (it != seen.end()) return it->second;
-        const float v = time_setting(ctx, m, t, l, w, b, reps, s, ev, &err);
+        const float v = time_setting(ctx, m, t, l, w, b, bd, reps, s, ev, &err);
         seen[key] = v;
         return v;
     };
@@ -1561,6 +1582,13 @@ extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* strea
             const float v = cost(bt, bl, bw, b);
             if (v < best) best = v, bb = b;
         }
+        for (uint32_t d : kMinLive) {
+            if (err != cudaSuccess) break;
+            const uint32_t keep = bd;
+            bd = d;
+            const float v = cost(bt, bl, bw, bb);
+            if (v < best) best = v; else bd = keep;
+        }
         if (!(best < 0.98f * before)) break;  // no gain worth another sweep
     }
     cudaEventDestroy(ev[0]);
@@ -1573,6 +1601,7 @@ extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* strea
     m->a.thread_max_key = bt;
     m->a.lane_max_key = bl;
     m->a.warp_max_key = bw;
+    m->a.drain_min_live = bd;
     m->block_threads = bb;
     CUDA_TRY(ctx, prepare_verify(bb));
     if (m->exec) {
@@ -1587,6 +1616,7 @@ extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* strea
     out->lane_max_key = bl;
     out->warp_max_key = bw;
     out->block_threads = bb;
+    out->drain_min_live = bd;
     out->best_ms = best;
     out->initial_ms = first;
     out->settings_tried = (uint32_t)seen.size();

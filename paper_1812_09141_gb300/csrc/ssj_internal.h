@@ -127,6 +127,7 @@ struct VerifyArgs {
     uint32_t thread_max_key;      // 2|r| <= this: one thread per pair
     uint32_t lane_max_key;        // 2|r| <= this (and r fits, >= kLaneMinCands candidates): one lane per pair
     uint32_t warp_max_key;        // 2|r| <= this: one warp per pair; above: one block
+    uint32_t drain_min_live;      // short-pair pass 2 re-parks below this many live lanes (0: default 16)
 };
 
 // Sizes of one launch, from which the workspace is carved.

@@ -67,7 +67,7 @@ struct ContEntry {
     uint4 m1;  // tokens of r and of s from the current blocks on, required overlap, overlap so far
     uint4 m2;  // instance, unused, unused, unused
 };
-constexpr uint32_t kDrainMinLive = 16;             // pass 2 re-parks a warp's pairs below this many live lanes
+constexpr uint32_t kDrainMinLive = 16;             // default: pass 2 re-parks a warp's pairs below this many live lanes
 constexpr uint32_t kTableBytes = kCont * sizeof(ContEntry);
 
 // Phases 2 and 3 run per warp and the warps of a CTA change phase at
@@ -930,9 +930,10 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
 
         // Pass 2 (drain_parked): the last m parked pairs, one per lane, merged
         // while at least min_live lanes still work; the rest are parked again.
-        auto drain = [&](uint32_t m, uint32_t min_live) {
-            n_cont = drain_parked(cont, n_cont, m, min_live, table, lane);
+        auto drain = [&](uint32_t m, uint32_t live) {
+            n_cont = drain_parked(cont, n_cont, m, live, table, lane);
         };
+        const uint32_t min_live = a.drain_min_live ? min(max(a.drain_min_live, 1u), 24u) : kDrainMinLive;
 
         for (uint32_t round = 0;; ++round) {
             uint32_t u = 0;
@@ -1015,7 +1016,7 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
                 const bool park = live && !st.fin;
                 const uint32_t kmask = __ballot_sync(kFull, park);
                 if (kmask) {
-                    while (n_cont + 32 > kCont) drain(32, kDrainMinLive);  // room for a full warp of parked pairs
+                    while (n_cont + 32 > kCont) drain(32, min_live);  // room for a full warp of parked pairs
                     if (park) {
                         ContEntry* ce = cont + n_cont + __popc(kmask & lt_mask);
                         ce->m0 = make_uint4(pr_id, ps_id, dr.x + st.qi, ds.x + st.qj);
@@ -1024,12 +1025,12 @@ __global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
                     }
                     n_cont += __popc(kmask);
                     __syncwarp();
-                    if (n_cont >= 32) drain(32, kDrainMinLive);
+                    if (n_cont >= 32) drain(32, min_live);
                 }
             }
         }
         // the tail: keep refilling lanes while more than a warp is parked, then finish
-        while (n_cont) drain(min(n_cont, 32u), n_cont > 32 ? kDrainMinLive : 1u);
+        while (n_cont) drain(min(n_cont, 32u), n_cont > 32 ? min_live : 1u);
     }
 }
 

@@ -179,6 +179,7 @@ def test_autotuned_launch_matches_oracle(ctx):
     assert t["block_threads"] in (128, 256, 512)
     assert t["thread_max_key"] in (32, 64, 128, 256, 512, 1024, 2048, 4096)
     assert t["warp_max_key"] >= t["thread_max_key"]
+    assert t["drain_min_live"] in (8, 12, 16, 20, 24)
     assert t["settings_tried"] >= 3 and 0 < t["best_ms"] <= t["initial_ms"]
     for r in res:
         for i, (got, w) in enumerate(zip(r, wants)):
@@ -257,3 +258,25 @@ def test_verify_batches_host_equals_single_calls(ctx):
     finally:
         for x in (h, hs, hR):
             ssj.ssj_unload_collection(ctx, x)
+
+
+def test_verify_batches_host_direct_equals_copies(ctx):
+    """SSJ_HOST_DIRECT: kernels reading pinned host inputs directly give the results of the copying
+    path; pageable inputs under the flag are copied as usual."""
+    import torch
+    c = synth.collection(synth.short_sets(n=20_000))
+    h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens)
+    pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    try:
+        batches = []
+        for p, q in [(3, 5), (4, 5)]:
+            pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=4)
+            batches.append((h, h, p, q, pinned(pr), pinned(co), pinned(ci), 0))
+            batches.append((h, h, p, q, pr, co, ci, 0))  # pageable
+        want = ssj.ssj_verify_batches(ctx, batches)
+        got = ssj.ssj_verify_batches(ctx, [b[:7] + (ssj.SSJ_HOST_DIRECT | ssj.SSJ_FORCE_WARP * (i % 2),)
+                                           for i, b in enumerate(batches)])
+        for g, w in zip(got, want):
+            assert np.array_equal(ssj.triples_to_array(g), ssj.triples_to_array(w))
+    finally:
+        ssj.ssj_unload_collection(ctx, h)
