@@ -638,8 +638,9 @@ def run_serving(args):
 
 def run_candgen(args):
     """Self-join with candidate generation on the device (ssj_self_join) against the CPU feeder
-    (16 threads) followed by the same GPU verification, on the short-set and long-set
-    collections; CUDA events and wall clock; results must agree."""
+    (16 threads) followed by the same GPU verification, and GroupJoin (CPU group candidates
+    expanded and verified on the device), on the short-set and long-set collections; wall
+    clock; results and candidate counts must agree."""
     import torch
     import synth
     import paper_1812_09141_gb300 as ssj
@@ -676,6 +677,19 @@ def run_candgen(args):
                 row["cpu_feeder_then_gpu"] = {"feeder_s": t_feed, "verify_s": t_ver, "candidates": len(ci),
                                               "results": cnt_cpu, "feeder_threads": threads}
                 if cnt_cpu != row["device"]["results"] or len(ci) != row["device"]["candidates"]:
+                    row["mismatch"] = True
+                # GroupJoin: CPU grouping and group candidates, expansion + verification on the device
+                t0 = time.perf_counter()
+                g = ssj.group_candidates(c.offsets, c.tokens, p, q)
+                t_grp = time.perf_counter() - t0
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                cnt_g, n_pairs = ssj.ssj_verify_groups(ctx, h, p, q, g, ssj.SSJ_COUNT_ONLY)
+                t_gv = time.perf_counter() - t0
+                row["groupjoin"] = {"groups": int(len(g.group_offsets) - 1), "probe_groups": int(len(g.probe_groups)),
+                                    "candidate_group_entries": int(len(g.cand_groups)), "expanded_pairs": n_pairs,
+                                    "results": cnt_g, "cpu_grouping_s": t_grp, "device_expand_verify_s": t_gv}
+                if cnt_g != cnt_cpu or n_pairs != len(ci):
                     row["mismatch"] = True
                 out["runs"].append(row)
             ssj.ssj_unload_collection(ctx, h)

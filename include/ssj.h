@@ -286,6 +286,40 @@ ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uint32_t q, ui
                          uint64_t cap, uint64_t* n_out, uint64_t* n_candidates);
 
 /* ------------------------------------------------------------------------
+ * GroupJoin: group candidates (ssj_groups_create in ssj_feeder.h) expanded
+ * and verified on the device (the paper's GroupJoin split, Section 4.1.3,
+ * leaves the expanded pairs to the host; here the whole verification runs
+ * on the device)
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    ssj_coll coll;                  /* self-join of this collection (ids are its set ids) */
+    uint32_t p, q;                  /* threshold, as for ssj_batch */
+    uint32_t flags;                 /* SSJ_SIM_*, SSJ_COUNT_ONLY, SSJ_SORTED, SSJ_DEVICE_PTRS (out only), SSJ_FORCE_* */
+    uint32_t n_groups;
+    const uint64_t* group_offsets;  /* n_groups + 1, host; group g holds members[group_offsets[g] ..
+                                       group_offsets[g+1]), every group non-empty */
+    const uint32_t* members;        /* set ids, host */
+    uint32_t n_probe_groups;
+    const uint32_t* probe_groups;   /* host group ids */
+    const uint64_t* cand_offsets;   /* n_probe_groups + 1, host, from 0 */
+    const uint32_t* cand_groups;    /* host group ids */
+} ssj_group_batch;
+
+/*
+ * Expand the groups on the device into member pairs (every member of probe
+ * group k against every member of its candidate groups, and every pair of
+ * members inside a group whose prefix for this threshold is not empty) and
+ * verify them with the launch of ssj_verify_batch.  Results as for a
+ * self-join batch: to out (host, or device with SSJ_DEVICE_PTRS), at most
+ * cap, *n_out the count (SSJ_ENOMEM above cap), *n_pairs (may be NULL) the
+ * expanded pairs verified.  Errors: SSJ_EINVAL (layout or ids), SSJ_ENOTFOUND,
+ * SSJ_ENOMEM, SSJ_EDEVICE.
+ */
+ssj_status ssj_verify_groups(ssj_ctx* ctx, const ssj_group_batch* gb, ssj_triple* out, uint64_t cap, uint64_t* n_out,
+                             uint64_t* n_pairs);
+
+/* ------------------------------------------------------------------------
  * Batched instances: many independent joins in one launch
  * ------------------------------------------------------------------------ */
 

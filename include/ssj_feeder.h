@@ -90,6 +90,42 @@ ssj_status ssj_feeder_progress(ssj_feeder* f, uint64_t* n_cands, uint32_t* probe
 
 void ssj_feeder_destroy(ssj_feeder* f);
 
+/* ------------------------------------------------------------------------
+ * GroupJoin candidates (the GRP algorithm of the paper's evaluation): sets
+ * of equal size and equal prefix form a group, filtering and indexing work
+ * on groups, and a candidate group pair stands for every pair of their
+ * members; ssj_verify_groups (ssj.h) expands them on the device.
+ * ------------------------------------------------------------------------ */
+
+typedef struct ssj_groups ssj_groups;
+
+/* Group the n_sets sets (host offsets / tokens as for ssj_feeder_create;
+ * copied) and generate group candidates of a self-join for opts->sim,
+ * opts->p / opts->q (opts->flags must be 0, n_threads is ignored).
+ * Groups are formed in (size, lexicographic) order of the frequency-
+ * renumbered sets; group k's members are set ids; probe group k is paired
+ * with the earlier groups that share a prefix token and pass the length
+ * filter.  The member pairs the groups stand for (every pair of a probe
+ * group's member with a candidate group's member, and every pair inside a
+ * group with a non-empty prefix) are exactly algorithm ALL's candidates.
+ * Errors: SSJ_EINVAL, SSJ_ENOMEM. */
+ssj_status ssj_groups_create(const uint64_t* offsets, const uint32_t* tokens, uint32_t n_sets,
+                             const ssj_feeder_opts* opts, ssj_groups** out);
+
+/* Sizes: groups, probe groups, candidate group entries, and the member pairs
+ * they stand for.  Any pointer may be NULL. */
+ssj_status ssj_groups_info(ssj_groups* g, uint32_t* n_groups, uint32_t* n_probe_groups, uint64_t* n_cand_groups,
+                           uint64_t* n_pairs);
+
+/* Copy the groups out (host arrays): group_offsets (n_groups + 1, into
+ * members), members (n_sets set ids), probe_groups (n_probe_groups group
+ * ids), cand_offsets (n_probe_groups + 1), cand_groups (n_cand_groups
+ * group ids). */
+ssj_status ssj_groups_copy(ssj_groups* g, uint64_t* group_offsets, uint32_t* members, uint32_t* probe_groups,
+                           uint64_t* cand_offsets, uint32_t* cand_groups);
+
+void ssj_groups_destroy(ssj_groups* g);
+
 #ifdef __cplusplus
 }
 #endif

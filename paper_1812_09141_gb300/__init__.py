@@ -85,6 +85,14 @@ class ssj_feeder_opts(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("n_threads", ctypes.c_uint32)]
 
 
+class ssj_group_batch(ctypes.Structure):
+    _fields_ = [("coll", ctypes.c_uint32), ("p", ctypes.c_uint32), ("q", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("n_groups", ctypes.c_uint32), ("group_offsets", ctypes.c_void_p),
+                ("members", ctypes.c_void_p), ("n_probe_groups", ctypes.c_uint32),
+                ("probe_groups", ctypes.c_void_p), ("cand_offsets", ctypes.c_void_p),
+                ("cand_groups", ctypes.c_void_p)]
+
+
 class ssj_serve_stats(ctypes.Structure):
     _fields_ = [("wall_s", ctypes.c_double), ("pairs", ctypes.c_uint64), ("results", ctypes.c_uint64),
                 ("eagain", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32)]
@@ -132,6 +140,11 @@ SIGNATURES = {
     "ssj_feeder_create": (_INT, [_VP, _VP, _U32, _U32, _U32, _U32, _P(_VP)]),
     "ssj_feeder_create_sim": (_INT, [_VP, _VP, _U32, _U32, _U32, _U32, _U32, _P(_VP)]),
     "ssj_feeder_create_ex": (_INT, [_VP, _VP, _U32, _VP, _VP, _U32, _P(ssj_feeder_opts), _P(_VP)]),
+    "ssj_groups_create": (_INT, [_VP, _VP, _U32, _P(ssj_feeder_opts), _P(_VP)]),
+    "ssj_groups_info": (_INT, [_VP, _P(_U32), _P(_U32), _P(_U64), _P(_U64)]),
+    "ssj_groups_copy": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "ssj_groups_destroy": (None, [_VP]),
+    "ssj_verify_groups": (_INT, [_VP, _P(ssj_group_batch), _VP, _U64, _P(_U64), _P(_U64)]),
     "ssj_feeder_next": (_INT, [_VP, _U32, _U64, _VP, _VP, _VP, _P(_U32), _P(_U64), _P(_INT)]),
     "ssj_feeder_progress": (_INT, [_VP, _P(_U64), _P(_U32), _P(_U32)]),
     "ssj_feeder_destroy": (None, [_VP]),
@@ -566,3 +579,59 @@ def triples_to_array(t) -> np.ndarray:
     if len(a):
         a = a[np.lexsort((a[:, 1], a[:, 0]))]
     return a
+
+
+# GroupJoin -----------------------------------------------------------------
+
+class Groups:
+    """GroupJoin candidates: group_offsets, members, probe_groups, cand_offsets, cand_groups (numpy),
+    and n_pairs, the member pairs they stand for."""
+
+    def __init__(self, group_offsets, members, probe_groups, cand_offsets, cand_groups, n_pairs):
+        self.group_offsets, self.members = group_offsets, members
+        self.probe_groups, self.cand_offsets, self.cand_groups = probe_groups, cand_offsets, cand_groups
+        self.n_pairs = n_pairs
+
+
+def group_candidates(offsets, tokens, p: int, q: int, sim: int = 0) -> Groups:
+    """Run ssj_groups_create and copy the groups out."""
+    offs, po = _host(offsets, np.uint64)
+    toks, pt = _host(tokens, np.uint32)
+    o = ssj_feeder_opts(sim, p, q, 0, 1)
+    h = ctypes.c_void_p()
+    _check(None, lib().ssj_groups_create(po, pt, len(offs) - 1, ctypes.byref(o), ctypes.byref(h)))
+    try:
+        ng, npg = ctypes.c_uint32(), ctypes.c_uint32()
+        ncg, npairs = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(None, lib().ssj_groups_info(h, ctypes.byref(ng), ctypes.byref(npg), ctypes.byref(ncg),
+                                           ctypes.byref(npairs)))
+        go = np.zeros(ng.value + 1, dtype=np.uint64)
+        mem = np.zeros(max(len(offs) - 1, 1), dtype=np.uint32)
+        pg = np.zeros(max(npg.value, 1), dtype=np.uint32)
+        co = np.zeros(npg.value + 1, dtype=np.uint64)
+        cg = np.zeros(max(ncg.value, 1), dtype=np.uint32)
+        _check(None, lib().ssj_groups_copy(h, go.ctypes.data, mem.ctypes.data, pg.ctypes.data, co.ctypes.data,
+                                           cg.ctypes.data))
+        return Groups(go, mem[:len(offs) - 1], pg[:npg.value], co, cg[:ncg.value], npairs.value)
+    finally:
+        lib().ssj_groups_destroy(h)
+
+
+def ssj_verify_groups(ctx: int, coll: int, p: int, q: int, g: Groups, flags: int = 0, cap: int | None = None):
+    """Expand and verify GroupJoin candidates on the device.  Returns (structured triples, n_pairs),
+    or (count, n_pairs) with SSJ_COUNT_ONLY."""
+    keep = [np.ascontiguousarray(a, dtype=t) for a, t in ((g.group_offsets, np.uint64), (g.members, np.uint32),
+                                                            (g.probe_groups, np.uint32), (g.cand_offsets, np.uint64),
+                                                            (g.cand_groups, np.uint32))]
+    ptr = [a.ctypes.data if a.size else None for a in keep]
+    gb = ssj_group_batch(coll, p, q, flags, len(keep[0]) - 1, ptr[0], ptr[1], len(keep[2]), ptr[2], ptr[3], ptr[4])
+    n_out, n_pairs = ctypes.c_uint64(), ctypes.c_uint64()
+    if flags & SSJ_COUNT_ONLY:
+        _check(ctx, lib().ssj_verify_groups(ctx, ctypes.byref(gb), None, 0, ctypes.byref(n_out), ctypes.byref(n_pairs)))
+        return n_out.value, n_pairs.value
+    cap = g.n_pairs if cap is None else cap
+    res = np.empty(max(int(cap), 1), dtype=TRIPLE_DTYPE)
+    _check(ctx, lib().ssj_verify_groups(ctx, ctypes.byref(gb), res.ctypes.data, int(cap), ctypes.byref(n_out),
+                                        ctypes.byref(n_pairs)))
+    return res[:n_out.value], n_pairs.value
+

@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libssj.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
               "--expt-relaxed-constexpr", "-I", INCLUDE]
-SOURCES = ["api.cu", "verify.cu", "layout.cu", "noalloc.cu", "probe.cu", "candgen.cu", "feeder.cpp", "renumber.cpp", "serve_driver.cpp"]
+SOURCES = ["api.cu", "verify.cu", "layout.cu", "noalloc.cu", "probe.cu", "candgen.cu", "feeder.cpp", "groups.cpp", "renumber.cpp", "serve_driver.cpp"]
 
 
 def _nvcc() -> str:

@@ -1015,6 +1015,182 @@ extern "C" ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uin
 }
 
 // ===========================================================================
+// GroupJoin: group candidates expanded on the device
+// ===========================================================================
+
+extern "C" ssj_status ssj_verify_groups(ssj_ctx* ctx, const ssj_group_batch* gb, ssj_triple* out, uint64_t cap,
+                                        uint64_t* n_out, uint64_t* n_pairs) {
+    if (!ctx || !gb || !n_out) return fail(ctx, SSJ_EINVAL, "NULL argument");
+    const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_SIM_MASK | SSJ_FORCE_THREAD |
+                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE;
+    if (gb->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown flag");
+    if (cap && !out && !(gb->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output with cap > 0");
+    if (!gb->group_offsets || (gb->n_groups && !gb->members) || (gb->n_probe_groups && (!gb->probe_groups ||
+        !gb->cand_offsets)))
+        return fail(ctx, SSJ_EINVAL, "NULL group arrays");
+    ssj_batch probe_b;
+    memset(&probe_b, 0, sizeof(probe_b));
+    probe_b.R = probe_b.S = gb->coll;
+    probe_b.p = gb->p;
+    probe_b.q = gb->q;
+    probe_b.flags = gb->flags & (SSJ_SIM_MASK | SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE);
+    Collection *R, *S;
+    ssj_status st = resolve(ctx, &probe_b, &R, &S);
+    if (st != SSJ_OK) return st;
+    const Collection& C = *R;
+    // host-side checks of the group layout (ids are the collection's)
+    const uint64_t n_members = gb->group_offsets[gb->n_groups];
+    if (gb->group_offsets[0] != 0) return fail(ctx, SSJ_EINVAL, "group_offsets[0] must be 0");
+    for (uint32_t g = 0; g < gb->n_groups; ++g)
+        if (gb->group_offsets[g + 1] <= gb->group_offsets[g]) return fail(ctx, SSJ_EINVAL, "group %u is empty", g);
+    for (uint64_t i = 0; i < n_members; ++i)
+        if (gb->members[i] >= C.n_sets) return fail(ctx, SSJ_EINVAL, "member id out of range");
+    const uint64_t n_cg = gb->n_probe_groups ? gb->cand_offsets[gb->n_probe_groups] : 0;
+    if (gb->n_probe_groups && gb->cand_offsets[0] != 0) return fail(ctx, SSJ_EINVAL, "cand_offsets[0] must be 0");
+    for (uint32_t k = 0; k < gb->n_probe_groups; ++k) {
+        if (gb->probe_groups[k] >= gb->n_groups || gb->cand_offsets[k + 1] < gb->cand_offsets[k])
+            return fail(ctx, SSJ_EINVAL, "probe group entry %u invalid", k);
+    }
+    for (uint64_t c = 0; c < n_cg; ++c)
+        if (gb->cand_groups[c] >= gb->n_groups) return fail(ctx, SSJ_EINVAL, "candidate group id out of range");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    std::vector<void*> mem;
+    auto release = [&]() {
+        for (void* m : mem) cudaFree(m);
+        mem.clear();
+    };
+    auto alloc = [&](size_t bytes) -> void* {
+        void* m = nullptr;
+        if (cudaMalloc(&m, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        mem.push_back(m);
+        return m;
+    };
+    const uint64_t n_entries = (uint64_t)gb->n_groups + gb->n_probe_groups;
+    GroupExpand x;
+    memset(&x, 0, sizeof(x));
+    x.toks4 = reinterpret_cast<const uint4*>(C.d_toks);
+    x.desc = C.d_desc;
+    x.sim = (gb->flags & SSJ_SIM_MASK) >> 8;
+    x.p = gb->p;
+    x.q = gb->q;
+    x.n_groups = gb->n_groups;
+    x.n_probe_groups = gb->n_probe_groups;
+    uint64_t* d_goff = static_cast<uint64_t*>(alloc(8ull * (gb->n_groups + 1)));
+    uint32_t* d_mem = static_cast<uint32_t*>(alloc(4ull * n_members));
+    uint32_t* d_pg = static_cast<uint32_t*>(alloc(4ull * gb->n_probe_groups));
+    uint64_t* d_coff = static_cast<uint64_t*>(alloc(8ull * (gb->n_probe_groups + 1)));
+    uint32_t* d_cg = static_cast<uint32_t*>(alloc(4ull * n_cg));
+    x.probe_off = static_cast<uint64_t*>(alloc(8ull * (n_entries + 1)));
+    x.pair_off = static_cast<uint64_t*>(alloc(8ull * (n_entries + 1)));
+    x.per_probe = static_cast<uint64_t*>(alloc(8ull * (n_entries + 1)));
+    x.scan_scratch = static_cast<uint64_t*>(alloc(8ull * scan_scratch_words(n_entries + 1)));
+    x.total = static_cast<uint64_t*>(alloc(8));
+    if (!d_goff || !d_mem || !d_pg || !d_coff || !d_cg || !x.probe_off || !x.pair_off || !x.per_probe ||
+        !x.scan_scratch || !x.total) {
+        release();
+        return fail(ctx, SSJ_ENOMEM, "group expansion");
+    }
+    cudaError_t e = cudaMemcpyAsync(d_goff, gb->group_offsets, 8ull * (gb->n_groups + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_members) e = cudaMemcpyAsync(d_mem, gb->members, 4ull * n_members, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && gb->n_probe_groups) {
+        e = cudaMemcpyAsync(d_pg, gb->probe_groups, 4ull * gb->n_probe_groups, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_coff, gb->cand_offsets, 8ull * (gb->n_probe_groups + 1), cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess && n_cg) e = cudaMemcpyAsync(d_cg, gb->cand_groups, 4ull * n_cg, cudaMemcpyHostToDevice, s);
+    x.group_offsets = d_goff;
+    x.members = d_mem;
+    x.probe_groups = d_pg;
+    x.cand_offsets = d_coff;
+    x.cand_groups = d_cg;
+    uint64_t words[2] = {0, 0};
+    x.stage = 0;
+    if (e == cudaSuccess) e = expand_groups(x, s, ctx->num_sms, words);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(ctx, e, "group expansion (count)");
+    }
+    const uint64_t probes = words[0], pairs = words[1];
+    if (n_pairs) *n_pairs = pairs;
+    if (probes > 0xFFFFFFFFull) {
+        release();
+        return fail(ctx, SSJ_EINVAL, "too many expanded probes");
+    }
+    x.probe_ids = static_cast<uint32_t*>(alloc(4ull * probes));
+    x.cand_offsets_out = static_cast<uint64_t*>(alloc(8ull * (probes + 1)));
+    x.cand_ids = static_cast<uint32_t*>(alloc(4ull * pairs));
+    if (!x.probe_ids || !x.cand_offsets_out || !x.cand_ids) {
+        release();
+        return fail(ctx, SSJ_ENOMEM, "expanded candidates (%llu pairs)", (unsigned long long)pairs);
+    }
+    x.stage = 1;
+    e = expand_groups(x, s, ctx->num_sms, words);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(ctx, e, "group expansion (write)");
+    }
+    ssj_batch b;
+    memset(&b, 0, sizeof(b));
+    b.R = b.S = gb->coll;
+    b.p = gb->p;
+    b.q = gb->q;
+    b.n_probes = (uint32_t)probes;
+    b.probe_ids = x.probe_ids;
+    b.cand_offsets = x.cand_offsets_out;
+    b.cand_ids = x.cand_ids;
+    b.n_cands = pairs;
+    b.flags = (gb->flags & ~(SSJ_DEVICE_PTRS | SSJ_SORTED)) | SSJ_DEVICE_PTRS;
+    const bool count_only = (gb->flags & SSJ_COUNT_ONLY) != 0;
+    const bool dev_out = (gb->flags & SSJ_DEVICE_PTRS) != 0;
+    ssj_triple* d_out = nullptr;
+    uint64_t d_cap = 0;
+    if (!count_only) {
+        if (dev_out) {
+            d_out = out;
+            d_cap = cap;
+        } else {
+            d_cap = std::min<uint64_t>(cap, pairs);
+            d_out = static_cast<ssj_triple*>(alloc(sizeof(ssj_triple) * std::max<uint64_t>(d_cap, 1)));
+            if (!d_out) {
+                release();
+                return fail(ctx, SSJ_ENOMEM, "group join output");
+            }
+        }
+    }
+    uint64_t count = 0;
+    st = ssj_verify_batch(ctx, &b, d_out, d_cap, &count);
+    *n_out = count;
+    if (st != SSJ_OK && st != SSJ_ENOMEM) {
+        release();
+        return st;
+    }
+    if (!count_only) {
+        const uint64_t n_copy = std::min(count, cap);
+        if (dev_out) {
+            if ((gb->flags & SSJ_SORTED) && n_copy) {
+                std::vector<ssj_triple> h(n_copy);
+                e = cudaMemcpy(h.data(), out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost);
+                std::sort(h.begin(), h.end(), triple_less);
+                if (e == cudaSuccess) e = cudaMemcpy(out, h.data(), sizeof(ssj_triple) * n_copy, cudaMemcpyHostToDevice);
+            }
+        } else if (n_copy) {
+            e = cudaMemcpy(out, d_out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && (gb->flags & SSJ_SORTED)) std::sort(out, out + n_copy, triple_less);
+        }
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(ctx, e, "group join results");
+        }
+    }
+    release();
+    if (count > cap && !count_only)
+        return fail(ctx, SSJ_ENOMEM, "%llu result pairs, room for %llu", (unsigned long long)count,
+                    (unsigned long long)cap);
+    return SSJ_OK;
+}
+
+// ===========================================================================
 // Serving: continuous batching
 // ===========================================================================
 

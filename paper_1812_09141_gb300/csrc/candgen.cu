@@ -22,6 +22,7 @@
 //      the group offsets are contiguous in group order.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "arith.h"
@@ -251,6 +252,97 @@ __global__ void __launch_bounds__(kGenWarps * 32) generate_kernel(Params P, cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// GroupJoin expansion: entry k < n_probe_groups is a probe group with its
+// candidate groups (every member of the probe group against every member of
+// those groups); entry n_probe_groups + g is group g itself (each member
+// against the later members, when the group's prefix is not empty).
+// ---------------------------------------------------------------------------
+
+struct GroupArgs {
+    const uint64_t* group_offsets;
+    const uint32_t* members;
+    const uint32_t* probe_groups;
+    const uint64_t* cand_offsets;
+    const uint32_t* cand_groups;
+    uint32_t n_groups, n_probe_groups;
+};
+
+// one warp per entry: probes, pairs and (inter entries) candidates per probe
+__global__ void group_count_kernel(Params P, GroupArgs G, uint64_t* n_probes, uint64_t* n_pairs, uint64_t* per_probe) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t n_entries = G.n_probe_groups + G.n_groups;
+    for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_entries; k += warps) {
+        uint64_t probes = 0, pairs = 0, sum = 0;
+        if (k < G.n_probe_groups) {
+            const uint32_t g = G.probe_groups[k];
+            const uint64_t m = G.group_offsets[g + 1] - G.group_offsets[g];
+            for (uint64_t c = G.cand_offsets[k] + lane; c < G.cand_offsets[k + 1]; c += 32) {
+                const uint32_t h = G.cand_groups[c];
+                sum += G.group_offsets[h + 1] - G.group_offsets[h];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o);
+            probes = sum ? m : 0;
+            pairs = m * sum;
+        } else {
+            const uint32_t g = k - G.n_probe_groups;
+            const uint64_t b = G.group_offsets[g], m = G.group_offsets[g + 1] - b;
+            if (m >= 2 && prefix_len(P, P.desc[G.members[b]].y) > 0) {
+                probes = m - 1;
+                pairs = m * (m - 1) / 2;
+            }
+        }
+        if (lane == 0) {
+            n_probes[k] = probes;
+            n_pairs[k] = pairs;
+            per_probe[k] = sum;
+        }
+    }
+}
+
+// one warp per entry: write the expanded probes, offsets and candidates
+__global__ void group_write_kernel(GroupArgs G, const uint64_t* probe_off, const uint64_t* pair_off,
+                                   const uint64_t* per_probe, uint32_t* probe_ids, uint64_t* cand_offsets,
+                                   uint32_t* cand_ids) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t n_entries = G.n_probe_groups + G.n_groups;
+    for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_entries; k += warps) {
+        const uint64_t p0 = probe_off[k], np = probe_off[k + 1] - p0, c0 = pair_off[k];
+        if (np == 0) continue;
+        if (k < G.n_probe_groups) {
+            const uint32_t g = G.probe_groups[k];
+            const uint64_t b = G.group_offsets[g], S = per_probe[k];
+            for (uint64_t i = 0; i < np; ++i) {
+                if (lane == 0) {
+                    probe_ids[p0 + i] = G.members[b + i];
+                    cand_offsets[p0 + i] = c0 + i * S;
+                }
+                uint64_t w = c0 + i * S;  // the candidate groups' members, in order
+                for (uint64_t c = G.cand_offsets[k]; c < G.cand_offsets[k + 1]; ++c) {
+                    const uint32_t h = G.cand_groups[c];
+                    const uint64_t hb = G.group_offsets[h], hm = G.group_offsets[h + 1] - hb;
+                    for (uint64_t j = lane; j < hm; j += 32) cand_ids[w + j] = G.members[hb + j];
+                    w += hm;
+                }
+            }
+        } else {
+            const uint32_t g = k - G.n_probe_groups;
+            const uint64_t b = G.group_offsets[g], m = G.group_offsets[g + 1] - b;
+            for (uint64_t i = 0; i < np; ++i) {
+                const uint64_t w = c0 + i * (2 * m - i - 1) / 2;  // pairs of the members before i
+                if (lane == 0) {
+                    probe_ids[p0 + i] = G.members[b + i];
+                    cand_offsets[p0 + i] = w;
+                }
+                for (uint64_t j = i + 1 + lane; j < m; j += 32) cand_ids[w + (j - i - 1)] = G.members[b + j];
+            }
+        }
+    }
+}
+
 unsigned grid_for(uint64_t work, unsigned per_block, int num_sms, unsigned per_sm) {
     const uint64_t want = (work + per_block - 1) / per_block;
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)num_sms * per_sm));
@@ -320,6 +412,49 @@ cudaError_t candgen_run(const CandgenInput& in, cudaStream_t st, int num_sms, Ca
     e = cudaMemcpyAsync(host_word, in.out.packed, 8, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);  // *host_word: groups << 40 | candidates
+}
+
+cudaError_t expand_groups(const GroupExpand& x, cudaStream_t st, int num_sms, uint64_t* host_words) {
+    Params P;
+    memset(&P, 0, sizeof(P));
+    P.toks4 = x.toks4;
+    P.desc = x.desc;
+    P.sim = x.sim;
+    P.p = x.p;
+    P.q = x.q;
+    GroupArgs G;
+    G.group_offsets = x.group_offsets;
+    G.members = x.members;
+    G.probe_groups = x.probe_groups;
+    G.cand_offsets = x.cand_offsets;
+    G.cand_groups = x.cand_groups;
+    G.n_groups = x.n_groups;
+    G.n_probe_groups = x.n_probe_groups;
+    const uint64_t n_entries = (uint64_t)x.n_groups + x.n_probe_groups;
+    const unsigned tb = 256;
+    cudaError_t e;
+    if (x.stage == 0) {
+        e = cudaMemsetAsync(x.probe_off + n_entries, 0, 8, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(x.pair_off + n_entries, 0, 8, st);
+        if (e != cudaSuccess) return e;
+        if (n_entries)
+            group_count_kernel<<<grid_for(32 * n_entries, tb, num_sms, 8), tb, 0, st>>>(P, G, x.probe_off, x.pair_off,
+                                                                                         x.per_probe);
+        e = exclusive_scan_u64(x.probe_off, n_entries + 1, x.scan_scratch, x.total, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_words, x.total, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = exclusive_scan_u64(x.pair_off, n_entries + 1, x.scan_scratch, x.total, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_words + 1, x.total, 8, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return e;
+        return cudaStreamSynchronize(st);  // host_words: expanded probes, expanded pairs
+    }
+    if (n_entries)
+        group_write_kernel<<<grid_for(32 * n_entries, tb, num_sms, 8), tb, 0, st>>>(G, x.probe_off, x.pair_off,
+                                                                                     x.per_probe, x.probe_ids,
+                                                                                     x.cand_offsets_out, x.cand_ids);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // closing offset: the total number of pairs
+    return cudaMemcpyAsync(x.cand_offsets_out + host_words[0], x.pair_off + n_entries, 8, cudaMemcpyDeviceToDevice, st);
 }
 
 }  // namespace ssj

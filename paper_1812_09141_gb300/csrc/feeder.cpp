@@ -22,7 +22,7 @@
 #include <vector>
 
 #include "../../include/ssj_feeder.h"
-#include "arith.h"
+#include "filters.h"
 
 namespace ssj {
 void renumber_by_frequency(const uint64_t* offsets, const uint32_t* tokens, uint32_t n, std::vector<uint32_t>& out);
@@ -35,17 +35,6 @@ struct Block {
     std::vector<uint64_t> offs;    // probe.size()+1, relative
     std::vector<uint32_t> cands;   // original ids
 };
-
-// ceil(p*x/q) with 128-bit intermediate
-inline uint64_t ceil_mul_div(uint64_t x, uint64_t p, uint64_t q) {
-    return (uint64_t)(((unsigned __int128)p * x + q - 1) / q);
-}
-
-// floor(q*x/p) with 128-bit intermediate, saturated to 32 bits
-inline uint32_t floor_mul_div_sat(uint64_t x, uint64_t q, uint64_t p) {
-    const unsigned __int128 v = (unsigned __int128)q * x / p;
-    return v > 0xFFFFFFFFu ? 0xFFFFFFFFu : (uint32_t)v;
-}
 
 constexpr uint32_t kPruned = 0xFFFFFFFFu;
 
@@ -111,50 +100,12 @@ struct ssj_feeder {
     uint64_t emitted = 0;
     uint32_t probed = 0;
 
-    // Least overlap a set of size len shares with any partner that can reach
-    // the threshold: Jaccard t|x|, Dice t|x|/(2-t), Cosine t^2|x|, plain
-    // overlap t (rounded up).  It is also the smallest partner size the
-    // length filter admits for a probe of size len.
-    uint64_t min_overlap(uint64_t len) const {
-        switch (sim) {
-            case 1: return ceil_mul_div(len, p, 2ull * q - p);
-            case 2: return (uint64_t)(((unsigned __int128)p * p * len + (unsigned __int128)q * q - 1) /
-                                      ((unsigned __int128)q * q));
-            case 3: return ((uint64_t)p + q - 1) / q;
-            default: return ceil_mul_div(len, p, q);
-        }
-    }
+    ssj::Filters flt;  // prefix and length filters of the function and threshold
 
-    // Largest partner size the length filter admits for a probe of size len.
-    uint32_t max_partner(uint64_t len) const {
-        switch (sim) {
-            case 1: return floor_mul_div_sat(len, 2ull * q - p, p);
-            case 2: return (uint32_t)std::min<unsigned __int128>(
-                        (unsigned __int128)q * q * len / ((unsigned __int128)p * p), 0xFFFFFFFFu);
-            case 3: return 0xFFFFFFFFu;
-            default: return floor_mul_div_sat(len, q, p);
-        }
-    }
-
-    // Equivalent overlap of a pair (Table "Similarity Functions"), for the
-    // PPJoin bound.
-    uint32_t required(uint32_t nr, uint32_t ns) const {
-        switch (sim) {
-            case 1: return ssj::required_overlap_magic(nr, ns, p, 2 * q, ssj::div_magic(2ull * q));
-            case 2: return ssj::required_overlap_cosine(p, q, nr, ns);
-            case 3: return (uint32_t)(((uint64_t)p + q - 1) / q);
-            default: return ssj::required_overlap_magic(nr, ns, p, p + q, ssj::div_magic((uint64_t)p + q));
-        }
-    }
-
-    // Prefix of len - min_overlap + 1 tokens (none if no partner can reach t).
-    uint32_t prefix_len(uint32_t len) const {
-        if (len == 0) return 0;
-        const uint64_t need = min_overlap(len);
-        if (need > len) return 0;
-        const uint64_t pl = (uint64_t)len + 1 - need;
-        return pl > len ? len : (uint32_t)pl;
-    }
+    uint64_t min_overlap(uint64_t len) const { return flt.min_overlap(len); }
+    uint32_t max_partner(uint64_t len) const { return flt.max_partner(len); }
+    uint32_t required(uint32_t nr, uint32_t ns) const { return flt.required(nr, ns); }
+    uint32_t prefix_len(uint32_t len) const { return flt.prefix_len(len); }
 
     // Candidates of one probe: index entries in positions [lo, hi) sharing a
     // prefix token with r, deduplicated (stamp) or, with PPJoin, counted
@@ -285,12 +236,7 @@ extern "C" ssj_status ssj_feeder_create_ex(const uint64_t* r_offsets, const uint
                                            const ssj_feeder_opts* opts, ssj_feeder** out) {
     if (!opts || !out) return SSJ_EINVAL;
     const uint32_t sim = opts->sim, p = opts->p, q = opts->q;
-    if (sim > 3 || (opts->flags & ~SSJ_FEEDER_PPJOIN)) return SSJ_EINVAL;
-    if (sim == 3) {
-        if (p == 0 || q == 0 || p >= (1u << 31) || q >= (1u << 31)) return SSJ_EINVAL;
-    } else if (p == 0 || p > q || q >= (1u << 31)) {
-        return SSJ_EINVAL;
-    }
+    if (!ssj::Filters::valid(sim, p, q) || (opts->flags & ~SSJ_FEEDER_PPJOIN)) return SSJ_EINVAL;
     if (check_sets(r_offsets, r_tokens, n_r) != SSJ_OK) return SSJ_EINVAL;
     const bool rs = s_offsets != nullptr;
     if (rs && check_sets(s_offsets, s_tokens, n_s) != SSJ_OK) return SSJ_EINVAL;
@@ -300,6 +246,9 @@ extern "C" ssj_status ssj_feeder_create_ex(const uint64_t* r_offsets, const uint
         f->p = p;
         f->q = q;
         f->sim = sim;
+        f->flt.sim = sim;
+        f->flt.p = p;
+        f->flt.q = q;
         f->rs = rs;
         f->ppjoin = (opts->flags & SSJ_FEEDER_PPJOIN) != 0;
         if (!rs) {

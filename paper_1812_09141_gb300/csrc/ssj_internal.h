@@ -206,6 +206,36 @@ struct CandgenInput {
 cudaError_t candgen_run(const CandgenInput& in, cudaStream_t st, int num_sms, CandgenIndex* ix,
                         uint64_t* host_word);
 
+// GroupJoin expansion on the device (candgen.cu).  Entries: the probe
+// groups, then every group (pairs inside it).  probe_off / pair_off /
+// per_probe hold n_entries + 1 words; scan_scratch
+// scan_scratch_words(n_entries + 1); total one word.
+struct GroupExpand {
+    const uint4* toks4;
+    const uint2* desc;
+    uint32_t sim, p, q;
+    const uint64_t* group_offsets;
+    const uint32_t* members;
+    const uint32_t* probe_groups;
+    const uint64_t* cand_offsets;
+    const uint32_t* cand_groups;
+    uint32_t n_groups, n_probe_groups;
+    uint64_t* probe_off;
+    uint64_t* pair_off;
+    uint64_t* per_probe;
+    uint64_t* scan_scratch;
+    uint64_t* total;
+    int stage;                 // 0: count and scan; 1: write
+    uint32_t* probe_ids;       // stage 1 outputs: the expanded grouped batch
+    uint64_t* cand_offsets_out;
+    uint32_t* cand_ids;
+};
+
+// Stage 0 waits and leaves (expanded probes, expanded pairs) in
+// host_words[0..1] (pinned); stage 1 enqueues the writes (host_words[0]
+// must still hold the probe count).
+cudaError_t expand_groups(const GroupExpand& x, cudaStream_t st, int num_sms, uint64_t* host_words);
+
 // One launch of the read-bandwidth probe: `passes` sweeps over bytes (a
 // multiple of 16) at buf, on st; sink is a device word the kernel may write.
 cudaError_t read_probe(const void* buf, uint64_t bytes, uint32_t passes, uint32_t* sink, int num_sms,

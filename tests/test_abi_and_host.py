@@ -160,6 +160,40 @@ def test_feeder_ppjoin_prunes_without_losing_results(sim, pq):
     assert pruned == 0 if sim == oracle.OVERLAP else pruned > 0
 
 
+@pytest.mark.parametrize("sim,pq", [(oracle.JACCARD, (4, 5)), (oracle.JACCARD, (3, 5)), (oracle.DICE, (4, 5)),
+                                    (oracle.COSINE, (7, 10)), (oracle.OVERLAP, (8, 1))])
+def test_group_candidates_expand_to_allpairs_candidates(sim, pq):
+    """GroupJoin: expanding the group candidates (probe group x candidate group members, and the
+    pairs inside groups with a non-empty prefix) gives exactly the AllPairs candidates."""
+    for frac, edits in ((0.3, 0), (0.15, 2)):
+        spec = synth.tiny_self_join(seed=1001, n=700)
+        spec.plant_frac, spec.plant_edits = frac, edits
+        c = synth.collection(spec)
+        g = ssj.group_candidates(c.offsets, c.tokens, *pq, sim=sim)
+        go, mem = g.group_offsets.astype(np.int64), g.members
+        sizes = np.diff(c.offsets.astype(np.int64))
+        assert sorted(mem.tolist()) == list(range(c.n))
+        pairs = set()
+        for k, pgi in enumerate(g.probe_groups):
+            for cgi in g.cand_groups[g.cand_offsets[k]:g.cand_offsets[k + 1]]:
+                assert cgi < pgi  # earlier groups only
+                for a in mem[go[pgi]:go[pgi + 1]]:
+                    for b in mem[go[cgi]:go[cgi + 1]]:
+                        pairs.add((min(int(a), int(b)), max(int(a), int(b))))
+        for gi in range(len(go) - 1):
+            A = mem[go[gi]:go[gi + 1]]
+            size = int(sizes[A[0]])
+            assert all(int(sizes[x]) == size for x in A)
+            nonempty = size > 0 and (sim != oracle.OVERLAP or -(-pq[0] // pq[1]) <= size)
+            if nonempty:
+                pairs |= {(min(int(A[i]), int(A[j])), max(int(A[i]), int(A[j])))
+                          for i in range(len(A)) for j in range(i + 1, len(A))}
+        assert len(pairs) == g.n_pairs
+        pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, *pq, n_threads=2, sim=sim)
+        assert pairs == _pairs(pr, co, ci)
+        assert oracle.allpairs_self(c.offsets, c.tokens, *pq, sim=sim)[1] == g.n_pairs
+
+
 def test_feeder_threads_and_chunking_do_not_change_candidates():
     c = _planted(n=800)
     ref = ssj.feeder_all(c.offsets, c.tokens, 3, 5, n_threads=1, chunk=1 << 20)

@@ -97,3 +97,31 @@ def test_self_join_degenerate_collections(ctx):
             assert np.array_equal(ssj.triples_to_array(got), want), lists
         finally:
             ssj.ssj_unload_collection(ctx, h)
+
+
+@pytest.mark.parametrize("sim,pq", CASES)
+def test_group_join_expanded_on_the_device(ctx, sim, pq):
+    """GroupJoin candidates expanded and verified on the device equal the oracle's AllPairs join,
+    and the expanded pairs are exactly the AllPairs candidates."""
+    specs = []
+    for frac, edits in ((0.3, 0), (0.2, 2)):
+        spec = synth.tiny_self_join(seed=1001, n=800)
+        spec.plant_frac, spec.plant_edits = frac, edits
+        specs.append(spec)
+    short = synth.short_sets(n=20_000)
+    short.plant_frac, short.plant_edits = 0.2, 0
+    specs.append(short)
+    for spec in specs:
+        c = synth.collection(spec)
+        h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens, ssj.SSJ_RENUMBER_BY_FREQ)
+        try:
+            want, want_cands = oracle.allpairs_self(c.offsets, c.tokens, *pq, sim=sim)
+            g = ssj.group_candidates(c.offsets, c.tokens, *pq, sim=sim)
+            assert g.n_pairs == want_cands
+            got, n_pairs = ssj.ssj_verify_groups(ctx, h, *pq, g, SIM_FLAGS[sim])
+            assert n_pairs == want_cands
+            assert np.array_equal(ssj.triples_to_array(got), oracle.sort_triples(want)), (sim, pq, c.n)
+            cnt, _ = ssj.ssj_verify_groups(ctx, h, *pq, g, SIM_FLAGS[sim] | ssj.SSJ_COUNT_ONLY | ssj.SSJ_FORCE_WARP)
+            assert cnt == len(want)
+        finally:
+            ssj.ssj_unload_collection(ctx, h)
