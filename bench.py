@@ -343,6 +343,27 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# --------------------------------------------------------------------------- ranks
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest value over the ranks of the job (every rank gets it), then a barrier.
+    Each rank verifies the whole workload on its own GPU (replicas: the path has no exchange
+    step), so the job's time is its slowest rank's."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_value(pairs_per_step: int, steps: int, world: int, total_s: float) -> float:
+    """Pairs/s of the whole job: every rank verifies pairs_per_step per step (weak scaling)."""
+    return pairs_per_step * steps * world / total_s
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def run_ours(args, rank, world, local_rank):
@@ -423,12 +444,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     launches, plan_ms, verify_ms = ssj.ssj_profile_read(ctx)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     result_counts = [int(x) for x in counts.cpu().tolist()]
 
     # the same launch replayed from a CUDA graph (captured by the library)
@@ -791,7 +807,7 @@ def main():
     total_s = res["total_ms"] / 1e3
     input_bytes = (sum(4 * len(c.tokens) + 8 * c.n for c in colls)
                    + sum(4 * len(b[3]) + 8 * len(b[4]) + 4 * len(b[5]) for b in batches))
-    value = pairs_step * args.steps * world / total_s
+    value = whole_job_value(pairs_step, args.steps, world, total_s)
     peak, peak_kind = measured_hbm_peak()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,

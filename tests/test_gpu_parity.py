@@ -347,3 +347,45 @@ def test_full_long_sets_sampled(ctx):
         ok, _, _, _ = oracle.verify_pair(c.set(r), c.set(s), 3, 5)
         assert ok == ((min(r, s), max(r, s)) in keys)
     ssj.ssj_unload_collection(ctx, h)
+
+
+def test_full_serving_collection_and_served_slices(ctx):
+    """The 1,000,000-set serving collection: the whole self-join at t in {0.7, 0.8, 0.9} exact
+    against the oracle, then request-sized slices (1e3..1e7 pairs) of its candidates submitted
+    through the serving path, each equal to the oracle on that slice."""
+    c = synth.collection(synth.serving_collection())
+    h = load(ctx, c, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
+    try:
+        batches = {}
+        for p, q in [(7, 10), (4, 5), (9, 10)]:
+            b = feeder_batch(c, p, q, threads=16)
+            batches[(p, q)] = b
+            want = ora(c, c, True, p, q, b)
+            assert np.array_equal(gpu(ctx, h, h, p, q, b), want), (p, q)
+        b = batches[(7, 10)]
+        co = b.cand_offsets.astype(np.int64)
+        rng = np.random.default_rng(5)
+        tickets = []
+        sctx = ssj.ssj_create(0, mem_budget_bytes=1 << 30, max_inflight=4)
+        hs = ssj.ssj_load_collection(sctx, c.offsets, c.tokens, ssj.SSJ_RENUMBER_BY_FREQ)
+        try:
+            for want_pairs in (1_000, 30_000, 1_000_000, 8_000_000):
+                a = int(rng.integers(0, len(b.probe_ids) // 2))
+                e = int(np.searchsorted(co, co[a] + want_pairs, side="left"))
+                e = max(a + 1, min(e, len(b.probe_ids)))
+                sl = synth.Batch(b.probe_ids[a:e], (co[a:e + 1] - co[a]).astype(np.uint64),
+                                 b.cand_ids[co[a]:co[e]])
+                t = None
+                while t is None:
+                    t = ssj.ssj_submit(sctx, hs, hs, 7, 10, sl.probe_ids, sl.cand_offsets, sl.cand_ids)
+                    if t is None:
+                        for tt, ww in tickets:
+                            ssj.ssj_poll(sctx, tt, timeout_ms=100)
+                tickets.append((t, ora(c, c, True, 7, 10, sl)))
+            for t, want in tickets:
+                assert ssj.ssj_poll(sctx, t, timeout_ms=-1)
+                assert np.array_equal(ssj.triples_to_array(ssj.ssj_results(sctx, t)), want)
+        finally:
+            ssj.ssj_destroy(sctx)
+    finally:
+        ssj.ssj_unload_collection(ctx, h)
