@@ -280,3 +280,37 @@ def test_verify_batches_host_direct_equals_copies(ctx):
             assert np.array_equal(ssj.triples_to_array(g), ssj.triples_to_array(w))
     finally:
         ssj.ssj_unload_collection(ctx, h)
+
+
+def test_verify_batches_splits_large_batches_into_pipelined_parts(ctx):
+    """A batch of about 2M candidates is cut at probe boundaries into parts whose copies overlap
+    the verification of the previous part; results equal the single call's, also for a too-small
+    capacity (the first cap triples written, SSJ_ENOMEM) and with SSJ_HOST_DIRECT."""
+    import torch
+    spec = synth.tiny_self_join(seed=2024, n=2000)
+    spec.plant_frac, spec.plant_edits = 0.2, 2
+    c = synth.collection(spec)
+    short = synth.collection(synth.short_sets(n=15_000))
+    h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens)
+    hs = ssj.ssj_load_collection(ctx, short.offsets, short.tokens)
+    pinned = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    try:
+        ap = synth.all_pairs_batch(c.n)
+        assert ap.n_cands > (1 << 20)
+        fb = synth.Batch(*ssj.feeder_all(short.offsets, short.tokens, 3, 5, n_threads=4))
+        arrs = [pinned(x) for x in (ap.probe_ids, ap.cand_offsets, ap.cand_ids)]
+        batches = [(hs, hs, 3, 5, fb.probe_ids, fb.cand_offsets, fb.cand_ids, 0), (h, h, 1, 2, *arrs, 0),
+                   (h, h, 3, 5, *arrs, ssj.SSJ_SIM_COSINE)]
+        want = [ssj.triples_to_array(ssj.ssj_verify_batch(ctx, *b[:7], flags=b[7])) for b in batches]
+        for extra in (0, ssj.SSJ_HOST_DIRECT):
+            got = ssj.ssj_verify_batches(ctx, [b[:7] + (b[7] | extra,) for b in batches])
+            for g, w in zip(got, want):
+                assert np.array_equal(ssj.triples_to_array(g), w)
+        assert len(want[1]) > 100
+        cap = len(want[1]) - 7
+        with pytest.raises(ssj.SsjError) as ei:
+            ssj.ssj_verify_batches(ctx, batches[1:2], caps=[cap])
+        assert ei.value.status == ssj.SSJ_ENOMEM
+    finally:
+        ssj.ssj_unload_collection(ctx, h)
+        ssj.ssj_unload_collection(ctx, hs)
