@@ -128,11 +128,6 @@ struct ssj_ctx {
     uint64_t* h_count = nullptr;  // pinned
     uint32_t* h_err = nullptr;    // pinned
     Counters* last_ctr = nullptr;
-    // ssj_verify_batches: copy stream, one event per launch group, pinned host staging
-    cudaStream_t copy_stream = nullptr;
-    std::vector<cudaEvent_t> group_ev;
-    uint64_t* h_stage = nullptr;
-    uint64_t h_stage_cap = 0;
     // kernel timing (SSJ_CTX_PROFILE): events around plan and verify of each launch
     bool profile = false;
     std::vector<cudaEvent_t> prof_ev;  // 3 per recorded launch
@@ -432,9 +427,7 @@ extern "C" void ssj_destroy(ssj_ctx* ctx) {
     cudaFree(ctx->io);
     cudaFreeHost(ctx->h_count);
     cudaFreeHost(ctx->h_err);
-    cudaFreeHost(ctx->h_stage);
-    for (cudaEvent_t ev : ctx->group_ev) cudaEventDestroy(ev);
-    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+
     for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -743,9 +736,14 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
                                          ssj_triple* const* outs, const uint64_t* caps, uint64_t* n_outs) {
     if (!ctx || (n_batches && (!batches || !outs || !caps || !n_outs))) return fail(ctx, SSJ_EINVAL, "NULL argument");
     if (n_batches == 0) return SSJ_OK;
-    std::vector<Instance> proto(n_batches);
-    std::vector<uint64_t> n_cands(n_batches);
-    uint64_t total = 0;
+    std::vector<Instance> table(n_batches);
+    std::vector<uint64_t> n_cands(n_batches), io_off(n_batches);
+    LaunchShape sh;
+    sh.n_inst = n_batches;
+    sh.n_tiles = 0;
+    sh.total_probes = 0;
+    sh.total_cands = 0;
+    size_t off = align256(sizeof(uint64_t) * n_batches);  // counts first
     for (uint32_t i = 0; i < n_batches; ++i) {
         const ssj_batch* b = &batches[i];
         if (b->flags & SSJ_DEVICE_PTRS) return fail(ctx, SSJ_EINVAL, "batch %u: host pointers expected", i);
@@ -755,207 +753,84 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
         st = validate_host_batch(ctx, b, &n_cands[i]);
         if (st != SSJ_OK) return st;
         if (caps[i] && !outs[i] && !(b->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "batch %u: NULL output", i);
-        proto[i] = make_instance(b, *R, *S, n_cands[i]);
-        total += n_cands[i];
+        table[i] = make_instance(b, *R, *S, n_cands[i]);
+        table[i].tile_base = sh.n_tiles;
+        const uint64_t tiles = ((uint64_t)b->n_probes + 31) / 32;
+        if ((uint64_t)sh.n_tiles + tiles > 0x7FFFFFFull) return fail(ctx, SSJ_EINVAL, "too many probes in one call");
+        sh.n_tiles += (uint32_t)tiles;
+        sh.total_probes += b->n_probes;
+        sh.total_cands += n_cands[i];
+        // device staging of this batch: probe ids, offsets, candidate ids, output
+        io_off[i] = off;
+        off += align256(4ull * std::max<uint32_t>(b->n_probes, 1)) + align256(8ull * (b->n_probes + 1)) +
+               align256(4ull * std::max<uint64_t>(n_cands[i], 1));
+        const uint64_t cap = (b->flags & SSJ_COUNT_ONLY) ? 0 : std::min(caps[i], n_cands[i]);
+        off += align256(sizeof(ssj_triple) * std::max<uint64_t>(cap, 1));
     }
-    // Parts: probe ranges of at most about `target` candidates (large batches are cut at probe
-    // boundaries); launch groups: consecutive parts of at least `target` candidates.  The
-    // copies of group k+1 run on a copy stream while group k is verified.
-    const uint64_t target = std::max<uint64_t>(total / 4, 1ull << 20);
-    struct Part {
-        uint32_t batch, a, e;   // probes [a, e) of the batch
-        uint64_t c0, c1;        // their candidates
-        uint64_t io;            // device staging offset
-        uint64_t cap;           // output capacity on the device
-        bool rebased;           // offsets staged from the host copy (the part does not start at probe 0)
-        uint64_t h_offs;        // offset of its rebased offsets in the pinned staging (words)
-    };
-    std::vector<Part> parts;
-    for (uint32_t i = 0; i < n_batches; ++i) {
-        const ssj_batch* b = &batches[i];
-        const uint32_t np = b->n_probes;
-        uint32_t a = 0;
-        do {
-            uint32_t e = np;
-            if (n_cands[i] - (np ? b->cand_offsets[a] : 0) > target) {
-                // last probe boundary with at most target candidates after cand_offsets[a] (at least one probe)
-                const uint64_t lim = b->cand_offsets[a] + target;
-                const uint64_t* it = std::upper_bound(b->cand_offsets + a + 1, b->cand_offsets + np + 1, lim);
-                e = (uint32_t)std::max<ptrdiff_t>(a + 1, (it - b->cand_offsets) - 1);
-            }
-            Part pt;
-            pt.batch = i;
-            pt.a = a;
-            pt.e = e;
-            pt.c0 = np ? b->cand_offsets[a] : 0;
-            pt.c1 = np ? b->cand_offsets[e] : 0;
-            pt.rebased = !(a == 0 && e == np);
-            pt.h_offs = 0;
-            parts.push_back(pt);
-            a = e;
-        } while (a < np);
-    }
-    std::vector<std::pair<size_t, size_t>> groups;  // [first part, last part)
-    for (size_t k = 0; k < parts.size();) {
-        size_t j = k;
-        uint64_t acc = 0;
-        while (j < parts.size() && (j == k || acc < target)) acc += parts[j].c1 - parts[j].c0, ++j;
-        groups.emplace_back(k, j);
-        k = j;
-    }
-    // device staging: counts (one per part), then per part probe ids, offsets, candidates, output
-    size_t off = align256(sizeof(uint64_t) * parts.size());
-    uint64_t host_words = 0;
-    for (Part& pt : parts) {
-        const uint32_t np = pt.e - pt.a;
-        const uint64_t nc = pt.c1 - pt.c0;
-        pt.io = off;
-        off += align256(4ull * std::max<uint32_t>(np, 1)) + align256(8ull * (np + 1)) +
-               align256(4ull * std::max<uint64_t>(nc, 1));
-        pt.cap = (batches[pt.batch].flags & SSJ_COUNT_ONLY) ? 0 : std::min(caps[pt.batch], nc);
-        off += align256(sizeof(ssj_triple) * std::max<uint64_t>(pt.cap, 1));
-        if (pt.rebased) {
-            pt.h_offs = host_words;
-            host_words += np + 1;
-        }
-    }
-    // pinned host staging: rebased offsets, then one instance table per group
-    const uint64_t table_words = (sizeof(Instance) * parts.size() + 7) / 8 + groups.size();
     DeviceGuard g(ctx->device);
     ssj_status st = ensure_device_buffer(ctx, &ctx->io, &ctx->io_bytes, off);
     if (st != SSJ_OK) return st;
-    st = ensure_pinned(ctx, &ctx->h_stage, &ctx->h_stage_cap, host_words + table_words + groups.size() + 1);
+    st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(sh, ctx->num_sms));
     if (st != SSJ_OK) return st;
-    size_t ws_need = 0;
-    std::vector<LaunchShape> shapes(groups.size());
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-        LaunchShape& sh = shapes[gi];
-        sh.n_inst = (uint32_t)(groups[gi].second - groups[gi].first);
-        sh.n_tiles = 0;
-        sh.total_probes = 0;
-        sh.total_cands = 0;
-        for (size_t k = groups[gi].first; k < groups[gi].second; ++k) {
-            const uint64_t tiles = ((uint64_t)(parts[k].e - parts[k].a) + 31) / 32;
-            if ((uint64_t)sh.n_tiles + tiles > 0x7FFFFFFull) return fail(ctx, SSJ_EINVAL, "too many probes in one call");
-            sh.n_tiles += (uint32_t)tiles;
-            sh.total_probes += parts[k].e - parts[k].a;
-            sh.total_cands += parts[k].c1 - parts[k].c0;
-        }
-        ws_need = std::max(ws_need, workspace_bytes(sh, ctx->num_sms));
-    }
-    st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, ws_need);
-    if (st != SSJ_OK) return st;
-    if (!ctx->copy_stream && groups.size() > 1) {
-        CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-    }
-    while (ctx->group_ev.size() < groups.size()) {
-        cudaEvent_t ev;
-        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        ctx->group_ev.push_back(ev);
-    }
     cudaStream_t s = ctx->stream;
-    cudaStream_t cs = groups.size() > 1 ? ctx->copy_stream : s;
     char* base = static_cast<char*>(ctx->io);
     uint64_t* d_counts = reinterpret_cast<uint64_t*>(base);
-    uint64_t* hs = ctx->h_stage;
-    Instance* h_tables = reinterpret_cast<Instance*>(hs + host_words);
-    uint32_t* h_errs = reinterpret_cast<uint32_t*>(hs + host_words + table_words);
-    std::vector<Instance> table(parts.size());
-    if (groups.size() > 1) {
-        // the copy stream starts after everything already queued on the compute stream
-        CUDA_TRY(ctx, cudaEventRecord(ctx->group_ev[0], s));
-        CUDA_TRY(ctx, cudaStreamWaitEvent(cs, ctx->group_ev[0], 0));
+    for (uint32_t i = 0; i < n_batches; ++i) {
+        const ssj_batch* b = &batches[i];
+        char* p = base + io_off[i];
+        uint32_t* d_probe = reinterpret_cast<uint32_t*>(p); p += align256(4ull * std::max<uint32_t>(b->n_probes, 1));
+        uint64_t* d_offs = reinterpret_cast<uint64_t*>(p);  p += align256(8ull * (b->n_probes + 1));
+        uint32_t* d_cand = reinterpret_cast<uint32_t*>(p);  p += align256(4ull * std::max<uint64_t>(n_cands[i], 1));
+        // SSJ_HOST_DIRECT: pinned arrays the device can address are read by the kernels
+        // themselves (over the host link), with no staging copy
+        const void* dv_probe = (b->flags & SSJ_HOST_DIRECT) ? device_view(b->probe_ids) : nullptr;
+        const void* dv_offs = (b->flags & SSJ_HOST_DIRECT) ? device_view(b->cand_offsets) : nullptr;
+        const void* dv_cand = (b->flags & SSJ_HOST_DIRECT) ? device_view(b->cand_ids) : nullptr;
+        if (b->n_probes && !dv_probe)
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_probe, b->probe_ids, 4ull * b->n_probes, cudaMemcpyHostToDevice, s));
+        if (b->n_probes && !dv_offs)
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_offs, b->cand_offsets, 8ull * (b->n_probes + 1), cudaMemcpyHostToDevice, s));
+        if (n_cands[i] && !dv_cand)
+            CUDA_TRY(ctx, cudaMemcpyAsync(d_cand, b->cand_ids, 4ull * n_cands[i], cudaMemcpyHostToDevice, s));
+        Instance& I = table[i];
+        I.probe_ids = dv_probe ? static_cast<const uint32_t*>(dv_probe) : d_probe;
+        I.cand_offsets = dv_offs ? static_cast<const uint64_t*>(dv_offs) : d_offs;
+        I.cand_ids = dv_cand ? static_cast<const uint32_t*>(dv_cand) : d_cand;
+        I.out = reinterpret_cast<ssj_triple*>(p);
+        I.cap = (b->flags & SSJ_COUNT_ONLY) ? 0 : std::min(caps[i], n_cands[i]);
+        I.count = reinterpret_cast<unsigned long long*>(d_counts + i);
     }
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-        for (size_t k = groups[gi].first; k < groups[gi].second; ++k) {
-            Part& pt = parts[k];
-            const ssj_batch* b = &batches[pt.batch];
-            const uint32_t np = pt.e - pt.a;
-            const uint64_t nc = pt.c1 - pt.c0;
-            char* p = base + pt.io;
-            uint32_t* d_probe = reinterpret_cast<uint32_t*>(p); p += align256(4ull * std::max<uint32_t>(np, 1));
-            uint64_t* d_offs = reinterpret_cast<uint64_t*>(p);  p += align256(8ull * (np + 1));
-            uint32_t* d_cand = reinterpret_cast<uint32_t*>(p);  p += align256(4ull * std::max<uint64_t>(nc, 1));
-            const bool direct = (b->flags & SSJ_HOST_DIRECT) != 0;
-            const void* dv_probe = direct && np ? device_view(b->probe_ids + pt.a) : nullptr;
-            const void* dv_offs = direct && np && !pt.rebased ? device_view(b->cand_offsets) : nullptr;
-            const void* dv_cand = direct && nc ? device_view(b->cand_ids + pt.c0) : nullptr;
-            if (np && !dv_probe)
-                CUDA_TRY(ctx, cudaMemcpyAsync(d_probe, b->probe_ids + pt.a, 4ull * np, cudaMemcpyHostToDevice, cs));
-            if (np && !dv_offs) {
-                const uint64_t* src = b->cand_offsets;
-                if (pt.rebased) {
-                    uint64_t* h = hs + pt.h_offs;
-                    for (uint32_t k2 = 0; k2 <= np; ++k2) h[k2] = b->cand_offsets[pt.a + k2] - pt.c0;
-                    src = h;
-                }
-                CUDA_TRY(ctx, cudaMemcpyAsync(d_offs, src, 8ull * (np + 1), cudaMemcpyHostToDevice, cs));
-            }
-            if (nc && !dv_cand)
-                CUDA_TRY(ctx, cudaMemcpyAsync(d_cand, b->cand_ids + pt.c0, 4ull * nc, cudaMemcpyHostToDevice, cs));
-            Instance I = proto[pt.batch];
-            I.probe_ids = dv_probe ? static_cast<const uint32_t*>(dv_probe) : d_probe;
-            I.cand_offsets = dv_offs ? static_cast<const uint64_t*>(dv_offs) : d_offs;
-            I.cand_ids = dv_cand ? static_cast<const uint32_t*>(dv_cand) : d_cand;
-            I.n_probes = np;
-            I.n_cands = nc;
-            I.out = reinterpret_cast<ssj_triple*>(p);
-            I.cap = pt.cap;
-            I.count = reinterpret_cast<unsigned long long*>(d_counts + k);
-            table[k] = I;
-        }
-        if (groups.size() > 1) CUDA_TRY(ctx, cudaEventRecord(ctx->group_ev[gi], cs));
-    }
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-        if (groups.size() > 1) CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->group_ev[gi], 0));
-        VerifyArgs a;
-        memset(&a, 0, sizeof(a));
-        a.thread_max_key = ctx->thread_max_key;
-        a.lane_max_key = ctx->lane_max_key;
-        a.warp_max_key = ctx->warp_max_key;
-        bind_workspace(a, ctx->ws, shapes[gi], ctx->num_sms);
-        a.table = a.table_out;
-        Instance* ht = h_tables + groups[gi].first;
-        uint32_t tb = 0, tile = 0;
-        for (size_t k = groups[gi].first; k < groups[gi].second; ++k, ++tb) {
-            ht[tb] = table[k];
-            ht[tb].tile_base = tile;
-            tile += (ht[tb].n_probes + 31) / 32;
-        }
-        CUDA_TRY(ctx, cudaMemcpyAsync(a.table_out, ht, sizeof(Instance) * tb, cudaMemcpyHostToDevice, s));
-        ctx->last_ctr = a.ctr;
-        cudaError_t e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_verify");
-        CUDA_TRY(ctx, cudaMemcpyAsync(h_errs + gi, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    }
-    std::vector<uint64_t> counts(parts.size());
-    CUDA_TRY(ctx, cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint64_t) * parts.size(), cudaMemcpyDeviceToHost, s));
+    VerifyArgs a;
+    memset(&a, 0, sizeof(a));
+    a.thread_max_key = ctx->thread_max_key;
+    a.lane_max_key = ctx->lane_max_key;
+    a.warp_max_key = ctx->warp_max_key;
+    bind_workspace(a, ctx->ws, sh, ctx->num_sms);
+    a.table = a.table_out;
+    CUDA_TRY(ctx, cudaMemcpyAsync(a.table_out, table.data(), sizeof(Instance) * n_batches, cudaMemcpyHostToDevice, s));
+    ctx->last_ctr = a.ctr;
+    cudaError_t e = launch_verify(a, s, ctx->num_sms, ctx->block_threads, profile_events(ctx));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch_verify");
+    std::vector<uint64_t> counts(n_batches);
+    CUDA_TRY(ctx, cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint64_t) * n_batches, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_err, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    uint32_t derr = 0;
-    for (size_t gi = 0; gi < groups.size(); ++gi) derr |= h_errs[gi];
+    const uint32_t derr = *ctx->h_err;
     if (derr & ERR_GUARD) return fail(ctx, SSJ_EDEVICE, "internal loop bound reached on the device (code %u)", derr);
     if (derr) return fail(ctx, SSJ_EINVAL, "batch rejected by the device checks (code %u)", derr);
     bool short_cap = false;
-    std::vector<uint64_t> written(n_batches, 0);
-    for (uint32_t i = 0; i < n_batches; ++i) n_outs[i] = 0;
-    for (size_t k = 0; k < parts.size(); ++k) {
-        const Part& pt = parts[k];
-        const uint32_t i = pt.batch;
-        n_outs[i] += counts[k];
+    for (uint32_t i = 0; i < n_batches; ++i) {
+        n_outs[i] = counts[i];
         if (batches[i].flags & SSJ_COUNT_ONLY) continue;
-        const uint64_t room = caps[i] - written[i];
-        const uint64_t n_copy = std::min(std::min(counts[k], room), pt.cap);
+        const uint64_t n_copy = std::min(counts[i], caps[i]);
         if (n_copy)
-            CUDA_TRY(ctx, cudaMemcpyAsync(outs[i] + written[i], table[k].out, sizeof(ssj_triple) * n_copy,
-                                          cudaMemcpyDeviceToHost, s));
-        written[i] += n_copy;
+            CUDA_TRY(ctx, cudaMemcpyAsync(outs[i], table[i].out, sizeof(ssj_triple) * n_copy, cudaMemcpyDeviceToHost, s));
+        short_cap |= counts[i] > caps[i];
     }
     CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    for (uint32_t i = 0; i < n_batches; ++i) {
-        short_cap |= n_outs[i] > caps[i] && !(batches[i].flags & SSJ_COUNT_ONLY);
+    for (uint32_t i = 0; i < n_batches; ++i)
         if ((batches[i].flags & SSJ_SORTED) && !(batches[i].flags & SSJ_COUNT_ONLY))
-            std::sort(outs[i], outs[i] + written[i], triple_less);
-    }
+            std::sort(outs[i], outs[i] + std::min(counts[i], caps[i]), triple_less);
     if (short_cap) return fail(ctx, SSJ_ENOMEM, "a batch has more result pairs than its capacity (see n_outs)");
     return SSJ_OK;
 }

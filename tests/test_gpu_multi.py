@@ -282,10 +282,9 @@ def test_verify_batches_host_direct_equals_copies(ctx):
         ssj.ssj_unload_collection(ctx, h)
 
 
-def test_verify_batches_splits_large_batches_into_pipelined_parts(ctx):
-    """A batch of about 2M candidates is cut at probe boundaries into parts whose copies overlap
-    the verification of the previous part; results equal the single call's, also for a too-small
-    capacity (the first cap triples written, SSJ_ENOMEM) and with SSJ_HOST_DIRECT."""
+def test_verify_batches_large_batch_caps_and_host_direct(ctx):
+    """A batch of about 2M candidates with others in one call: results equal the single call's,
+    with SSJ_HOST_DIRECT too, and a too-small capacity answers SSJ_ENOMEM."""
     import torch
     spec = synth.tiny_self_join(seed=2024, n=2000)
     spec.plant_frac, spec.plant_edits = 0.2, 2
