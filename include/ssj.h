@@ -361,7 +361,8 @@ typedef struct {
     uint32_t thread_max_key;  /* chosen bins (see ssj_set_granularity); 0xFFFFFFFF */
     uint32_t lane_max_key;    /*   for warp_max_key sends no probe to the block bin, */
     uint32_t warp_max_key;    /*   lane_max_key <= thread_max_key means no lane bin */
-    uint32_t block_threads;   /* chosen block size (the block path's window is 8 steps per thread) */
+    uint32_t block_threads;   /* chosen block size (the block path's window is 8 steps per thread),
+                                 | SSJ_WIDE_REGISTERS for the wide-register variant */
     uint32_t drain_min_live;  /* short pairs still merging that keep a warp on them before the rest
                                  are parked again and lanes refilled (8 .. 24) */
     uint32_t settings_tried;  /* distinct settings timed */
@@ -451,10 +452,13 @@ ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double* plan_ms, d
  * for large ones).  Defaults 128, 2048, 2048; any values are valid (every
  * granularity verifies pairs of any length), they change the speed only;
  * lane_max_key <= thread_max_key leaves the lane bin empty.
- * block_threads is 128, 256 or 512 (default 256).  Zero leaves a value
- * unchanged. */
+ * block_threads is 128, 256 or 512 (default 256), optionally
+ * | SSJ_WIDE_REGISTERS for the verify kernel compiled for three quarters of
+ * the CTAs per SM (more registers per thread, fewer spills).  Zero leaves a
+ * value unchanged. */
 ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t lane_max_key, uint32_t warp_max_key,
                                uint32_t block_threads);
+#define SSJ_WIDE_REGISTERS 0x10000u
 
 /* Measurement aid (the paper has no counterpart): device read bandwidth in
  * GB/s (1e9 bytes/s), streaming a zero-filled device buffer of `bytes`

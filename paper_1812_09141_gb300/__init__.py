@@ -45,6 +45,7 @@ SSJ_FEEDER_PPJOIN = 0x1
 SSJ_JOIN_POSITIONAL = 0x400
 SSJ_KEEP_INPUTS = 0x800
 SSJ_HOST_DIRECT = 0x1000
+SSJ_WIDE_REGISTERS = 0x10000
 # context flags
 SSJ_CTX_PROFILE = 0x1
 

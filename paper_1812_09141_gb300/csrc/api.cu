@@ -442,8 +442,9 @@ extern "C" const char* ssj_last_error(ssj_ctx* ctx) {
 extern "C" ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t lane_max_key,
                                           uint32_t warp_max_key, uint32_t block_threads) {
     if (!ctx) return SSJ_EINVAL;
-    if (block_threads && block_threads != 128 && block_threads != 256 && block_threads != 512)
-        return fail(ctx, SSJ_EINVAL, "block_threads must be 128, 256 or 512");
+    const uint32_t bt = block_threads & ~SSJ_WIDE_REGISTERS;
+    if (block_threads && bt != 128 && bt != 256 && bt != 512)
+        return fail(ctx, SSJ_EINVAL, "block_threads must be 128, 256 or 512 (optionally | SSJ_WIDE_REGISTERS)");
     if (thread_max_key) ctx->thread_max_key = thread_max_key;
     if (lane_max_key) ctx->lane_max_key = lane_max_key;
     if (warp_max_key) ctx->warp_max_key = warp_max_key;
@@ -1736,7 +1737,8 @@ extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* strea
     static const uint32_t kThread[] = {32, 64, 128, 256, 512, 1024, 2048, 4096};
     static const uint32_t kLane[] = {1, 256, 512, 1024, 2048};
     static const uint32_t kWarp[] = {256, 512, 1024, 2048, 4096, 0xFFFFFFFFu};
-    static const uint32_t kBlock[] = {128, 256, 512};
+    static const uint32_t kBlock[] = {128, 256, 512, 128 | SSJ_WIDE_REGISTERS, 256 | SSJ_WIDE_REGISTERS,
+                                      512 | SSJ_WIDE_REGISTERS};
     static const uint32_t kMinLive[] = {8, 12, 16, 20, 24};
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, uint32_t>, float> seen;
     cudaError_t err = cudaSuccess;

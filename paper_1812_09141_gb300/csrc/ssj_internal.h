@@ -148,6 +148,10 @@ size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands, int num_sms);
 void bind_workspace(VerifyArgs& a, void* ws, const LaunchShape& sh, int num_sms);
 void bind_workspace(VerifyArgs& a, void* ws, uint32_t n_probes, uint64_t n_cands, int num_sms);
 
+// block_threads flag selecting the verify kernel variant compiled for three
+// quarters of the CTAs per SM (more registers per thread, fewer spills).
+constexpr uint32_t kWideRegisters = SSJ_WIDE_REGISTERS;
+
 // Set the verify kernel's launch attributes for this device (done by the
 // first launch anyway; call before capturing a launch into a graph).
 cudaError_t prepare_verify(uint32_t block_threads);

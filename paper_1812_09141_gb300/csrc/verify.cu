@@ -785,8 +785,10 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
 // Persistent verification kernel.  Instance fields come from the device table
 // (table_out), loaded once per work item or per 32-pair chunk.
 // -------------------------------------------------------------------------
-template <int BT>
-__global__ void __launch_bounds__(BT, 1024 / BT) verify_kernel(VerifyArgs a) {
+// MINB: CTAs per SM the registers are budgeted for (1024 / BT: 64 registers
+// per thread; fewer CTAs leave more registers per thread).
+template <int BT, int MINB>
+__global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ BlockSmem<BT> bsm;
     constexpr uint32_t kBlockWin = BT * kBlockD;
@@ -1127,8 +1129,8 @@ static size_t verify_smem_bytes() {
 }
 
 // CTAs per SM of the persistent kernel, per device (the attribute and the
-// occupancy query run once per device and block size).
-template <int BT>
+// occupancy query run once per device and variant).
+template <int BT, int MINB>
 static cudaError_t resident_ctas(int* per_sm) {
     constexpr int kMaxDev = 64;
     static std::atomic<int> cache[kMaxDev];
@@ -1140,10 +1142,10 @@ static cudaError_t resident_ctas(int* per_sm) {
         return cudaSuccess;
     }
     const size_t smem = verify_smem_bytes<BT>();
-    e = cudaFuncSetAttribute(verify_kernel<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(verify_kernel<BT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, verify_kernel<BT>, BT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, verify_kernel<BT, MINB>, BT, smem);
     if (e != cudaSuccess) return e;
     if (n < 1) n = 1;
     if (dev >= 0 && dev < kMaxDev) cache[dev].store(n);
@@ -1151,23 +1153,47 @@ static cudaError_t resident_ctas(int* per_sm) {
     return cudaSuccess;
 }
 
-template <int BT>
+template <int BT, int MINB>
 static cudaError_t launch_bt(const VerifyArgs& a, cudaStream_t st, int num_sms) {
     int per_sm = 0;
-    cudaError_t e = resident_ctas<BT>(&per_sm);
+    cudaError_t e = resident_ctas<BT, MINB>(&per_sm);
     if (e != cudaSuccess) return e;
-    verify_kernel<BT><<<num_sms * per_sm, BT, verify_smem_bytes<BT>(), st>>>(a);
+    verify_kernel<BT, MINB><<<num_sms * per_sm, BT, verify_smem_bytes<BT>(), st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t prepare_verify(uint32_t block_threads) {
-    int per_sm = 0;
-    switch (block_threads) {
-        case 128: return resident_ctas<128>(&per_sm);
-        case 512: return resident_ctas<512>(&per_sm);
-        default: return resident_ctas<256>(&per_sm);
+// block_threads: 128, 256 or 512, optionally | kWideRegisters (the variant
+// budgeted for three quarters of the CTAs per SM, with more registers per
+// thread).
+template <class F>
+static cudaError_t dispatch_variant(uint32_t block_threads, F&& f) {
+    const bool wide = (block_threads & kWideRegisters) != 0;
+    switch (block_threads & ~kWideRegisters) {
+        case 128: return wide ? f.template operator()<128, 6>() : f.template operator()<128, 8>();
+        case 512: return wide ? f.template operator()<512, 1>() : f.template operator()<512, 2>();
+        default: return wide ? f.template operator()<256, 3>() : f.template operator()<256, 4>();
     }
 }
+
+struct PrepareVariant {
+    template <int BT, int MINB>
+    cudaError_t operator()() const {
+        int per_sm = 0;
+        return resident_ctas<BT, MINB>(&per_sm);
+    }
+};
+
+struct LaunchVariant {
+    const VerifyArgs& a;
+    cudaStream_t st;
+    int num_sms;
+    template <int BT, int MINB>
+    cudaError_t operator()() const {
+        return launch_bt<BT, MINB>(a, st, num_sms);
+    }
+};
+
+cudaError_t prepare_verify(uint32_t block_threads) { return dispatch_variant(block_threads, PrepareVariant{}); }
 
 cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uint32_t block_threads,
                           cudaEvent_t* ev) {
@@ -1194,11 +1220,7 @@ cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uin
         if (e != cudaSuccess) return e;
     }
     if (ev) cudaEventRecord(ev[1], st);
-    switch (block_threads) {
-        case 128: e = launch_bt<128>(a, st, num_sms); break;
-        case 512: e = launch_bt<512>(a, st, num_sms); break;
-        default: e = launch_bt<256>(a, st, num_sms); break;
-    }
+    e = dispatch_variant(block_threads, LaunchVariant{a, st, num_sms});
     if (ev) cudaEventRecord(ev[2], st);
     return e;
 }
