@@ -406,11 +406,14 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     if args.granularity:
         # a fixed setting (profiling runs: no tuning launches before the timed ones)
-        t, l, w, b = (int(x) for x in args.granularity.split(","))
+        g = [int(x) for x in args.granularity.split(",")]
+        t, l, w, b = g[:4]
+        d = g[4] if len(g) > 4 else 0
         ssj.ssj_set_granularity(ctx, t, l, w, b)
+        ssj.ssj_set_short_pairs(ctx, d)
         multi = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
         tune = {"thread_max_key": t, "lane_max_key": l, "warp_max_key": w, "block_threads": b,
-                "chosen_by": "--granularity"}
+                "drain_min_live": d, "chosen_by": "--granularity"}
     else:
         multi = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
         # granularity and block size chosen by the library's autotuner on this launch (untimed)
@@ -418,6 +421,7 @@ def run_ours(args, rank, world, local_rank):
         tune["chosen_by"] = "ssj_multi_autotune (median of 5 launches per setting)"
         ssj.ssj_set_granularity(ctx, tune["thread_max_key"], tune["lane_max_key"],
                                 min(tune["warp_max_key"], 1 << 30), tune["block_threads"])
+        ssj.ssj_set_short_pairs(ctx, tune["drain_min_live"])
 
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -730,7 +734,7 @@ def main():
     ap.add_argument("--sim", default="jaccard", choices=sorted(SIM_NAMES),
                     help="similarity function of every instance (overlap uses thresholds 6, 8, 10, 12)")
     ap.add_argument("--ppjoin", action="store_true", help="PPJoin positional filter in the CPU feeder")
-    ap.add_argument("--granularity", default="", help="thread,lane,warp,block_threads: fixed setting instead of "
+    ap.add_argument("--granularity", default="", help="thread,lane,warp,block_threads[,drain_min_live]: fixed setting instead of "
                     "the autotuner's (profiling runs)")
     args = ap.parse_args()
     global SIM

@@ -460,6 +460,15 @@ ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t l
                                uint32_t block_threads);
 #define SSJ_WIDE_REGISTERS 0x10000u
 
+/* Short-pair refill threshold of later launches of the context (prepared
+ * launches take it at ssj_multi_create; ssj_multi_autotune tunes it per
+ * launch).  Pairs verified one per thread are merged three block steps each,
+ * then the undecided ones are parked in shared memory and merged by full
+ * warps that park them again once fewer than drain_min_live (1 .. 24) lanes
+ * are still merging, refilling the lanes from later pairs.  0 restores the
+ * default (16).  Every value computes the same results.  Errors: SSJ_EINVAL. */
+ssj_status ssj_set_short_pairs(ssj_ctx* ctx, uint32_t drain_min_live);
+
 /* Measurement aid (the paper has no counterpart): device read bandwidth in
  * GB/s (1e9 bytes/s), streaming a zero-filled device buffer of `bytes`
  * (rounded down to a multiple of 16; allocated and freed here) `passes` times

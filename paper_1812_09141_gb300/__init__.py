@@ -135,6 +135,7 @@ SIGNATURES = {
     "ssj_poll": (_INT, [_VP, _U64, _INT, _P(_INT)]),
     "ssj_results": (_INT, [_VP, _U64, _VP, _U64, _P(_U64)]),
     "ssj_set_granularity": (_INT, [_VP, _U32, _U32, _U32, _U32]),
+    "ssj_set_short_pairs": (_INT, [_VP, _U32]),
     "ssj_profile_read": (_INT, [_VP, _P(_U32), _P(ctypes.c_double), _P(ctypes.c_double)]),
     "ssj_serve_replay": (_INT, [_VP, _P(ssj_request), _U32, _P(ctypes.c_double), _P(ssj_serve_stats)]),
     "ssj_serve_coprocess": (_INT, [_VP, _U32, _VP, _VP, _U32, _U32, _U32, _U32, _U64, _P(ssj_coprocess_stats)]),
@@ -447,6 +448,11 @@ def ssj_results(ctx: int, ticket: int, count_only: bool = False):
 def ssj_set_granularity(ctx: int, thread_max_key: int = 0, lane_max_key: int = 0, warp_max_key: int = 0,
                         block_threads: int = 0) -> None:
     _check(ctx, lib().ssj_set_granularity(ctx, thread_max_key, lane_max_key, warp_max_key, block_threads))
+
+
+def ssj_set_short_pairs(ctx: int, drain_min_live: int = 0) -> None:
+    """Short-pair refill threshold of later launches: 1..24, or 0 (the default, 16)."""
+    _check(ctx, lib().ssj_set_short_pairs(ctx, drain_min_live))
 
 
 def ssj_profile_read(ctx: int) -> tuple[int, float, float]:

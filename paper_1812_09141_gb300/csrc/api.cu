@@ -111,6 +111,7 @@ struct ssj_ctx {
     uint64_t budget = 0;
     uint32_t max_inflight = 0;
     uint32_t thread_max_key = 128;
+    uint32_t drain_min_live = 0;  // short-pair policy (0: default)
     uint32_t lane_max_key = 2048;
     uint32_t warp_max_key = 2048;
     uint32_t block_threads = 256;
@@ -316,6 +317,7 @@ VerifyArgs make_args(ssj_ctx* ctx, const ssj_batch* b, const Collection& R, cons
     a.single = make_instance(b, R, S, n_cands);
     a.table = nullptr;
     a.thread_max_key = ctx->thread_max_key;
+    a.drain_min_live = ctx->drain_min_live;
     a.lane_max_key = ctx->lane_max_key;
     a.warp_max_key = ctx->warp_max_key;
     return a;
@@ -449,6 +451,13 @@ extern "C" ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key,
     if (lane_max_key) ctx->lane_max_key = lane_max_key;
     if (warp_max_key) ctx->warp_max_key = warp_max_key;
     if (block_threads) ctx->block_threads = block_threads;
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_set_short_pairs(ssj_ctx* ctx, uint32_t drain_min_live) {
+    if (!ctx) return SSJ_EINVAL;
+    if (drain_min_live > 24) return fail(ctx, SSJ_EINVAL, "drain_min_live must be 0 .. 24");
+    ctx->drain_min_live = drain_min_live;
     return SSJ_OK;
 }
 
@@ -804,6 +813,7 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
     VerifyArgs a;
     memset(&a, 0, sizeof(a));
     a.thread_max_key = ctx->thread_max_key;
+    a.drain_min_live = ctx->drain_min_live;
     a.lane_max_key = ctx->lane_max_key;
     a.warp_max_key = ctx->warp_max_key;
     bind_workspace(a, ctx->ws, sh, ctx->num_sms);
@@ -1606,6 +1616,7 @@ extern "C" ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, u
     if (e != cudaSuccess) return fail(ctx, SSJ_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     memset(&m->a, 0, sizeof(m->a));
     m->a.thread_max_key = ctx->thread_max_key;
+    m->a.drain_min_live = ctx->drain_min_live;
     m->a.lane_max_key = ctx->lane_max_key;
     m->a.warp_max_key = ctx->warp_max_key;
     m->block_threads = ctx->block_threads;

@@ -3,8 +3,8 @@
 // delimits the sets, transferred once).
 //
 // GB300 layout: every set starts on a 16-byte boundary so that verification
-// reads sets with aligned 128-bit loads; the gap after a set is filled with
-// 0xFFFFFFFF; desc[i] = (first 16-byte chunk of set i, |set i|).
+// reads sets with aligned 128-bit loads; the gap after a set repeats its
+// last token; desc[i] = (first 16-byte chunk of set i, |set i|).
 //
 // Steps, all on the device after one host-to-device copy of the raw
 // offsets and tokens:
@@ -111,7 +111,10 @@ __global__ void scatter_kernel(const uint64_t* __restrict__ offs, const uint32_t
         const uint64_t sc = start_chunk[i];
         const uint64_t padded = ((len + 3) >> 2) << 2;
         uint32_t* d = dst + (sc << 2);
-        for (uint64_t t = lane; t < padded; t += 32) d[t] = t < len ? toks[a + t] : 0xFFFFFFFFu;
+        // the padding repeats the set's last token (the verify kernel's block
+        // compare relies on it: a repeated token neither adds a match on the
+        // candidate side nor changes the block's last token)
+        for (uint64_t t = lane; t < padded; t += 32) d[t] = toks[a + (t < len ? t : len - 1)];
         if (lane == 0) desc[i] = make_uint2((uint32_t)sc, (uint32_t)len);
     }
 }

@@ -63,7 +63,7 @@ constexpr int kPlanThreads = 256;                  // plan kernel block size
 
 // A parked pair with its merge state.
 struct ContEntry {
-    uint4 m0;  // r id, s id, current 16-byte block of r, of s (indices into the token arrays)
+    uint4 m0;  // probe slot (its r id is rid[slot]), s id, current 16-byte block of r, of s (token array indices)
     uint4 m1;  // tokens of r and of s from the current blocks on, required overlap, overlap so far
     uint4 m2;  // instance, unused, unused, unused
 };
@@ -78,10 +78,6 @@ constexpr uint32_t kWarpPhase2Bytes = (kWarpABuf + kWarpBBuf) * 4;
 constexpr uint32_t kWarpSliceBytes =
     ((kWarpPhase2Bytes > kTableBytes ? kWarpPhase2Bytes : kTableBytes) + 15u) & ~15u;
 
-__device__ __forceinline__ uint32_t sel4(const uint4& v, uint32_t k) {
-    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
-}
-
 // 1 if x equals one of the four tokens of s (distinct within a block).
 __device__ __forceinline__ uint32_t match4(uint32_t x, const uint4& s) {
     return (x == s.x) | (x == s.y) | (x == s.z) | (x == s.w);
@@ -93,14 +89,23 @@ struct BlockState {
     bool fin, rej;
 };
 
+// Matches between the valid tokens of an r block and an s block whose
+// padding repeats the set's last token (the collection layout): a repeated
+// s token changes no membership test, and the r lanes past nvr valid ones
+// all repeat the last valid token, whose match is subtracted again.
+__device__ __forceinline__ uint32_t block_matches(const uint4& rc, const uint4& sc, uint32_t nvr) {
+    const uint32_t mw = match4(rc.w, sc);
+    return match4(rc.x, sc) + match4(rc.y, sc) + match4(rc.z, sc) + mw - (4u - nvr) * mw;
+}
+
 // One block step: count the matches between block qi of r (rc) and block qj
 // of s (sc), then advance the block whose last valid token is smaller (both
 // on a tie).  Every matching pair of tokens sits in a pair of blocks that is
 // current together exactly once, so the count is exact.  Before the step the
 // positional bound o + min(|r| - 4qi, |s| - 4qj) < req rejects the pair; the
 // bound counts whole current blocks, so it only over-estimates the reachable
-// overlap and never rejects a passing pair.  Tokens past a set's end (the
-// padding of its last block) are masked by position.
+// overlap and never rejects a passing pair.  A block's last lane holds its
+// last valid token (the padding repeats it).
 __device__ __forceinline__ void block_step(const uint4& rc, const uint4& sc, uint32_t nr, uint32_t ns, uint32_t req,
                                            bool early, BlockState& st, bool& adv_r, bool& adv_s) {
     adv_r = adv_s = false;
@@ -111,23 +116,9 @@ __device__ __forceinline__ void block_step(const uint4& rc, const uint4& sc, uin
         st.fin = true;
         return;
     }
-    const uint32_t nvr = min(remr, 4u), nvs = min(rems, 4u);
-    const uint32_t ra[4] = {rc.x, rc.y, rc.z, rc.w};
-    const uint32_t sb[4] = {sc.x, sc.y, sc.z, sc.w};
-    uint32_t c = 0;
-    if (nvr == 4 && nvs == 4) {
-        c = match4(rc.x, sc) + match4(rc.y, sc) + match4(rc.z, sc) + match4(rc.w, sc);
-    } else {
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) c += ((uint32_t)x < nvr && (uint32_t)y < nvs && ra[x] == sb[y]) ? 1u : 0u;
-    }
-    st.o += c;
-    const uint32_t rmax = nvr == 4 ? rc.w : sel4(rc, nvr - 1);
-    const uint32_t smax = nvs == 4 ? sc.w : sel4(sc, nvs - 1);
-    adv_r = rmax <= smax;
-    adv_s = smax <= rmax;
+    st.o += block_matches(rc, sc, min(remr, 4u));
+    adv_r = rc.w <= sc.w;
+    adv_s = sc.w <= rc.w;
     st.qi += adv_r ? 1u : 0u;
     st.qj += adv_s ? 1u : 0u;
     st.fin = (4 * st.qi >= nr || 4 * st.qj >= ns);
@@ -306,38 +297,20 @@ __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const
 
 // Block step of pass 2 on a (block cursor, tokens remaining) state; the same
 // step as block_step: positional bound, 16 compares between the current
-// blocks (masked by position at a set's end), then the block with the
-// smaller last valid token advances (both on a tie).  rn / sn hold the next
-// block of each side, loaded one step ahead.
+// blocks, then the block with the smaller last valid token advances (both on
+// a tie).  rn / sn hold the next block of each side, loaded one step ahead.
 __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4& sn, const uint4* rb,
                                           const uint4* sb, uint32_t& rcur, uint32_t& scur, uint32_t& remr,
                                           uint32_t& rems, uint32_t& o, uint32_t req, bool early, bool& fin,
                                           bool& rej) {
-    const uint32_t m = min(remr, rems);
-    if (early && o + m < req) {
+    if (early && o + min(remr, rems) < req) {
         rej = true;
         fin = true;
         return;
     }
-    uint32_t rmax, smax;
-    if (m >= 4) {
-        o += match4(rc.x, sc) + match4(rc.y, sc) + match4(rc.z, sc) + match4(rc.w, sc);
-        rmax = rc.w;
-        smax = sc.w;
-    } else {
-        const uint32_t nvr = min(remr, 4u), nvs = min(rems, 4u);
-        const uint32_t ra[4] = {rc.x, rc.y, rc.z, rc.w};
-        const uint32_t sv[4] = {sc.x, sc.y, sc.z, sc.w};
-        uint32_t c = 0;
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) c += ((uint32_t)x < nvr && (uint32_t)y < nvs && ra[x] == sv[y]) ? 1u : 0u;
-        o += c;
-        rmax = sel4(rc, nvr - 1);
-        smax = sel4(sc, nvs - 1);
-    }
-    const bool ar = rmax <= smax, as = smax <= rmax;
+    if (remr >= 4) o += match4(rc.x, sc) + match4(rc.y, sc) + match4(rc.z, sc) + match4(rc.w, sc);
+    else o += block_matches(rc, sc, remr);  // r's last block
+    const bool ar = rc.w <= sc.w, as = sc.w <= rc.w;
     if (ar) {
         rc = rn;
         ++rcur;
@@ -358,14 +331,16 @@ __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4
 // while at least min_live lanes are still undecided; decided pairs are
 // emitted, undecided ones parked again, compacted, so that lanes are refilled
 // from later pairs instead of idling behind the longest merge of the warp.
-// min_live = 1 finishes every pair.  Returns the new number of parked pairs.
+// min_live = 1 finishes every pair.  A parked pair carries its probe slot;
+// the r id is read from it only for a survivor.  Returns the new number of
+// parked pairs.
 __device__ __noinline__ uint32_t drain_parked(ContEntry* cont, uint32_t n_cont, uint32_t m, uint32_t min_live,
-                                              const Instance* table, int lane) {
+                                              const Instance* table, const uint32_t* rid_of_slot, int lane) {
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint4 zero4 = make_uint4(0, 0, 0, 0);
     const uint32_t base = n_cont - m;
     const bool have = (uint32_t)lane < m;
-    uint32_t rid = 0, sid = 0, rcur = 0, scur = 0, remr = 0, rems = 0, req = 0, o = 0, inst = 0;
+    uint32_t slot = 0, sid = 0, rcur = 0, scur = 0, remr = 0, rems = 0, req = 0, o = 0, inst = 0;
     const uint4* rb = nullptr;
     const uint4* sb = nullptr;
     bool early = true, fin = true, rej = false;
@@ -373,7 +348,7 @@ __device__ __noinline__ uint32_t drain_parked(ContEntry* cont, uint32_t n_cont, 
     if (have) {
         const ContEntry* ce = cont + base + lane;
         const uint4 m0 = ce->m0, m1 = ce->m1, m2 = ce->m2;
-        rid = m0.x;
+        slot = m0.x;
         sid = m0.y;
         rcur = m0.z;
         scur = m0.w;
@@ -399,13 +374,14 @@ __device__ __noinline__ uint32_t drain_parked(ContEntry* cont, uint32_t n_cont, 
     if (have && fin && (!early || (!rej && o >= req))) {
         const Instance& I = table[inst];
         const unsigned long long idx = atomicAdd(I.count, 1ull);
-        if (!(I.flags & VF_COUNT_ONLY)) emit_triple(I.out, I.cap, (I.flags & VF_SELF_JOIN) != 0, idx, rid, sid, o);
+        if (!(I.flags & VF_COUNT_ONLY))
+            emit_triple(I.out, I.cap, (I.flags & VF_SELF_JOIN) != 0, idx, rid_of_slot[slot], sid, o);
     }
     const bool again = have && !fin;
     const uint32_t amask = __ballot_sync(kFull, again);
     if (again) {
         ContEntry* ce = cont + base + __popc(amask & lt_mask);
-        ce->m0 = make_uint4(rid, sid, rcur, scur);
+        ce->m0 = make_uint4(slot, sid, rcur, scur);
         ce->m1 = make_uint4(remr, rems, req, o);
         ce->m2 = make_uint4(inst, 0u, 0u, 0u);
     }
@@ -715,42 +691,44 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
         {
             const unsigned long long cta_base = s_base[par][0], cta_total = s_pre[par][kPlanWarps];
             if (cta_base + cta_total <= a.pair_cap) {
-                for (unsigned long long f0 = 0; f0 < cta_total; f0 += 4 * kPlanThreads) {
-                    uint32_t v[4], kk[4];
-                    unsigned long long fa[4];
+                // each thread writes 4 consecutive slots (cta_total is a multiple of
+                // 32, so all 4 exist): it locates the first by binary search and
+                // follows the tile and probe boundaries for the other three
+                for (unsigned long long f0 = 4ull * threadIdx.x; f0 < cta_total; f0 += 4ull * kPlanThreads) {
+                    int w = 0;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const unsigned long long f = f0 + u * kPlanThreads + threadIdx.x;
-                        fa[u] = f;
-                        v[u] = 0u;
-                        kk[u] = kNoProbe;
-                        if (f < cta_total) {
-                            int w = 0;
+                    for (int step = kPlanWarps / 2; step >= 1; step >>= 1)
+                        if (s_pre[par][w + step] <= f0) w += step;
+                    uint32_t pos = 0, out[8];
+                    bool located = false;
 #pragma unroll
-                            for (int step = kPlanWarps / 2; step >= 1; step >>= 1)
-                                if (s_pre[par][w + step] <= f) w += step;
-                            const unsigned long long fl = f - s_pre[par][w];
-                            const unsigned long long tt = s_incl[par][w][31];
-                            if (fl < tt) {
-                                uint32_t pos = 0;
+                    for (int e = 0; e < 4; ++e) {
+                        const unsigned long long f = f0 + e;
+                        while (f >= s_pre[par][w + 1]) {  // into the next tile with slots
+                            ++w;
+                            located = false;
+                        }
+                        const unsigned long long fl = f - s_pre[par][w];
+                        out[2 * e] = kNoProbe;
+                        out[2 * e + 1] = 0u;
+                        if (fl < s_incl[par][w][31]) {
+                            if (!located) {
+                                pos = 0;
 #pragma unroll
                                 for (int step = 16; step >= 1; step >>= 1)
                                     if (s_incl[par][w][pos + step - 1] <= fl) pos += step;
-                                const unsigned long long ex = pos ? s_incl[par][w][pos - 1] : 0ull;
-                                kk[u] = s_slot[par][w][pos];
-                                v[u] = s_cand[par][w][s_c0[par][w][pos] + (fl - ex)];
+                                located = true;
+                            } else {
+                                while (s_incl[par][w][pos] <= fl) ++pos;  // past probes that end before fl
                             }
+                            const unsigned long long ex = pos ? s_incl[par][w][pos - 1] : 0ull;
+                            out[2 * e] = s_slot[par][w][pos];
+                            out[2 * e + 1] = s_cand[par][w][s_c0[par][w][pos] + (fl - ex)];
                         }
                     }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (fa[u] < cta_total) {
-                            PairRef pr;
-                            pr.k = kk[u];
-                            pr.s = v[u];
-                            a.pairs[cta_base + fa[u]] = pr;
-                        }
-                    }
+                    uint4* dst = reinterpret_cast<uint4*>(a.pairs + cta_base + f0);
+                    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
+                    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
                 }
             }
         }
@@ -933,7 +911,7 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
         // Pass 2 (drain_parked): the last m parked pairs, one per lane, merged
         // while at least min_live lanes still work; the rest are parked again.
         auto drain = [&](uint32_t m, uint32_t live) {
-            n_cont = drain_parked(cont, n_cont, m, live, table, lane);
+            n_cont = drain_parked(cont, n_cont, m, live, table, a.rid, lane);
         };
         const uint32_t min_live = a.drain_min_live ? min(max(a.drain_min_live, 1u), 24u) : kDrainMinLive;
 
@@ -960,7 +938,7 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 const uint4* s_toks4 = I.s_toks4;
                 // ---- pass 1
                 bool live = false;
-                uint32_t pr_id = 0, ps_id = 0, nr = 0, ns = 0, req = 0;
+                uint32_t pr_k = 0, ps_id = 0, nr = 0, ns = 0, req = 0;
                 uint2 dr = make_uint2(0, 0), ds = make_uint2(0, 0);
                 {
                     const PairRef pr = a.pairs[first + lane];
@@ -969,12 +947,15 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                         if (ps_id >= s_n_sets) {
                             atomicOr(&a.ctr->err, ERR_CAND_ID);
                         } else {
-                            dr = a.rdesc[pr.k];
-                            pr_id = a.rid[pr.k];
+                            pr_k = pr.k;
+                            dr = a.rdesc[pr_k];
                             ds = I.s_desc[ps_id];
                             nr = dr.y;
                             ns = ds.y;
-                            if (!(self_join && pr_id == ps_id)) {
+                            // (r, r) of a self-join: non-empty sets have disjoint blocks, so
+                            // equal descriptors name the same set; empty ones need the id
+                            const bool same = self_join && dr.x == ds.x && nr == ns && (nr > 0 || a.rid[pr_k] == ps_id);
+                            if (!same) {
                                 req = required_overlap(sim, p, den, magic, nr, ns);
                                 live = emit_all || (nr + ns > 0 && req <= min(nr, ns));  // length filter
                             }
@@ -1011,7 +992,9 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                     if (lane == 0) b0 = atomicAdd(I.count, (unsigned long long)__popc(pmask));
                     if (!(flags & VF_COUNT_ONLY)) {
                         b0 = __shfl_sync(kFull, b0, 0);
-                        if (pass) emit_triple(I.out, I.cap, self_join, b0 + __popc(pmask & lt_mask), pr_id, ps_id, st.o);
+                        if (pass)
+                            emit_triple(I.out, I.cap, self_join, b0 + __popc(pmask & lt_mask), a.rid[pr_k], ps_id,
+                                        st.o);
                     }
                 }
                 // undecided pairs: park them with their merge state
@@ -1021,7 +1004,7 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                     while (n_cont + 32 > kCont) drain(32, min_live);  // room for a full warp of parked pairs
                     if (park) {
                         ContEntry* ce = cont + n_cont + __popc(kmask & lt_mask);
-                        ce->m0 = make_uint4(pr_id, ps_id, dr.x + st.qi, ds.x + st.qj);
+                        ce->m0 = make_uint4(pr_k, ps_id, dr.x + st.qi, ds.x + st.qj);
                         ce->m1 = make_uint4(nr - 4 * st.qi, ns - 4 * st.qj, req, st.o);
                         ce->m2 = make_uint4(inst, 0u, 0u, 0u);
                     }
@@ -1210,9 +1193,16 @@ cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uin
     // the plan kernel also runs for empty batches: it clears the instances' counts
     {
         // one round of tiles per CTA and round (kPlanThreads / 32 tiles), one wave of CTAs
+        static int plan_ctas_per_sm = 0;  // resident CTAs per SM (same value from every thread)
+        if (plan_ctas_per_sm == 0) {
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, plan_kernel, kPlanThreads, 0) != cudaSuccess || n < 1)
+                n = 4;
+            plan_ctas_per_sm = n;
+        }
         const int threads = kPlanThreads;
         uint64_t blocks = ((uint64_t)a.n_tiles * 32 + threads - 1) / threads;
-        const uint64_t max_blocks = (uint64_t)num_sms * 6;
+        const uint64_t max_blocks = (uint64_t)num_sms * (uint64_t)plan_ctas_per_sm;
         if (blocks > max_blocks) blocks = max_blocks;
         if (blocks < 1) blocks = 1;
         plan_kernel<<<(unsigned)blocks, threads, 0, st>>>(a);

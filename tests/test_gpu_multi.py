@@ -86,7 +86,10 @@ def _alone(ctx, R, S, p, q, b, fl):
                                                      flags=fl))
 
 
-def test_multi_mixed_instances_equal_their_single_launches(ctx):
+@pytest.mark.parametrize("policy", [0, 1, 24])
+def test_multi_mixed_instances_equal_their_single_launches(ctx, policy):
+    """Ten instances of different collections, thresholds and flags in one launch (their chunks
+    mix in the short-pair phase) equal their single launches, at several short-pair refill thresholds."""
     spec = synth.tiny_self_join(n=600)
     spec.plant_frac, spec.plant_edits = 0.2, 2
     c_tiny = synth.collection(spec)
@@ -112,12 +115,16 @@ def test_multi_mixed_instances_equal_their_single_launches(ctx):
         (h_short, h_short, 7, 10, fb(c_short, 7, 10), ssj.SSJ_EMIT_ALL),
     ]
     want = [_alone(ctx, *cs) for cs in cases]
-    for res in _run_multi(ctx, cases, graph_reps=2):
-        for i, (got, w) in enumerate(zip(res, want)):
-            if isinstance(w, int):
-                assert got == w, i
-            else:
-                assert np.array_equal(got, w), (i, len(got), len(w))
+    ssj.ssj_set_short_pairs(ctx, policy)
+    try:
+        for res in _run_multi(ctx, cases, graph_reps=2):
+            for i, (got, w) in enumerate(zip(res, want)):
+                if isinstance(w, int):
+                    assert got == w, i
+                else:
+                    assert np.array_equal(got, w), (i, len(got), len(w))
+    finally:
+        ssj.ssj_set_short_pairs(ctx, 0)
     for h in (h_tiny, h_short, h_long, hR):
         ssj.ssj_unload_collection(ctx, h)
 

@@ -125,6 +125,41 @@ def test_planted_long_sets_many_survivors(ctx):
     ssj.ssj_unload_collection(ctx, h)
 
 
+POLICIES = [1, 8, 24]
+
+
+@pytest.mark.parametrize("bt", [256, 128 | ssj.SSJ_WIDE_REGISTERS, 512 | ssj.SSJ_WIDE_REGISTERS])
+@pytest.mark.parametrize("policy", POLICIES)
+def test_short_pair_policies(ctx, policy, bt):
+    """Every short-pair refill threshold gives the oracle's join: tiny
+    all pairs (also every overlap), scaled short and long sets, thread bin for all probes."""
+    ssj.ssj_set_granularity(ctx, 1 << 30, 1, 1 << 30, bt)
+    ssj.ssj_set_short_pairs(ctx, policy)
+    try:
+        c = planted_tiny(n=900)
+        h = load(ctx, c)
+        b = synth.all_pairs_batch(c.n)
+        for p, q in [(4, 5), (3, 5)]:
+            assert np.array_equal(gpu(ctx, h, h, p, q, b), ora(c, c, True, p, q, b)), (p, q)
+        every = ora(c, c, True, 3, 5, b, flags=oracle.EMIT_ALL)
+        assert np.array_equal(gpu(ctx, h, h, 3, 5, b, ssj.SSJ_EMIT_ALL), every)
+        ssj.ssj_unload_collection(ctx, h)
+        for spec, ths in ((synth.short_sets(n=20_000), [(9, 10), (7, 10), (3, 5)]),
+                          (synth.long_sets(n=1200), [(3, 5), (4, 5)])):
+            spec.plant_frac, spec.plant_edits = 0.2, 3
+            c = synth.collection(spec)
+            h = load(ctx, c, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
+            for p, q in ths:
+                b = feeder_batch(c, p, q)
+                want = oracle.sort_triples(oracle.allpairs_self(c.offsets, c.tokens, p, q)[0])
+                assert len(want) > 0
+                assert np.array_equal(gpu(ctx, h, h, p, q, b), want), (p, q, len(want))
+            ssj.ssj_unload_collection(ctx, h)
+    finally:
+        ssj.ssj_set_granularity(ctx, 128, 2048, 2048, 256)
+        ssj.ssj_set_short_pairs(ctx, 0)
+
+
 # ----------------------------------------------------------------- arbitrary batches
 
 @pytest.mark.parametrize("seed", range(3))
