@@ -310,19 +310,22 @@ __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4
     }
     if (remr >= 4) o += match4(rc.x, sc) + match4(rc.y, sc) + match4(rc.z, sc) + match4(rc.w, sc);
     else o += block_matches(rc, sc, remr);  // r's last block
+    // the advance as selects rather than branches (lanes of a warp differ in it)
     const bool ar = rc.w <= sc.w, as = sc.w <= rc.w;
-    if (ar) {
-        rc = rn;
-        ++rcur;
-        remr = remr > 4 ? remr - 4 : 0;
-        if (remr > 4) rn = __ldg(rb + rcur + 1);
-    }
-    if (as) {
-        sc = sn;
-        ++scur;
-        rems = rems > 4 ? rems - 4 : 0;
-        if (rems > 4) sn = __ldg(sb + scur + 1);
-    }
+    rc.x = ar ? rn.x : rc.x;
+    rc.y = ar ? rn.y : rc.y;
+    rc.z = ar ? rn.z : rc.z;
+    rc.w = ar ? rn.w : rc.w;
+    sc.x = as ? sn.x : sc.x;
+    sc.y = as ? sn.y : sc.y;
+    sc.z = as ? sn.z : sc.z;
+    sc.w = as ? sn.w : sc.w;
+    rcur += ar ? 1u : 0u;
+    scur += as ? 1u : 0u;
+    remr = ar ? (remr > 4 ? remr - 4 : 0u) : remr;
+    rems = as ? (rems > 4 ? rems - 4 : 0u) : rems;
+    if (ar && remr > 4) rn = __ldg(rb + rcur + 1);
+    if (as && rems > 4) sn = __ldg(sb + scur + 1);
     fin = remr == 0 || rems == 0;
 }
 
@@ -368,7 +371,8 @@ __device__ __noinline__ uint32_t drain_parked(ContEntry* cont, uint32_t n_cont, 
         if (rems > 4) sn = __ldg(sb + scur + 1);
     }
     __syncwarp();  // every entry is read before any is written again
-    while ((uint32_t)__popc(__ballot_sync(kFull, !fin)) >= min_live) {
+    while ((uint32_t)__popc(__ballot_sync(kFull, !fin)) >= min_live) {  // two steps per check
+        if (!fin) lean_step(rc, rn, sc, sn, rb, sb, rcur, scur, remr, rems, o, req, early, fin, rej);
         if (!fin) lean_step(rc, rn, sc, sn, rb, sb, rcur, scur, remr, rems, o, req, early, fin, rej);
     }
     if (have && fin && (!early || (!rej && o >= req))) {
