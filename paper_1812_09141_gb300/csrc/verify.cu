@@ -108,20 +108,17 @@ __device__ __forceinline__ uint32_t block_matches(const uint4& rc, const uint4& 
 // last valid token (the padding repeats it).
 __device__ __forceinline__ void block_step(const uint4& rc, const uint4& sc, uint32_t nr, uint32_t ns, uint32_t req,
                                            bool early, BlockState& st, bool& adv_r, bool& adv_s) {
-    adv_r = adv_s = false;
-    if (st.fin) return;
     const uint32_t remr = nr - 4 * st.qi, rems = ns - 4 * st.qj;
-    if (early && st.o + min(remr, rems) < req) {
-        st.rej = true;
-        st.fin = true;
-        return;
-    }
-    st.o += block_matches(rc, sc, min(remr, 4u));
-    adv_r = rc.w <= sc.w;
-    adv_s = sc.w <= rc.w;
+    const bool bad = !st.fin && early && st.o + min(remr, rems) < req;
+    const bool go = !st.fin && !bad;
+    st.rej = st.rej || bad;
+    const uint32_t c = block_matches(rc, sc, min(remr, 4u));
+    st.o += go ? c : 0u;
+    adv_r = go && rc.w <= sc.w;
+    adv_s = go && sc.w <= rc.w;
     st.qi += adv_r ? 1u : 0u;
     st.qj += adv_s ? 1u : 0u;
-    st.fin = (4 * st.qi >= nr || 4 * st.qj >= ns);
+    st.fin = st.fin || bad || 4 * st.qi >= nr || 4 * st.qj >= ns;
 }
 
 // Equivalent overlap of the instance's similarity function with t = p/q
@@ -303,15 +300,13 @@ __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4
                                           const uint4* sb, uint32_t& rcur, uint32_t& scur, uint32_t& remr,
                                           uint32_t& rems, uint32_t& o, uint32_t req, bool early, bool& fin,
                                           bool& rej) {
-    if (early && o + min(remr, rems) < req) {
-        rej = true;
-        fin = true;
-        return;
-    }
-    if (remr >= 4) o += match4(rc.x, sc) + match4(rc.y, sc) + match4(rc.z, sc) + match4(rc.w, sc);
-    else o += block_matches(rc, sc, remr);  // r's last block
+    const bool bad = !fin && early && o + min(remr, rems) < req;
+    const bool go = !fin && !bad;
+    rej = rej || bad;
+    const uint32_t c = block_matches(rc, sc, min(remr, 4u));
+    o += go ? c : 0u;
     // the advance as selects rather than branches (lanes of a warp differ in it)
-    const bool ar = rc.w <= sc.w, as = sc.w <= rc.w;
+    const bool ar = go && rc.w <= sc.w, as = go && sc.w <= rc.w;
     rc.x = ar ? rn.x : rc.x;
     rc.y = ar ? rn.y : rc.y;
     rc.z = ar ? rn.z : rc.z;
@@ -326,7 +321,7 @@ __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4
     rems = as ? (rems > 4 ? rems - 4 : 0u) : rems;
     if (ar && remr > 4) rn = __ldg(rb + rcur + 1);
     if (as && rems > 4) sn = __ldg(sb + scur + 1);
-    fin = remr == 0 || rems == 0;
+    fin = fin || bad || remr == 0 || rems == 0;
 }
 
 // Pass 2 of the short-pair phase: the parked pairs [n_cont - m, n_cont) are
