@@ -109,7 +109,7 @@ const char* ssj_last_error(ssj_ctx* ctx);
  * offsets[i+1]) (host).  Each set must hold fewer than 2^31 tokens.
  * The data are copied; the caller may free them on return.
  * Device layout: tokens padded so that every set starts on a 16-byte
- * boundary (pad value 0xFFFFFFFF), plus one 8-byte (start, length)
+ * boundary (the padding repeats the set's last token), plus one 8-byte (start, length)
  * descriptor per set.  Empty sets are allowed and never match.
  * Errors: SSJ_EINVAL (NULL pointers, decreasing offsets, unsorted set with
  * SSJ_VALIDATE, unknown flag), SSJ_ENOMEM, SSJ_EDEVICE. */

@@ -105,7 +105,9 @@ __device__ __forceinline__ uint32_t block_matches(const uint4& rc, const uint4& 
 // positional bound o + min(|r| - 4qi, |s| - 4qj) < req rejects the pair; the
 // bound counts whole current blocks, so it only over-estimates the reachable
 // overlap and never rejects a passing pair.  A block's last lane holds its
-// last valid token (the padding repeats it).
+// last valid token (the padding repeats it).  The step is predicated code:
+// the lanes of a warp are at different points of different pairs, so a lane
+// whose pair is decided computes and discards instead of branching away.
 __device__ __forceinline__ void block_step(const uint4& rc, const uint4& sc, uint32_t nr, uint32_t ns, uint32_t req,
                                            bool early, BlockState& st, bool& adv_r, bool& adv_s) {
     const uint32_t remr = nr - 4 * st.qi, rems = ns - 4 * st.qj;
@@ -295,7 +297,8 @@ __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const
 // Block step of pass 2 on a (block cursor, tokens remaining) state; the same
 // step as block_step: positional bound, 16 compares between the current
 // blocks, then the block with the smaller last valid token advances (both on
-// a tie).  rn / sn hold the next block of each side, loaded one step ahead.
+// a tie), predicated like block_step.  rn / sn hold the next block of each
+// side, loaded one step ahead.
 __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4& sn, const uint4* rb,
                                           const uint4* sb, uint32_t& rcur, uint32_t& scur, uint32_t& remr,
                                           uint32_t& rems, uint32_t& o, uint32_t req, bool early, bool& fin,
@@ -305,7 +308,6 @@ __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4
     rej = rej || bad;
     const uint32_t c = block_matches(rc, sc, min(remr, 4u));
     o += go ? c : 0u;
-    // the advance as selects rather than branches (lanes of a warp differ in it)
     const bool ar = go && rc.w <= sc.w, as = go && sc.w <= rc.w;
     rc.x = ar ? rn.x : rc.x;
     rc.y = ar ? rn.y : rc.y;
