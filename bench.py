@@ -22,7 +22,8 @@ roofline  algorithmic bytes of the verify kernel (candidate stream, set
         descriptors, the tokens the positional filter lets the merge read,
         results) over its own event-timed duration, against the measured HBM
         copy bandwidth; l2_aware_roofline adds the L2 read rate measured by
-        the library's probe.
+        the library's probe; a_pair the looser count with the probe's
+        tokens read once per pair.
 warm_l2 / plain_per_batch  the same launch without the flush, and one
         plan + verify call per instance instead of one batched launch.
 cpu_baseline / --impl reference  the CPU oracle as it stands, on host cores.
@@ -179,7 +180,11 @@ def oracle_accounting(colls, batches):
         # the part that comes from HBM even with the collection resident in L2:
         # the candidate stream and the output
         a_hbm = 12 * len(pr) + 4 * len(ci) + 12 * len(tr) + 8
-        return {"bytes": int(a), "hbm_bytes": int(a_hbm), "survivors": int(len(tr)), "pairs": int(len(ci))}
+        # the looser per-pair figure: both sides' consumed tokens for every pair
+        a_pair = (12 * len(pr) + 4 * len(ci) + 8 * (len(pr) + len(ci)) + 4 * int(cr.astype(np.int64).sum())
+                  + 4 * int(cs.astype(np.int64).sum()) + 12 * len(tr) + 8)
+        return {"bytes": int(a), "hbm_bytes": int(a_hbm), "pair_bytes": int(a_pair), "survivors": int(len(tr)),
+                "pairs": int(len(ci))}
 
     with cf.ThreadPoolExecutor(max(1, min(len(batches), os.cpu_count() or 1))) as ex:
         return list(ex.map(one, batches))
@@ -862,6 +867,11 @@ def main():
                             "kernel": "verify_kernel", "peak_source": f"{peak_kind} copy bandwidth",
                             "algorithmic_bytes_per_launch": bytes_step}
         line["gbs_vs_hbm_peak"] = {"achieved_gbs": achieved, "frac": achieved / peak}
+        pair_step = sum(a["pair_bytes"] for a in acc)
+        line["a_pair"] = {"bytes_per_launch": pair_step, "achieved_gbs": pair_step / verify_s_step / 1e9,
+                          "frac": pair_step / verify_s_step / 1e9 / peak,
+                          "note": "both sides' consumed tokens counted for every pair (the probe's tokens once "
+                                  "per pair, not once per probe)"}
         hbm_step = sum(a["hbm_bytes"] for a in acc)
         l2 = res["l2_gbs"]
         bound_s = max(hbm_step / (peak * 1e9), bytes_step / (l2 * 1e9))
