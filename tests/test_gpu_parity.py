@@ -203,6 +203,36 @@ def test_edge_sets_and_sizes(ctx):
     ssj.ssj_unload_collection(ctx, h)
 
 
+def test_set_tails_and_extreme_token_values(ctx):
+    """Every tail shape of the last 16-byte block (lengths 1..13), the last token of a set equal to
+    a token inside another set's block, and token values 0 and 2^32 - 1 (the padding repeats a
+    set's last token, so no value is reserved)."""
+    top = 0xFFFFFFFF
+    rng = np.random.default_rng(11)
+    sets = [[0], [top], [0, top], [top - 1, top], [5], [5, 6, 7, 8, 9], [1, 5, 9], [9], [4, 5, 6, 7],
+            [4, 5, 6, 7, 8], [1, 2, 3, 4, 5, 6, 7, 8, 9], [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12],
+            [3, 1 << 31, top], [1 << 31, top]]
+    for n in range(1, 14):
+        base = np.sort(rng.choice(40, size=n, replace=False)).tolist()
+        sets.append(base)
+        sets.append(sorted(set(base[:-1] + [top - n])))
+        sets.append(sorted(set(base + [base[-1] + 1])) if base[-1] + 1 < 40 else base[:-1] + [41])
+    c = synth.from_lists(sets)
+    h = load(ctx, c)
+    b = synth.all_pairs_batch(c.n)
+    try:
+        for p, q in [(1, 1), (4, 5), (1, 2), (1, 100)]:
+            want = oracle.sort_triples(oracle.bruteforce_self(c.offsets, c.tokens, p, q))
+            assert len(want) > 0
+            for gran in GRANULARITIES:
+                assert np.array_equal(gpu(ctx, h, h, p, q, b, gran), want), (p, q, gran)
+        every = ora(c, c, True, 1, 2, b, flags=oracle.EMIT_ALL)
+        for gran in GRANULARITIES:
+            assert np.array_equal(gpu(ctx, h, h, 1, 2, b, ssj.SSJ_EMIT_ALL | gran), every), gran
+    finally:
+        ssj.ssj_unload_collection(ctx, h)
+
+
 def test_empty_and_degenerate_batches(ctx):
     c = planted_tiny(n=50)
     h = load(ctx, c)
