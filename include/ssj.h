@@ -394,7 +394,10 @@ ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands);
  * only after that stream has seen the work).  *code = 0 when no check fired;
  * bit 0: probe id out of range, bit 1: candidate id out of range, bit 2:
  * offsets decreasing or past the candidate array, bit 3: an internal loop
- * bound was reached (a library bug, reported instead of hanging). */
+ * bound was reached (a library bug, reported instead of hanging), bit 4:
+ * (libssj_checked.so, the build with -DSSJ_CHECKED, only) an index of the
+ * plan or verify kernels was out of its array's bounds and the access was
+ * skipped (a library bug, reported instead of faulting). */
 ssj_status ssj_device_error(ssj_ctx* ctx, uint32_t* code);
 
 /* ------------------------------------------------------------------------

@@ -16,7 +16,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libssj.so")
+# SSJ_LIBRARY=checked loads the checked build (every kernel index tested, an
+# out-of-bounds one reported as device error bit 4 instead of faulting).
+LIB_PATH = os.path.join(_HERE, "libssj_checked.so" if os.environ.get("SSJ_LIBRARY") == "checked" else "libssj.so")
 
 # status codes
 SSJ_OK, SSJ_EINVAL, SSJ_ENOMEM, SSJ_EAGAIN, SSJ_ETIMEDOUT, SSJ_EBUSY, SSJ_ENOTFOUND, SSJ_EDEVICE = range(8)

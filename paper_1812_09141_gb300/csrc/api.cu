@@ -295,6 +295,8 @@ Instance make_instance(const ssj_batch* b, const Collection& R, const Collection
     I.s_toks4 = reinterpret_cast<const uint4*>(S.d_toks);
     I.s_desc = S.d_desc;
     I.s_n_sets = S.n_sets;
+    I.r_n_chunks = R.n_chunks;
+    I.s_n_chunks = S.n_chunks;
     I.p = b->p;
     I.sim = (b->flags & SSJ_SIM_MASK) >> 8;
     switch (I.sim) {
@@ -720,7 +722,9 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
     const uint64_t count = *ctx->h_count;
     const uint32_t derr = *ctx->h_err;
     *n_out = count;
-    if (derr & ERR_GUARD) return fail(ctx, SSJ_EDEVICE, "internal loop bound reached on the device (code %u)", derr);
+    if (derr & (ERR_GUARD | ERR_BOUNDS))
+        return fail(ctx, SSJ_EDEVICE, "internal device check fired (code %u: %s%s)", derr,
+                    (derr & ERR_GUARD) ? "loop bound reached " : "", (derr & ERR_BOUNDS) ? "index out of bounds" : "");
     if (derr)
         return fail(ctx, SSJ_EINVAL, "batch rejected by the device checks (code %u: %s%s%s)", derr,
                     (derr & ERR_PROBE_ID) ? "probe id out of range " : "",
@@ -827,7 +831,9 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_err, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const uint32_t derr = *ctx->h_err;
-    if (derr & ERR_GUARD) return fail(ctx, SSJ_EDEVICE, "internal loop bound reached on the device (code %u)", derr);
+    if (derr & (ERR_GUARD | ERR_BOUNDS))
+        return fail(ctx, SSJ_EDEVICE, "internal device check fired (code %u: %s%s)", derr,
+                    (derr & ERR_GUARD) ? "loop bound reached " : "", (derr & ERR_BOUNDS) ? "index out of bounds" : "");
     if (derr) return fail(ctx, SSJ_EINVAL, "batch rejected by the device checks (code %u)", derr);
     bool short_cap = false;
     for (uint32_t i = 0; i < n_batches; ++i) {

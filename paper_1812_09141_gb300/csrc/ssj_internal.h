@@ -44,6 +44,7 @@ struct Instance {
     uint64_t magic;             // div_magic(den) for Jaccard and Dice
     uint64_t n_cands;
     uint64_t cap;
+    uint64_t r_n_chunks, s_n_chunks;  // 16-byte blocks of the token arrays (bounds of the checked build)
     uint32_t r_n_sets, s_n_sets;
     uint32_t p, den;            // t = p / q; den: see SIM_*
     uint32_t n_probes;
@@ -97,7 +98,18 @@ enum : uint32_t {
     ERR_CAND_ID = 2u,
     ERR_OFFSETS = 4u,
     ERR_GUARD = 8u,   // an internal loop bound was reached (a bug, reported instead of hanging)
+    ERR_BOUNDS = 16u, // checked build (SSJ_CHECKED): an index was out of bounds; the access was skipped
 };
+
+// The checked build (-DSSJ_CHECKED, libssj_checked.so) tests every index of
+// the plan and verify kernels against its array's extent before the access;
+// an index out of bounds sets ERR_BOUNDS and the access is skipped (a load
+// reads zeros), so a bug shows as an error status, never as a fault.
+#ifdef SSJ_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
 
 constexpr uint32_t kWarpItemCands = 8;   // most candidates per warp work item
 constexpr uint32_t kBlockItemCands = 16; // most candidates per block work item

@@ -61,6 +61,43 @@ constexpr uint32_t kFlatGrab = 4;                  // 32-pair chunks taken per d
 constexpr uint32_t kCont = 64;                     // parked pairs per warp in phase 3
 constexpr int kPlanThreads = 256;                  // plan kernel block size
 
+// Checked build (SSJ_CHECKED): the functions that are not inlined take the
+// token arrays' remaining extents and the error word as extra arguments;
+// the product build passes nothing and the checks compile away.
+#ifdef SSJ_CHECKED
+#define CHK_PARAMS , uint64_t chk_rlim, uint64_t chk_slim, uint32_t* chk_err
+#define CHK_ARGS(rl, sl, e) , (rl), (sl), (e)
+#define CHK_ERR_PARAM , uint32_t* chk_err
+#define CHK_ERR_ARG(e) , (e)
+#define CHK_RLIM chk_rlim
+#define CHK_SLIM chk_slim
+#define CHK_ERR chk_err
+#else
+#define CHK_PARAMS
+#define CHK_ARGS(rl, sl, e)
+#define CHK_ERR_PARAM
+#define CHK_ERR_ARG(e)
+#define CHK_RLIM (~0ull)
+#define CHK_SLIM (~0ull)
+#define CHK_ERR (static_cast<uint32_t*>(nullptr))
+#endif
+
+// Checked build: false, and ERR_BOUNDS set, when idx is not below n.
+__device__ __forceinline__ bool in_bounds(uint64_t idx, uint64_t n, uint32_t* err) {
+    if (kChecked && idx >= n) {
+        atomicOr(err, ERR_BOUNDS);
+        return false;
+    }
+    return true;
+}
+
+// Block idx of a token array with lim blocks from base on (the checked
+// build reads zeros past the end).
+__device__ __forceinline__ uint4 ld_block(const uint4* base, uint64_t idx, uint64_t lim, uint32_t* err) {
+    if (!in_bounds(idx, lim, err)) return make_uint4(0u, 0u, 0u, 0u);
+    return __ldg(base + idx);
+}
+
 // A parked pair with its merge state.
 struct ContEntry {
     uint4 m0;  // probe slot (its r id is rid[slot]), s id, current 16-byte block of r, of s (token array indices)
@@ -151,12 +188,15 @@ __device__ __forceinline__ void emit_triple(ssj_triple* out, uint64_t cap, bool 
 
 // Copy the 16-byte chunks covering tokens [x0, x0+n) of a set into dst
 // (16-byte aligned): dst[k] holds token (x0 & ~3) + k.
+// (lim: blocks of the token array from set4 on; dst_blocks: room at dst;
+// both checked in the checked build only.)
 template <int G>
 __device__ __forceinline__ void stage(const uint4* __restrict__ set4, uint32_t x0, uint32_t n, uint32_t* dst,
-                                      int lane) {
+                                      int lane, uint64_t lim, uint32_t dst_blocks, uint32_t* err) {
     const uint32_t c_lo = x0 >> 2, c_hi = (x0 + n + 3) >> 2;
     uint4* d4 = reinterpret_cast<uint4*>(dst);
-    for (uint32_t c = c_lo + lane; c < c_hi; c += G) d4[c - c_lo] = __ldg(set4 + c);
+    for (uint32_t c = c_lo + lane; c < c_hi; c += G)
+        if (in_bounds(c - c_lo, dst_blocks, err)) d4[c - c_lo] = ld_block(set4, c, lim, err);
 }
 
 // One lane's share of a window: binary search of its cross diagonal
@@ -204,7 +244,7 @@ __device__ __forceinline__ void lane_merge(const uint32_t* A, uint32_t rw, const
 // -------------------------------------------------------------------------
 __device__ uint32_t warp_merge(const uint4* __restrict__ r4, uint32_t nr, const uint4* __restrict__ s4, uint32_t ns,
                                uint32_t req, bool early, bool r_staged, uint32_t* abuf, uint32_t* bbuf, int lane,
-                               bool* rejected) {
+                               bool* rejected CHK_PARAMS) {
     uint32_t i0 = 0, j0 = 0, o = 0;
     *rejected = false;
     for (;;) {
@@ -218,10 +258,10 @@ __device__ uint32_t warp_merge(const uint4* __restrict__ r4, uint32_t nr, const 
         if (r_staged) {
             A = abuf + i0;
         } else {
-            stage<32>(r4, i0, rw, abuf, lane);
+            stage<32>(r4, i0, rw, abuf, lane, CHK_RLIM, kWarpABuf / 4, CHK_ERR);
             A = abuf + (i0 & 3u);
         }
-        stage<32>(s4, j0, sw, bbuf, lane);
+        stage<32>(s4, j0, sw, bbuf, lane, CHK_SLIM, kWarpBBuf / 4, CHK_ERR);
         __syncwarp();
         const uint32_t* B = bbuf + (j0 & 3u);
         const uint32_t d = min((uint32_t)lane * kWarpD, Wc), de = min(d + kWarpD, Wc);
@@ -253,7 +293,7 @@ struct BlockSmem {
 template <int BT>
 __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const uint4* __restrict__ s4,
                                 uint32_t ns, uint32_t req, bool early, const uint32_t* rbuf, bool r_staged,
-                                uint32_t* wbuf_r, uint32_t* wbuf_s, BlockSmem<BT>* sm, bool* rejected) {
+                                uint32_t* wbuf_r, uint32_t* wbuf_s, BlockSmem<BT>* sm, bool* rejected CHK_PARAMS) {
     constexpr uint32_t W = BT * kBlockD;
     const int tid = threadIdx.x;
     uint32_t i0 = 0, j0 = 0, o = 0;
@@ -269,10 +309,10 @@ __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const
         if (r_staged) {
             A = rbuf + i0;
         } else {
-            stage<BT>(r4, i0, rw, wbuf_r, tid);
+            stage<BT>(r4, i0, rw, wbuf_r, tid, CHK_RLIM, (W + 16) / 4, CHK_ERR);
             A = wbuf_r + (i0 & 3u);
         }
-        stage<BT>(s4, j0, sw, wbuf_s, tid);
+        stage<BT>(s4, j0, sw, wbuf_s, tid, CHK_SLIM, (W + 16) / 4, CHK_ERR);
         __syncthreads();
         const uint32_t* B = wbuf_s + (j0 & 3u);
         const uint32_t d = min((uint32_t)tid * kBlockD, Wc), de = min(d + kBlockD, Wc);
@@ -302,7 +342,7 @@ __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const
 __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4& sn, const uint4* rb,
                                           const uint4* sb, uint32_t& rcur, uint32_t& scur, uint32_t& remr,
                                           uint32_t& rems, uint32_t& o, uint32_t req, bool early, bool& fin,
-                                          bool& rej) {
+                                          bool& rej, uint64_t rlim, uint64_t slim, uint32_t* err) {
     const bool bad = !fin && early && o + min(remr, rems) < req;
     const bool go = !fin && !bad;
     rej = rej || bad;
@@ -321,8 +361,8 @@ __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4
     scur += as ? 1u : 0u;
     remr = ar ? (remr > 4 ? remr - 4 : 0u) : remr;
     rems = as ? (rems > 4 ? rems - 4 : 0u) : rems;
-    if (ar && remr > 4) rn = __ldg(rb + rcur + 1);
-    if (as && rems > 4) sn = __ldg(sb + scur + 1);
+    if (ar && remr > 4) rn = ld_block(rb, rcur + 1, rlim, err);
+    if (as && rems > 4) sn = ld_block(sb, scur + 1, slim, err);
     fin = fin || bad || remr == 0 || rems == 0;
 }
 
@@ -335,14 +375,16 @@ __device__ __forceinline__ void lean_step(uint4& rc, uint4& rn, uint4& sc, uint4
 // the r id is read from it only for a survivor.  Returns the new number of
 // parked pairs.
 __device__ __noinline__ uint32_t drain_parked(ContEntry* cont, uint32_t n_cont, uint32_t m, uint32_t min_live,
-                                              const Instance* table, const uint32_t* rid_of_slot, int lane) {
+                                              const Instance* table, const uint32_t* rid_of_slot,
+                                              int lane CHK_ERR_PARAM) {
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint4 zero4 = make_uint4(0, 0, 0, 0);
     const uint32_t base = n_cont - m;
-    const bool have = (uint32_t)lane < m;
+    const bool have = (uint32_t)lane < m && in_bounds(base + lane, kCont, CHK_ERR);
     uint32_t slot = 0, sid = 0, rcur = 0, scur = 0, remr = 0, rems = 0, req = 0, o = 0, inst = 0;
     const uint4* rb = nullptr;
     const uint4* sb = nullptr;
+    uint64_t rlim = 0, slim = 0;
     bool early = true, fin = true, rej = false;
     uint4 rc = zero4, rn = zero4, sc = zero4, sn = zero4;
     if (have) {
@@ -360,17 +402,19 @@ __device__ __noinline__ uint32_t drain_parked(ContEntry* cont, uint32_t n_cont, 
         const Instance& I = table[inst];
         rb = I.r_toks4;
         sb = I.s_toks4;
+        rlim = I.r_n_chunks;
+        slim = I.s_n_chunks;
         early = !(I.flags & VF_EMIT_ALL);
         fin = remr == 0 || rems == 0;
-        rc = __ldg(rb + rcur);
-        if (remr > 4) rn = __ldg(rb + rcur + 1);
-        sc = __ldg(sb + scur);
-        if (rems > 4) sn = __ldg(sb + scur + 1);
+        rc = ld_block(rb, rcur, rlim, CHK_ERR);
+        if (remr > 4) rn = ld_block(rb, rcur + 1, rlim, CHK_ERR);
+        sc = ld_block(sb, scur, slim, CHK_ERR);
+        if (rems > 4) sn = ld_block(sb, scur + 1, slim, CHK_ERR);
     }
     __syncwarp();  // every entry is read before any is written again
     while ((uint32_t)__popc(__ballot_sync(kFull, !fin)) >= min_live) {  // two steps per check
-        if (!fin) lean_step(rc, rn, sc, sn, rb, sb, rcur, scur, remr, rems, o, req, early, fin, rej);
-        if (!fin) lean_step(rc, rn, sc, sn, rb, sb, rcur, scur, remr, rems, o, req, early, fin, rej);
+        if (!fin) lean_step(rc, rn, sc, sn, rb, sb, rcur, scur, remr, rems, o, req, early, fin, rej, rlim, slim, CHK_ERR);
+        if (!fin) lean_step(rc, rn, sc, sn, rb, sb, rcur, scur, remr, rems, o, req, early, fin, rej, rlim, slim, CHK_ERR);
     }
     if (have && fin && (!early || (!rej && o >= req))) {
         const Instance& I = table[inst];
@@ -428,6 +472,7 @@ __device__ __noinline__ void lane_item(const Instance& I, const WorkItem& wi, ui
     bool active = false;
     uint32_t s_id = 0, ns = 0, req = 0, sq = 0;
     const uint4* s4 = nullptr;
+    uint64_t slim = 0;
     BlockState st;
     st.qi = st.qj = st.o = 0;
     st.fin = true;
@@ -438,7 +483,7 @@ __device__ __noinline__ void lane_item(const Instance& I, const WorkItem& wi, ui
         if (idle && cursor < wi.n) {
             const uint32_t my = cursor + __popc(idle & lt_mask);
             if (!active && my < wi.n) {
-                const uint32_t s = I.cand_ids[wi.c0 + my];
+                const uint32_t s = in_bounds(wi.c0 + my, I.n_cands, err) ? I.cand_ids[wi.c0 + my] : ~0u;
                 if (s >= I.s_n_sets) {
                     atomicOr(err, ERR_CAND_ID);
                 } else if (!(self_join && s == wi.r)) {
@@ -451,12 +496,13 @@ __device__ __noinline__ void lane_item(const Instance& I, const WorkItem& wi, ui
                         req = q;
                         sq = (ns + 3) >> 2;
                         s4 = I.s_toks4 + ds.x;
+                        slim = I.s_n_chunks - ds.x;
                         st.qi = st.qj = st.o = 0;
                         st.rej = false;
                         st.fin = nr == 0 || ns == 0;
                         rc = rq ? rsm[0] : zero4;
-                        sc = sq ? __ldg(s4) : zero4;
-                        sn = sq > 1 ? __ldg(s4 + 1) : zero4;
+                        sc = sq ? ld_block(s4, 0, slim, err) : zero4;
+                        sn = sq > 1 ? ld_block(s4, 1, slim, err) : zero4;
                     }
                 }
             }
@@ -469,10 +515,10 @@ __device__ __noinline__ void lane_item(const Instance& I, const WorkItem& wi, ui
         if (active && !st.fin) {
             bool ar, as;
             block_step(rc, sc, nr, ns, req, early, st, ar, as);
-            if (ar && st.qi < rq) rc = rsm[st.qi];
+            if (ar && st.qi < rq && in_bounds(st.qi, kWarpABuf / 4, err)) rc = rsm[st.qi];
             if (as) {
                 sc = sn;
-                if (st.qj + 1 < sq) sn = __ldg(s4 + st.qj + 1);
+                if (st.qj + 1 < sq) sn = ld_block(s4, st.qj + 1, slim, err);
             }
         }
         const bool done = active && st.fin;
@@ -567,6 +613,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
     __shared__ uint32_t s_slot[2][kPlanWarps][32];            // the lanes' probe slots
     __shared__ unsigned long long s_pre[2][kPlanWarps + 1];   // exclusive prefix of the tiles' padded ranges
     __shared__ const uint32_t* s_cand[2][kPlanWarps];         // the tiles' candidate arrays
+    __shared__ unsigned long long s_ncand[2][kPlanWarps];     // their lengths (checked build)
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     if (blockIdx.x == 0) {
@@ -614,8 +661,10 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
                     if (c1 > c0) atomicOr(&a.ctr->err, ERR_PROBE_ID);
                 } else {
                     rdesc = I.r_desc[r];
-                    a.rdesc[slot] = rdesc;
-                    a.rid[slot] = r;
+                    if (in_bounds(slot, 32ull * a.n_tiles + 1, &a.ctr->err)) {
+                        a.rdesc[slot] = rdesc;
+                        a.rid[slot] = r;
+                    }
                     n = c1 - c0;
                     bin = probe_bin(a, I.flags, rdesc.y, n);
                 }
@@ -675,6 +724,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
         s_c0[par][warp][lane] = c0;
         s_slot[par][warp][lane] = slot;
         if (lane == 0) s_cand[par][warp] = I.cand_ids;
+        if (kChecked && lane == 0) s_ncand[par][warp] = I.n_cands;
         if (threadIdx.x == 0) {
             unsigned long long acc = 0;
             for (int w = 0; w < kPlanWarps; ++w) {
@@ -723,8 +773,10 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
                                 while (s_incl[par][w][pos] <= fl) ++pos;  // past probes that end before fl
                             }
                             const unsigned long long ex = pos ? s_incl[par][w][pos - 1] : 0ull;
+                            const unsigned long long ci = s_c0[par][w][pos] + (fl - ex);
                             out[2 * e] = s_slot[par][w][pos];
-                            out[2 * e + 1] = s_cand[par][w][s_c0[par][w][pos] + (fl - ex)];
+                            out[2 * e + 1] =
+                                in_bounds(ci, kChecked ? s_ncand[par][w] : 0ull, &a.ctr->err) ? s_cand[par][w][ci] : 0u;
                         }
                     }
                     uint4* dst = reinterpret_cast<uint4*>(a.pairs + cta_base + f0);
@@ -805,19 +857,22 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
             __syncthreads();
             if (it >= n_block) break;
             const WorkItem bi = a.block_items[it];
+            if (!in_bounds(bi.inst, a.n_inst, &a.ctr->err)) continue;  // (uniform over the CTA)
             const Instance& I = table[bi.inst];
             const uint32_t flags = I.flags;
             const bool emit_all = (flags & VF_EMIT_ALL) != 0, early = !emit_all;
             const bool self_join = (flags & VF_SELF_JOIN) != 0;
+            if (!in_bounds(bi.r, I.r_n_sets, &a.ctr->err)) continue;
             const uint2 dr = I.r_desc[bi.r];
             const uint32_t nr = dr.y;
             const uint4* r4 = I.r_toks4 + dr.x;
             const bool r_staged = nr + 4 <= kBlockRCap;
             if (r_staged) {
-                stage<BT>(r4, 0, nr, rbuf, tid);
+                stage<BT>(r4, 0, nr, rbuf, tid, I.r_n_chunks - dr.x, (kBlockRCap + 16) / 4, &a.ctr->err);
                 __syncthreads();
             }
             for (uint32_t m = 0; m < bi.n; ++m) {
+                if (!in_bounds(bi.c0 + m, I.n_cands, &a.ctr->err)) break;
                 const uint32_t s = I.cand_ids[bi.c0 + m];
                 if (s >= I.s_n_sets) {
                     if (tid == 0) atomicOr(&a.ctr->err, ERR_CAND_ID);
@@ -830,7 +885,8 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
                 bool rej;
                 const uint32_t o = block_merge<BT>(r4, nr, I.s_toks4 + ds.x, ns, req, early, rbuf, r_staged, wr, ws,
-                                                   &bsm, &rej);
+                                                   &bsm, &rej
+                                                   CHK_ARGS(I.r_n_chunks - dr.x, I.s_n_chunks - ds.x, &a.ctr->err));
                 const bool pass = emit_all || (!rej && o >= req);
                 if (pass && tid == 0) {
                     const unsigned long long idx = atomicAdd(I.count, 1ull);
@@ -855,16 +911,18 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
             it = __shfl_sync(kFull, it, 0);
             if (it >= n_warp) break;
             const WorkItem wi = a.warp_items[it];
+            if (!in_bounds(wi.inst, a.n_inst, &a.ctr->err)) continue;  // (uniform over the warp)
             const Instance& I = table[wi.inst];
             const uint32_t flags = I.flags;
             const bool emit_all = (flags & VF_EMIT_ALL) != 0, early = !emit_all;
             const bool self_join = (flags & VF_SELF_JOIN) != 0;
+            if (!in_bounds(wi.r, I.r_n_sets, &a.ctr->err)) continue;
             const uint2 dr = I.r_desc[wi.r];
             const uint32_t nr = dr.y;
             const uint4* r4 = I.r_toks4 + dr.x;
             const bool r_staged = nr + 4 <= kWarpRCap;
             if (r_staged) {
-                stage<32>(r4, 0, nr, abuf, lane);
+                stage<32>(r4, 0, nr, abuf, lane, I.r_n_chunks - dr.x, kWarpABuf / 4, &a.ctr->err);
                 __syncwarp();
             }
             if (wi.pad == 1 && r_staged) {
@@ -873,6 +931,7 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 continue;
             }
             for (uint32_t m = 0; m < wi.n; ++m) {
+                if (!in_bounds(wi.c0 + m, I.n_cands, &a.ctr->err)) break;
                 const uint32_t s = I.cand_ids[wi.c0 + m];
                 if (s >= I.s_n_sets) {
                     if (lane == 0) atomicOr(&a.ctr->err, ERR_CAND_ID);
@@ -885,7 +944,8 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
                 bool rej;
                 const uint32_t o =
-                    warp_merge(r4, nr, I.s_toks4 + ds.x, ns, req, early, r_staged, abuf, bbuf, lane, &rej);
+                    warp_merge(r4, nr, I.s_toks4 + ds.x, ns, req, early, r_staged, abuf, bbuf, lane,
+                               &rej CHK_ARGS(I.r_n_chunks - dr.x, I.s_n_chunks - ds.x, &a.ctr->err));
                 const bool pass = emit_all || (!rej && o >= req);
                 if (pass) {
                     if (flags & VF_COUNT_ONLY) {
@@ -912,7 +972,7 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
         // Pass 2 (drain_parked): the last m parked pairs, one per lane, merged
         // while at least min_live lanes still work; the rest are parked again.
         auto drain = [&](uint32_t m, uint32_t live) {
-            n_cont = drain_parked(cont, n_cont, m, live, table, a.rid, lane);
+            n_cont = drain_parked(cont, n_cont, m, live, table, a.rid, lane CHK_ERR_ARG(&a.ctr->err));
         };
         const uint32_t min_live = a.drain_min_live ? min(max(a.drain_min_live, 1u), 24u) : kDrainMinLive;
 
@@ -928,7 +988,9 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 const unsigned long long first = ((unsigned long long)u * kFlatGrab + sub) * 32;
                 if (first >= n_pairs) break;  // warp-uniform
                 // the chunk's instance (uniform)
+                if (!in_bounds(first / 32, a.pair_cap / 32 + 1, &a.ctr->err)) break;
                 const uint32_t inst = a.chunk_inst[first / 32];
+                if (!in_bounds(inst, a.n_inst, &a.ctr->err)) continue;
                 const Instance& I = table[inst];
                 const uint32_t flags = I.flags;
                 const bool emit_all = (flags & VF_EMIT_ALL) != 0, early = !emit_all;
@@ -942,7 +1004,11 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 uint32_t pr_k = 0, ps_id = 0, nr = 0, ns = 0, req = 0;
                 uint2 dr = make_uint2(0, 0), ds = make_uint2(0, 0);
                 {
-                    const PairRef pr = a.pairs[first + lane];
+                    PairRef pr;
+                    pr.k = kNoProbe;
+                    pr.s = 0;
+                    if (in_bounds(first + lane, a.pair_cap, &a.ctr->err)) pr = a.pairs[first + lane];
+                    if (pr.k != kNoProbe && !in_bounds(pr.k, 32ull * a.n_tiles + 1, &a.ctr->err)) pr.k = kNoProbe;
                     if (pr.k != kNoProbe) {
                         ps_id = pr.s;
                         if (ps_id >= s_n_sets) {
@@ -967,12 +1033,13 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 if (live) {
                     const uint4* r4 = r_toks4 + dr.x;
                     const uint4* s4 = s_toks4 + ds.x;
-                    if (nr > 0) r0 = __ldg(r4);
-                    if (nr > 4) r1 = __ldg(r4 + 1);
-                    if (nr > 8) r2 = __ldg(r4 + 2);
-                    if (ns > 0) s0 = __ldg(s4);
-                    if (ns > 4) s1 = __ldg(s4 + 1);
-                    if (ns > 8) s2 = __ldg(s4 + 2);
+                    const uint64_t rlim = I.r_n_chunks - dr.x, slim = I.s_n_chunks - ds.x;
+                    if (nr > 0) r0 = ld_block(r4, 0, rlim, &a.ctr->err);
+                    if (nr > 4) r1 = ld_block(r4, 1, rlim, &a.ctr->err);
+                    if (nr > 8) r2 = ld_block(r4, 2, rlim, &a.ctr->err);
+                    if (ns > 0) s0 = ld_block(s4, 0, slim, &a.ctr->err);
+                    if (ns > 4) s1 = ld_block(s4, 1, slim, &a.ctr->err);
+                    if (ns > 8) s2 = ld_block(s4, 2, slim, &a.ctr->err);
                 }
                 BlockState st;
                 st.qi = st.qj = st.o = 0;
@@ -1003,7 +1070,7 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 const uint32_t kmask = __ballot_sync(kFull, park);
                 if (kmask) {
                     while (n_cont + 32 > kCont) drain(32, min_live);  // room for a full warp of parked pairs
-                    if (park) {
+                    if (park && in_bounds(n_cont + __popc(kmask & lt_mask), kCont, &a.ctr->err)) {
                         ContEntry* ce = cont + n_cont + __popc(kmask & lt_mask);
                         ce->m0 = make_uint4(pr_k, ps_id, dr.x + st.qi, ds.x + st.qj);
                         ce->m1 = make_uint4(nr - 4 * st.qi, ns - 4 * st.qj, req, st.o);

@@ -37,10 +37,13 @@ def _declared_functions():
     return names
 
 
-def test_every_declared_function_is_exported_and_bound():
+@pytest.mark.parametrize("name", ["libssj.so", "libssj_checked.so"])
+def test_every_declared_function_is_exported_and_bound(name):
+    """The product library and its checked build export every function include/*.h declares."""
     declared = _declared_functions()
     assert "ssj_verify_batch" in declared and "ssj_submit" in declared
-    out = subprocess.run(["nm", "-D", "--defined-only", ssj.LIB_PATH], capture_output=True, text=True, check=True)
+    path = os.path.join(os.path.dirname(ssj.LIB_PATH), name)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True)
     exported = {ln.split()[-1] for ln in out.stdout.splitlines() if " T " in ln}
     missing = declared - exported
     assert not missing, f"declared but not exported: {missing}"
