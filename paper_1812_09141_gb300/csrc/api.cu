@@ -25,6 +25,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "arith.h"
 #include "ssj_internal.h"
@@ -40,6 +41,19 @@ void renumber_by_frequency(const uint64_t* offsets, const uint32_t* tokens, uint
 }  // namespace ssj
 
 using namespace ssj;
+
+namespace {
+
+// An NVTX range over a scope: names the API calls and the serving phases on
+// a profiler's timeline (a no-op when no tool is attached).
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -469,6 +483,7 @@ extern "C" ssj_status ssj_set_short_pairs(ssj_ctx* ctx, uint32_t drain_min_live)
 
 extern "C" ssj_status ssj_load_collection(ssj_ctx* ctx, const uint64_t* offsets, const uint32_t* tokens,
                                           uint32_t n_sets, uint32_t flags, ssj_coll* out) {
+    NvtxScope nvtx_scope("ssj_load_collection");
     if (!ctx || !offsets || !out) return fail(ctx, SSJ_EINVAL, "NULL argument");
     if (flags & ~(SSJ_RENUMBER_BY_FREQ | SSJ_VALIDATE | SSJ_PIN_L2)) return fail(ctx, SSJ_EINVAL, "unknown load flag");
     if (offsets[0] != 0) return fail(ctx, SSJ_EINVAL, "offsets[0] must be 0");
@@ -650,6 +665,7 @@ extern "C" ssj_status ssj_device_error(ssj_ctx* ctx, uint32_t* code) {
 
 extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* out, uint64_t cap,
                                        uint64_t* n_out) {
+    NvtxScope nvtx_scope("ssj_verify_batch");
     Collection *R, *S;
     ssj_status st = resolve(ctx, batch, &R, &S);
     if (st != SSJ_OK) return st;
@@ -748,6 +764,7 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
 
 extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches, uint32_t n_batches,
                                          ssj_triple* const* outs, const uint64_t* caps, uint64_t* n_outs) {
+    NvtxScope nvtx_scope("ssj_verify_batches");
     if (!ctx || (n_batches && (!batches || !outs || !caps || !n_outs))) return fail(ctx, SSJ_EINVAL, "NULL argument");
     if (n_batches == 0) return SSJ_OK;
     std::vector<Instance> table(n_batches);
@@ -858,6 +875,7 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
 
 extern "C" ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uint32_t q, uint32_t flags,
                                     ssj_triple* out, uint64_t cap, uint64_t* n_out, uint64_t* n_candidates) {
+    NvtxScope nvtx_scope("ssj_self_join");
     if (!ctx || !n_out) return fail(ctx, SSJ_EINVAL, "NULL argument");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_SIM_MASK | SSJ_JOIN_POSITIONAL |
                            SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE;
@@ -1042,6 +1060,7 @@ extern "C" ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uin
 
 extern "C" ssj_status ssj_verify_groups(ssj_ctx* ctx, const ssj_group_batch* gb, ssj_triple* out, uint64_t cap,
                                         uint64_t* n_out, uint64_t* n_pairs) {
+    NvtxScope nvtx_scope("ssj_verify_groups");
     if (!ctx || !gb || !n_out) return fail(ctx, SSJ_EINVAL, "NULL argument");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_SIM_MASK | SSJ_FORCE_THREAD |
                            SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE;
@@ -1277,6 +1296,7 @@ void completion_loop(ssj_ctx* ctx, int slot) {
             t = sl.pending;
         }
         std::string err;
+        NvtxScope nvtx_scope("ssj serving: wait for the batch's kernels, copy its results");
         cudaError_t e = cudaEventSynchronize(t->kernel_done);
         uint64_t count = 0;
         if (e == cudaSuccess) {
@@ -1318,6 +1338,7 @@ void completion_loop(ssj_ctx* ctx, int slot) {
 }  // namespace
 
 extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t* ticket) {
+    NvtxScope nvtx_scope("ssj_submit");
     if (!ctx || !batch || !ticket) return fail(ctx, SSJ_EINVAL, "NULL argument");
     std::unique_lock<std::mutex> lk(ctx->mu);
     Collection *R, *S;
@@ -1486,6 +1507,7 @@ extern "C" ssj_status ssj_poll(ssj_ctx* ctx, uint64_t ticket, int timeout_ms, in
 }
 
 extern "C" ssj_status ssj_results(ssj_ctx* ctx, uint64_t ticket, ssj_triple* out, uint64_t cap, uint64_t* n_out) {
+    NvtxScope nvtx_scope("ssj_results");
     if (!ctx || !n_out) return SSJ_EINVAL;
     std::unique_lock<std::mutex> lk(ctx->mu);
     auto it = ctx->tickets.find(ticket);
@@ -1650,6 +1672,7 @@ extern "C" ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, u
 }
 
 extern "C" ssj_status ssj_multi_launch(ssj_ctx* ctx, ssj_multi* m, void* stream) {
+    NvtxScope nvtx_scope("ssj_multi_launch");
     if (!ctx || !m) return SSJ_EINVAL;
     DeviceGuard g(ctx->device);
     ctx->last_ctr = m->a.ctr;
@@ -1737,6 +1760,7 @@ float time_setting(ssj_ctx* ctx, const ssj_multi* m, uint32_t tmax, uint32_t lma
 
 extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* stream, uint32_t reps,
                                          ssj_tune_result* out) {
+    NvtxScope nvtx_scope("ssj_multi_autotune");
     if (!ctx || !m || !out) return fail(ctx, SSJ_EINVAL, "NULL argument");
     reps = std::max<uint32_t>(reps, 3);
     DeviceGuard g(ctx->device);

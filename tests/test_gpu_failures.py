@@ -1,0 +1,141 @@
+"""Failure paths of the serving and batch API, made on the host (no GPU fault, trap or hang):
+busy collections, full slots, a batch over the memory budget, unknown tickets, a result buffer
+too small, a poll that times out, malformed batches and a context that outlives its faults."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+import paper_1812_09141_gb300 as ssj
+from paper_1812_09141_gb300 import _build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def coll():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    _build.build()
+    spec = synth.tiny_self_join(seed=1001, n=600)
+    spec.plant_frac, spec.plant_edits = 0.2, 2
+    return synth.collection(spec)
+
+
+def _status(ctx, fn, *args):
+    return fn(ctx, *args)
+
+
+def test_unload_while_a_ticket_is_uncollected_is_busy(coll):
+    ctx = ssj.ssj_create(0, max_inflight=2)
+    try:
+        h = ssj.ssj_load_collection(ctx, coll.offsets, coll.tokens)
+        b = synth.all_pairs_batch(coll.n)
+        t = ssj.ssj_submit(ctx, h, h, 4, 5, b.probe_ids, b.cand_offsets, b.cand_ids)
+        assert t is not None
+        assert ssj.ssj_poll(ctx, t, -1)  # finished on the GPU, but not collected yet
+        with pytest.raises(ssj.SsjError) as ei:
+            ssj.ssj_unload_collection(ctx, h)
+        assert ei.value.status == ssj.SSJ_EBUSY
+        got = ssj.triples_to_array(ssj.ssj_results(ctx, t))
+        assert np.array_equal(got, oracle.sort_triples(oracle.bruteforce_self(coll.offsets, coll.tokens, 4, 5)))
+        ssj.ssj_unload_collection(ctx, h)  # free once collected
+    finally:
+        ssj.ssj_destroy(ctx)
+
+
+def test_full_slots_answer_eagain_until_a_ticket_is_collected(coll):
+    ctx = ssj.ssj_create(0, max_inflight=2)
+    try:
+        h = ssj.ssj_load_collection(ctx, coll.offsets, coll.tokens)
+        b = synth.all_pairs_batch(coll.n)
+        args = (h, h, 4, 5, b.probe_ids, b.cand_offsets, b.cand_ids)
+        t1, t2 = ssj.ssj_submit(ctx, *args), ssj.ssj_submit(ctx, *args)
+        assert t1 is not None and t2 is not None
+        assert ssj.ssj_submit(ctx, *args) is None  # SSJ_EAGAIN: both slots hold uncollected tickets
+        assert ssj.ssj_poll(ctx, t1, -1)
+        r1 = ssj.ssj_results(ctx, t1)
+        t3 = ssj.ssj_submit(ctx, *args)  # a slot is free again
+        assert t3 is not None
+        for t in (t2, t3):
+            assert ssj.ssj_poll(ctx, t, -1)
+            assert np.array_equal(ssj.triples_to_array(ssj.ssj_results(ctx, t)), ssj.triples_to_array(r1))
+    finally:
+        ssj.ssj_destroy(ctx)
+
+
+def test_batch_over_the_budget_unknown_ticket_and_small_buffer(coll):
+    ctx = ssj.ssj_create(0, mem_budget_bytes=1 << 20, max_inflight=2)
+    try:
+        h = ssj.ssj_load_collection(ctx, coll.offsets, coll.tokens)
+        big = synth.all_pairs_batch(coll.n)  # ~180k pairs: its device inputs exceed 1 MiB
+        with pytest.raises(ssj.SsjError) as ei:
+            ssj.ssj_submit(ctx, h, h, 4, 5, big.probe_ids, big.cand_offsets, big.cand_ids)
+        assert ei.value.status == ssj.SSJ_EINVAL
+        done = ctypes.c_int()
+        assert ssj.lib().ssj_poll(ctx, 987654321, 0, ctypes.byref(done)) == ssj.SSJ_ENOTFOUND
+        # a small batch fits; collecting it into a buffer that is too small answers SSJ_ENOMEM
+        # with the count needed, and the ticket stays collectable
+        probes = np.arange(0, 40, dtype=np.uint32)
+        offs = np.arange(0, 41, dtype=np.uint64) * 20
+        cands = np.concatenate([np.arange(i + 1, i + 21) % coll.n for i in range(40)]).astype(np.uint32)
+        t = ssj.ssj_submit(ctx, h, h, 1, 5, probes, offs, cands)
+        assert t is not None and ssj.ssj_poll(ctx, t, -1)
+        n = ctypes.c_uint64()
+        assert ssj.lib().ssj_results(ctx, t, None, 0, ctypes.byref(n)) == ssj.SSJ_OK
+        want = oracle.sort_triples(oracle.verify_batch(coll.offsets, coll.tokens, coll.offsets, coll.tokens, True,
+                                                       1, 5, probes, offs, cands))
+        assert n.value == len(want) and n.value >= 2
+        small = np.empty(1, dtype=ssj.TRIPLE_DTYPE)
+        assert ssj.lib().ssj_results(ctx, t, small.ctypes.data, 1, ctypes.byref(n)) == ssj.SSJ_ENOMEM
+        assert n.value == len(want)
+        got = ssj.triples_to_array(ssj.ssj_results(ctx, t))
+        assert np.array_equal(got, want)
+    finally:
+        ssj.ssj_destroy(ctx)
+
+
+def test_poll_timeout_is_not_destructive(coll):
+    """A zero-timeout poll right after submitting a large batch answers either 'not yet'
+    (SSJ_ETIMEDOUT) or 'done'; either way a waiting poll then completes it with the right join."""
+    ctx = ssj.ssj_create(0, max_inflight=2)
+    try:
+        spec = synth.long_sets(n=3000)
+        c = synth.collection(spec)
+        h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens)
+        pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, 3, 5, n_threads=4)
+        t = ssj.ssj_submit(ctx, h, h, 3, 5, pr, co, ci)
+        done = ctypes.c_int(7)
+        st = ssj.lib().ssj_poll(ctx, t, 0, ctypes.byref(done))
+        assert (st, done.value) in ((ssj.SSJ_ETIMEDOUT, 0), (ssj.SSJ_OK, 1))
+        assert ssj.ssj_poll(ctx, t, -1)
+        got = ssj.triples_to_array(ssj.ssj_results(ctx, t))
+        assert np.array_equal(got, oracle.sort_triples(oracle.verify_batch(c.offsets, c.tokens, c.offsets, c.tokens,
+                                                                           True, 3, 5, pr, co, ci)))
+    finally:
+        ssj.ssj_destroy(ctx)
+
+
+def test_context_survives_rejected_batches(coll):
+    """Malformed batches (ids out of range, bad offsets, bad thresholds) are rejected with a status,
+    and the same context then verifies a valid batch correctly."""
+    ctx = ssj.ssj_create(0)
+    try:
+        h = ssj.ssj_load_collection(ctx, coll.offsets, coll.tokens)
+        b = synth.all_pairs_batch(coll.n)
+        bad_ids = b.cand_ids.copy()
+        bad_ids[len(bad_ids) // 2] = coll.n + 5
+        bad_offs = b.cand_offsets.copy()
+        bad_offs[3] = bad_offs[5] + 1
+        for args in ((4, 5, b.probe_ids, b.cand_offsets, bad_ids), (4, 5, b.probe_ids, bad_offs, b.cand_ids),
+                     (6, 5, b.probe_ids, b.cand_offsets, b.cand_ids), (0, 5, b.probe_ids, b.cand_offsets, b.cand_ids)):
+            with pytest.raises(ssj.SsjError) as ei:
+                ssj.ssj_verify_batch(ctx, h, h, *args)
+            assert ei.value.status == ssj.SSJ_EINVAL
+        got = ssj.triples_to_array(ssj.ssj_verify_batch(ctx, h, h, 4, 5, b.probe_ids, b.cand_offsets, b.cand_ids))
+        assert np.array_equal(got, oracle.sort_triples(oracle.bruteforce_self(coll.offsets, coll.tokens, 4, 5)))
+    finally:
+        ssj.ssj_destroy(ctx)
