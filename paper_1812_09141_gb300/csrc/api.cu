@@ -94,6 +94,7 @@ struct Ticket {
     uint64_t count = 0;
     TicketState state = TicketState::kRunning;
     std::string error;
+    uint32_t derr = 0;  // device check bits of a failed batch
     int slot = -1;
 };
 
@@ -249,6 +250,21 @@ const void* device_view(const void* p) {
 // (the first and last offsets); ids and the monotonicity of the offsets are
 // checked on the device by the plan and verify kernels, which report
 // violations through the error word.
+// Status of a launch's device check bits: the caller's input errors (ids,
+// offsets) are SSJ_EINVAL even when a capacity guard fired as their
+// consequence; a guard or bounds check alone is a library bug, SSJ_EDEVICE.
+ssj_status device_check_status(ssj_ctx* ctx, uint32_t derr) {
+    if (derr & (ERR_PROBE_ID | ERR_CAND_ID | ERR_OFFSETS))
+        return fail(ctx, SSJ_EINVAL, "batch rejected by the device checks (code %u: %s%s%s)", derr,
+                    (derr & ERR_PROBE_ID) ? "probe id out of range " : "",
+                    (derr & ERR_CAND_ID) ? "candidate id out of range " : "",
+                    (derr & ERR_OFFSETS) ? "offsets not nondecreasing from 0 to n_cands" : "");
+    if (derr)
+        return fail(ctx, SSJ_EDEVICE, "internal device check fired (code %u: %s%s)", derr,
+                    (derr & ERR_GUARD) ? "loop bound reached " : "", (derr & ERR_BOUNDS) ? "index out of bounds" : "");
+    return SSJ_OK;
+}
+
 ssj_status validate_host_batch(ssj_ctx* ctx, const ssj_batch* b, uint64_t* n_cands) {
     if (b->n_probes && (!b->probe_ids || !b->cand_offsets)) return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
     if (!b->cand_offsets) {
@@ -738,14 +754,7 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
     const uint64_t count = *ctx->h_count;
     const uint32_t derr = *ctx->h_err;
     *n_out = count;
-    if (derr & (ERR_GUARD | ERR_BOUNDS))
-        return fail(ctx, SSJ_EDEVICE, "internal device check fired (code %u: %s%s)", derr,
-                    (derr & ERR_GUARD) ? "loop bound reached " : "", (derr & ERR_BOUNDS) ? "index out of bounds" : "");
-    if (derr)
-        return fail(ctx, SSJ_EINVAL, "batch rejected by the device checks (code %u: %s%s%s)", derr,
-                    (derr & ERR_PROBE_ID) ? "probe id out of range " : "",
-                    (derr & ERR_CAND_ID) ? "candidate id out of range " : "",
-                    (derr & ERR_OFFSETS) ? "offsets not nondecreasing from 0 to n_cands" : "");
+    if (derr) return device_check_status(ctx, derr);
     if (count_only) return SSJ_OK;
     const uint64_t n_copy = std::min(count, cap);
     if (!dev) {
@@ -848,10 +857,7 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_err, &a.ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const uint32_t derr = *ctx->h_err;
-    if (derr & (ERR_GUARD | ERR_BOUNDS))
-        return fail(ctx, SSJ_EDEVICE, "internal device check fired (code %u: %s%s)", derr,
-                    (derr & ERR_GUARD) ? "loop bound reached " : "", (derr & ERR_BOUNDS) ? "index out of bounds" : "");
-    if (derr) return fail(ctx, SSJ_EINVAL, "batch rejected by the device checks (code %u)", derr);
+    if (derr) return device_check_status(ctx, derr);
     bool short_cap = false;
     for (uint32_t i = 0; i < n_batches; ++i) {
         n_outs[i] = counts[i];
@@ -1301,7 +1307,10 @@ void completion_loop(ssj_ctx* ctx, int slot) {
         uint64_t count = 0;
         if (e == cudaSuccess) {
             count = *sl.h_count;
-            if (*sl.h_err) err = "device-side batch check failed";
+            if (*sl.h_err) {
+                err = "device-side batch check failed";
+                t->derr = *sl.h_err;
+            }
         } else {
             err = std::string("batch failed: ") + cudaGetErrorString(e);
         }
@@ -1502,7 +1511,8 @@ extern "C" ssj_status ssj_poll(ssj_ctx* ctx, uint64_t ticket, int timeout_ms, in
     }
     *done = ready() ? 1 : 0;
     if (!*done) return SSJ_ETIMEDOUT;
-    if (t->state == TicketState::kFailed) return fail(ctx, SSJ_EDEVICE, "%s", t->error.c_str());
+    if (t->state == TicketState::kFailed)
+        return t->derr ? device_check_status(ctx, t->derr) : fail(ctx, SSJ_EDEVICE, "%s", t->error.c_str());
     return SSJ_OK;
 }
 
@@ -1518,7 +1528,7 @@ extern "C" ssj_status ssj_results(ssj_ctx* ctx, uint64_t ticket, ssj_triple* out
     if (!out && t->state == TicketState::kDone) return SSJ_OK;
     ssj_status st = SSJ_OK;
     if (t->state == TicketState::kFailed) {
-        st = fail(ctx, SSJ_EDEVICE, "%s", t->error.c_str());
+        st = t->derr ? device_check_status(ctx, t->derr) : fail(ctx, SSJ_EDEVICE, "%s", t->error.c_str());
     } else if (!(t->flags & SSJ_COUNT_ONLY)) {
         if (cap < t->count) return fail(ctx, SSJ_ENOMEM, "%llu result pairs, room for %llu",
                                         (unsigned long long)t->count, (unsigned long long)cap);

@@ -25,10 +25,6 @@ def coll():
     return synth.collection(spec)
 
 
-def _status(ctx, fn, *args):
-    return fn(ctx, *args)
-
-
 def test_unload_while_a_ticket_is_uncollected_is_busy(coll):
     ctx = ssj.ssj_create(0, max_inflight=2)
     try:
@@ -122,7 +118,7 @@ def test_poll_timeout_is_not_destructive(coll):
 def test_context_survives_rejected_batches(coll):
     """Malformed batches (ids out of range, bad offsets, bad thresholds) are rejected with a status,
     and the same context then verifies a valid batch correctly."""
-    ctx = ssj.ssj_create(0)
+    ctx = ssj.ssj_create(0, max_inflight=2)
     try:
         h = ssj.ssj_load_collection(ctx, coll.offsets, coll.tokens)
         b = synth.all_pairs_batch(coll.n)
@@ -136,6 +132,20 @@ def test_context_survives_rejected_batches(coll):
                 ssj.ssj_verify_batch(ctx, h, h, *args)
             assert ei.value.status == ssj.SSJ_EINVAL
         got = ssj.triples_to_array(ssj.ssj_verify_batch(ctx, h, h, 4, 5, b.probe_ids, b.cand_offsets, b.cand_ids))
-        assert np.array_equal(got, oracle.sort_triples(oracle.bruteforce_self(coll.offsets, coll.tokens, 4, 5)))
+        want = oracle.sort_triples(oracle.bruteforce_self(coll.offsets, coll.tokens, 4, 5))
+        assert np.array_equal(got, want)
+        # the same through serving: the failed ticket reports SSJ_EINVAL and frees its slot
+        for _ in range(3):
+            t = ssj.ssj_submit(ctx, h, h, 4, 5, b.probe_ids, b.cand_offsets, bad_ids)
+            assert t is not None
+            with pytest.raises(ssj.SsjError) as ei:
+                ssj.ssj_poll(ctx, t, -1)
+            assert ei.value.status == ssj.SSJ_EINVAL
+            with pytest.raises(ssj.SsjError) as ei:
+                ssj.ssj_results(ctx, t)
+            assert ei.value.status == ssj.SSJ_EINVAL
+        t = ssj.ssj_submit(ctx, h, h, 4, 5, b.probe_ids, b.cand_offsets, b.cand_ids)
+        assert ssj.ssj_poll(ctx, t, -1)
+        assert np.array_equal(ssj.triples_to_array(ssj.ssj_results(ctx, t)), want)
     finally:
         ssj.ssj_destroy(ctx)
