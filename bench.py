@@ -1,23 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark: candidate pairs verified per second on one GB300.
 
-Workload (default "short_sets"): the prefix-filter self-join over 200,000
-short sets (sizes lognormal mean 20, sigma 0.6, clipped 2..200; Zipf(1.0)
-tokens over a 1,000,000 vocabulary), at Jaccard t in {0.9, 0.8, 0.7, 0.6}.
-The CPU feeder produces the four candidate batches once (untimed); one
-step verifies all four on the GPU in one batched launch (one plan and one
-verify kernel over the four instances), with the granularity chosen by the
-library's autotuner beforehand.  Synthetic, seeded data.  Other workloads:
-tiny (all 499,500 pairs of 1,000 sets), long_sets, serving_collection,
-uneven_instances (256 joins in one launch), serving (continuous batching:
-latency percentiles and the filter/verify co-process).
+Workload (default "uneven_instances"): 256 independent prefix-filter
+self-joins verified in one batched launch (one plan and one persistent
+verify kernel over every instance): collection sizes log-uniform 500..50,000
+sets, mean set size log-uniform 5..500 (lognormal, sigma 0.6), Zipf s in
+[0.6, 1.2] over 1e5 tokens, t uniform over {0.6, ..., 0.95}.  The CPU feeder
+produces the candidate batches once (untimed); the granularity is chosen by
+the library's autotuner beforehand.  Synthetic, seeded data.  Other
+workloads: tiny (all 499,500 pairs of 1,000 sets), short_sets (200k short
+sets, four thresholds), long_sets, serving_collection, rs_short, serving
+(continuous batching only), candgen.
 
 value   pairs/s with inputs resident in HBM; L2 is flushed (512 MiB write)
         before every timed step; CUDA events on the launching stream; max
-        over ranks.
+        over ranks.  With N ranks every batch is split into N contiguous
+        probe ranges, one per rank (strong scaling; no data exchange).
 e2e     the same metric through the public synchronous call with pinned
         host buffers: host->device copies, kernels and the result readback
         in the timed region.
+served  (default workload, one rank) continuous batching on the resident
+        1,000,000-set collection: p50/p99 submit-to-result latency of 1,000
+        Poisson-arriving requests at 0.5x and 0.9x of the closed-loop peak,
+        device-memory budget M_c = 4 GiB.
 roofline  algorithmic bytes of the verify kernel (candidate stream, set
         descriptors, the tokens the positional filter lets the merge read,
         results) over its own event-timed duration, against the measured HBM
@@ -190,24 +195,36 @@ def oracle_accounting(colls, batches):
         return list(ex.map(one, batches))
 
 
-def cpu_baseline(colls, batches, min_seconds=10.0, max_seconds=30.0, max_call_pairs=8_000_000):
-    """The oracle (single-threaded C) timed on the host over the workload's batches, in order,
-    for at least min_seconds: whole batches while they are small, else probe-prefix slices of
-    at most max_call_pairs candidates taken from each batch in turn, so the sample stays
-    bounded and covers every instance."""
+def stride_sample(batches, target_pairs: int):
+    """Every k-th probe of each batch with all of its candidates, k chosen so that the sample
+    holds about target_pairs candidates (k = 1: the whole batches).  A uniform stride over probes
+    is not biased by the feeder's size order.  Returns (sample batches, k)."""
+    pairs_step = sum(len(b[5]) for b in batches)
+    stride = max(1, int(math.ceil(pairs_step / max(target_pairs, 1))))
+    if stride == 1:
+        return batches, 1
+    sample = []
+    for k, p, q, pr, co, ci in batches:
+        co64 = co.astype(np.int64)
+        pick = np.arange(0, len(pr), stride)
+        counts = co64[pick + 1] - co64[pick]
+        offs = np.zeros(len(pick) + 1, dtype=np.uint64)
+        offs[1:] = np.cumsum(counts)
+        cands = (np.concatenate([ci[co64[a]:co64[a + 1]] for a in pick]) if len(pick)
+                 else np.zeros(0, dtype=np.uint32))
+        sample.append((k, p, q, pr[pick], offs, cands.astype(np.uint32)))
+    return sample, stride
+
+
+def cpu_baseline(colls, batches, min_seconds=10.0, max_seconds=30.0, pass_pairs=4_000_000):
+    """The oracle (single-threaded C) timed on the host over a fixed sample of the workload's
+    batches (stride_sample, about pass_pairs candidates), repeated for at least min_seconds."""
     import oracle
     pairs_step = sum(len(b[5]) for b in batches)
-    calls = []
-    for k, p, q, pr, co, ci in batches:
-        co = co.astype(np.int64)
-        if co[-1] <= max_call_pairs:
-            calls.append((k, p, q, pr, co.astype(np.uint64), ci))
-        else:
-            b = max(1, int(np.searchsorted(co, max_call_pairs, side="right")) - 1)
-            calls.append((k, p, q, pr[:b], co[:b + 1].astype(np.uint64), ci[:int(co[b])]))
+    sample, stride = stride_sample(batches, pass_pairs)
     pairs, total_t, reps = 0, 0.0, 0
     while total_t < min_seconds and reps < 1000:
-        for k, p, q, pr, co, ci in calls:
+        for k, p, q, pr, co, ci in sample:
             cR, cS, selfj = coll_pair(colls, k)
             t0 = time.perf_counter()
             oracle.verify_batch(cR.offsets, cR.tokens, cS.offsets, cS.tokens, selfj, p, q, pr, co, ci, sim=SIM)
@@ -218,9 +235,9 @@ def cpu_baseline(colls, batches, min_seconds=10.0, max_seconds=30.0, max_call_pa
         reps += 1
         if total_t > max_seconds:
             break
-    whole = all(len(c[5]) == len(b[5]) for c, b in zip(calls, batches))
-    what = (f"{pairs / max(pairs_step, 1):.2f} steps of {pairs_step}" if whole else
-            f"probe-prefix slices of <= {max_call_pairs} candidates of each of the {len(batches)} batches")
+    what = (f"{pairs / max(pairs_step, 1):.2f} steps of {pairs_step}" if stride == 1 else
+            f"every {stride}-th probe of each of the {len(batches)} batches with all its candidates, "
+            f"{reps} pass(es)")
     return {"value": pairs / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{pairs} candidate pairs of the workload ({what}), {total_t:.1f} s of single-threaded CPU work"}
 
@@ -364,9 +381,35 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def whole_job_value(pairs_per_step: int, steps: int, world: int, total_s: float) -> float:
-    """Pairs/s of the whole job: every rank verifies pairs_per_step per step (weak scaling)."""
-    return pairs_per_step * steps * world / total_s
+def whole_job_value(pairs_all_ranks: int, steps: int, total_s: float) -> float:
+    """Pairs/s of the whole job: the ranks share every step's pairs (each verifies its own probe
+    ranges), so the job verifies pairs_all_ranks per step in the slowest rank's time."""
+    return pairs_all_ranks * steps / total_s
+
+
+def rank_share(batches, rank: int, world: int):
+    """This rank's part of every batch: a contiguous range of probes holding about 1/world of the
+    batch's candidates (the probe ranges of the ranks tile the batch, so every candidate is
+    verified by exactly one rank).  Offsets are rebased to the range."""
+    if world == 1:
+        return batches
+    out = []
+    for k, p, q, pr, co, ci in batches:
+        co64 = co.astype(np.int64)
+        cut = np.searchsorted(co64, np.linspace(0, co64[-1], world + 1), side="left")
+        cut[0], cut[-1] = 0, len(pr)
+        cut = np.maximum.accumulate(np.minimum(cut, len(pr)))
+        a, b = int(cut[rank]), int(cut[rank + 1])
+        out.append((k, p, q, pr[a:b], (co64[a:b + 1] - co64[a]).astype(np.uint64), ci[co64[a]:co64[b]]))
+    return out
+
+
+def common_config(cfg, batches, args):
+    """The config both arms report (same keys and values): the workload and its candidates."""
+    return dict(cfg, pairs_per_step=int(sum(len(b[5]) for b in batches)), instances_per_launch=len(batches),
+                similarity=args.sim,
+                candidates=("AllPairs prefix filter" + (" + PPJoin" if args.ppjoin else ""))
+                if args.workload != "tiny" else "all pairs")
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -381,8 +424,10 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     cfg, colls, inst = workload(args.workload)
-    batches = make_batches(colls, inst, all_pairs=args.workload == "tiny", ppjoin=args.ppjoin)
+    all_batches = make_batches(colls, inst, all_pairs=args.workload == "tiny", ppjoin=args.ppjoin)
+    batches = rank_share(all_batches, rank, world)
     pairs_step = sum(len(b[5]) for b in batches)
+    pairs_all = sum(len(b[5]) for b in all_batches)
     sim_flags = SIM << 8
 
     stream = torch.cuda.Stream(device=dev)
@@ -559,31 +604,35 @@ def run_ours(args, rank, world, local_rank):
     ssj.ssj_multi_destroy(ctx, multi)
     ssj.ssj_destroy(ctx)
 
+    # end-to-end times: the slowest rank's
+    e2e_t = max_over_ranks(e2e_t, world, dev)
+    e2e_single_t = max_over_ranks(e2e_single_t, world, dev)
+    e2e_direct_t = max_over_ranks(e2e_direct_t, world, dev)
     result = {"total_ms": total_ms, "step_ms": step_ms, "verify_ms": verify_ms, "plan_ms": plan_ms,
-              "launches": launches, "counts": result_counts, "pairs_step": pairs_step, "graph_ms": graph_ms,
-              "e2e_value": pairs_step * e2e_steps / e2e_t * world if e2e_t > 0 else None, "h2d": h2d, "d2h": d2h,
-              "e2e_single_value": pairs_step * e2e_steps / e2e_single_t * world if e2e_single_t > 0 else None,
-              "e2e_direct_value": pairs_step * e2e_steps / e2e_direct_t * world if e2e_direct_t > 0 else None,
-              "clocks": clocks.summary(), "cfg": cfg, "tune": tune, "warm_ms": warm_ms, "plain_ms": plain_ms,
+              "launches": launches, "counts": result_counts, "pairs_step": pairs_step, "pairs_all": pairs_all,
+              "graph_ms": graph_ms, "cfg": common_config(cfg, all_batches, args),
+              "e2e_value": pairs_all * e2e_steps / e2e_t if e2e_t > 0 else None, "h2d": h2d, "d2h": d2h,
+              "e2e_single_value": pairs_all * e2e_steps / e2e_single_t if e2e_single_t > 0 else None,
+              "e2e_direct_value": pairs_all * e2e_steps / e2e_direct_t if e2e_direct_t > 0 else None,
+              "clocks": clocks.summary(), "tune": tune, "warm_ms": warm_ms, "plain_ms": plain_ms,
               "l2_gbs": l2_gbs, "hbm_read_gbs": hbm_read_gbs}
     return result, colls, batches
 
 
-def run_serving(args):
+def measure_serving(requests: int, budgets=(4, 1), coprocess: bool = True, seed: int = 2024):
     """Continuous batching on a resident 1M-set collection: closed-loop peak, then open-loop
-    Poisson arrivals at 0.5x and 0.9x of that peak, for two device-memory budgets; and the
-    filter/verify co-process (Section 3.2) with chunks handed over as the CPU filter makes them."""
+    Poisson arrivals at 0.5x and 0.9x of that peak, for each device-memory budget M_c (GiB); and,
+    if coprocess, the filter/verify co-process (Section 3.2) with chunks handed over as the CPU
+    filter makes them."""
     import torch
     import synth
     import paper_1812_09141_gb300 as ssj
-    from paper_1812_09141_gb300 import _build
 
-    _build.build()
-    torch.cuda.set_device(0)
     c = synth.collection(synth.serving_collection())
     ts = [(7, 10), (4, 5), (9, 10)]
     threads = max(1, min(16, os.cpu_count() or 1))
     pools = []
+
     def pinned(a):
         t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         return t.numpy()
@@ -592,8 +641,8 @@ def run_serving(args):
     for p, q in ts:
         pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, p, q, n_threads=threads)
         pools.append((p, q, pinned(pr), co.astype(np.int64), pinned(ci)))
-    rng = np.random.default_rng(2024)
-    n_req = args.requests
+    rng = np.random.default_rng(seed)
+    n_req = requests
 
     def make_requests(arrivals, h):
         picks = []
@@ -626,8 +675,8 @@ def run_serving(args):
     out = {"workload": "serving", "collection": "1M sets, lognormal(12, 0.6) clip [2,200], Zipf(1.0) over 2e6",
            "requests": n_req, "request_sizes": "log-uniform [1e3, 1e7] pairs, slices of the CPU filter's "
            "candidates at t in {0.7, 0.8, 0.9}, in pinned host memory kept until collected (SSJ_KEEP_INPUTS)",
-           "runs": []}
-    for budget_gb in (4, 1):
+           "latency": "host clock from ssj_submit to the completion that ssj_poll reports", "runs": []}
+    for budget_gb in budgets:
         ctx = ssj.ssj_create(0, mem_budget_bytes=budget_gb << 30, max_inflight=8)
         try:
             h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
@@ -652,13 +701,22 @@ def run_serving(args):
                                             "p50_ms_small": 1e3 * float(np.percentile(lat[sizes2 < 1e5], 50)),
                                             "p99_ms_large": 1e3 * float(np.percentile(lat[sizes2 >= 1e6], 99)),
                                             "max_inflight": st["max_inflight"], "eagain": st["eagain"]}
-            if budget_gb == 4:
+            if coprocess and budget_gb == 4:
                 cp = ssj.ssj_serve_coprocess(ctx, h, c.offsets, c.tokens, 7, 10, threads, 1 << 20)
                 run["coprocess_t0.7"] = dict(cp, chunk_cands=1 << 20, filter_threads=threads)
             out["runs"].append(run)
         finally:
             ssj.ssj_destroy(ctx)
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def run_serving(args):
+    import torch
+    from paper_1812_09141_gb300 import _build
+
+    _build.build()
+    torch.cuda.set_device(0)
+    print(json.dumps(measure_serving(args.requests)), flush=True)
 
 
 def run_candgen(args):
@@ -723,13 +781,53 @@ def run_candgen(args):
     print(json.dumps(out), flush=True)
 
 
+def run_reference(args):
+    """The CPU oracle as it stands (single-threaded C) on this workload's candidates.  Each step
+    verifies a fixed bounded sample: every k-th probe of each batch (with all of its candidates),
+    k chosen so that the sample holds about REF_STEP_PAIRS candidates, or the whole step when it
+    is smaller; a uniform stride over probes, so the sample is not biased by the feeder's size
+    order."""
+    import oracle
+    cfg, colls, inst = workload(args.workload)
+    batches = make_batches(colls, inst, all_pairs=args.workload == "tiny", ppjoin=args.ppjoin)
+    pairs_step = sum(len(b[5]) for b in batches)
+    sample, stride = stride_sample(batches, REF_STEP_PAIRS)
+    sample_pairs = sum(len(x[5]) for x in sample)
+
+    def one_step():
+        for k, p, q, pr, co, ci in sample:
+            cR, cS, selfj = coll_pair(colls, k)
+            oracle.verify_batch(cR.offsets, cR.tokens, cS.offsets, cS.tokens, selfj, p, q, pr, co, ci, sim=SIM)
+    one_step()  # warm-up
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    dt = time.perf_counter() - t0
+    v = sample_pairs * args.steps / dt
+    whole = stride == 1
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "strong" if args.gpus > 1 else "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic", "config": common_config(cfg, batches, args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": (f"{args.steps} full steps of the workload ({pairs_step} pairs each)"
+                                        if whole else
+                                        f"{args.steps} steps of a fixed sample of {sample_pairs} of the "
+                                        f"{pairs_step} candidate pairs of a step: every {stride}-th probe of "
+                                        f"each of the {len(batches)} batches with all its candidates")
+                                       + ", after one warm-up step, one host thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="short_sets")
+    ap.add_argument("--workload", default="uneven_instances")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served-latency leg of the default workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="bytes written between timed steps to evict L2 (0 disables; only for profiling runs)")
@@ -762,79 +860,52 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cfg, colls, inst = workload(args.workload)
-        batches = make_batches(colls, inst, all_pairs=args.workload == "tiny", ppjoin=args.ppjoin)
-        import oracle
-        pairs_step = sum(len(b[5]) for b in batches)
-
-        # each step verifies a bounded sample: a probe-prefix slice of every batch, about
-        # REF_STEP_PAIRS candidates in all, split in proportion to the batches' sizes
-        sample = []
-        for k, p, q, pr, co, ci in batches:
-            co64 = co.astype(np.int64)
-            want = max(1000, REF_STEP_PAIRS * len(ci) // max(pairs_step, 1))
-            b = len(pr) if co64[-1] <= want else max(1, int(np.searchsorted(co64, want, side="right")) - 1)
-            sample.append((k, p, q, pr[:b], co64[:b + 1].astype(np.uint64), ci[:int(co64[b])]))
-        sample_pairs = sum(len(x[5]) for x in sample)
-
-        def one_step():
-            for k, p, q, pr, co, ci in sample:
-                cR, cS, selfj = coll_pair(colls, k)
-                oracle.verify_batch(cR.offsets, cR.tokens, cS.offsets, cS.tokens, selfj, p, q, pr, co, ci, sim=SIM)
-        one_step()  # warm-up
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            one_step()
-        dt = time.perf_counter() - t0
-        v = sample_pairs * args.steps / dt
-        whole = sample_pairs == pairs_step
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-                "data": "synthetic",
-                "config": dict(cfg, pairs_per_step=pairs_step, instances_per_launch=len(batches),
-                               similarity=args.sim,
-                               candidates="AllPairs prefix filter" + (" + PPJoin" if args.ppjoin else "")
-                               if args.workload != "tiny" else "all pairs"),
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": (f"{args.steps} full steps of the workload ({pairs_step} pairs each)"
-                                            if whole else
-                                            f"{args.steps} steps of a fixed sample of {sample_pairs} of the "
-                                            f"{pairs_step} candidate pairs of a step (a probe-prefix slice of each "
-                                            f"of the {len(batches)} batches)") + ", after one warm-up step"},
-                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
+        run_reference(args)
         return
 
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     res, colls, batches = run_ours(args, rank, world, local_rank)
+    served = None
+    if world == 1 and args.workload == "uneven_instances" and not args.no_serving:
+        # the served path on the resident 1M-set collection, in the same line
+        served = measure_serving(args.requests, budgets=(4,), coprocess=False)
     if rank != 0:
         return
     pairs_step = res["pairs_step"]
     total_s = res["total_ms"] / 1e3
     input_bytes = (sum(4 * len(c.tokens) + 8 * c.n for c in colls)
                    + sum(4 * len(b[3]) + 8 * len(b[4]) + 4 * len(b[5]) for b in batches))
-    value = whole_job_value(pairs_step, args.steps, world, total_s)
+    value = whole_job_value(res["pairs_all"], args.steps, total_s)
     peak, peak_kind = measured_hbm_peak()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": dict(res["cfg"], pairs_per_step=pairs_step, instances_per_launch=len(batches),
-                           similarity=args.sim, candidates="AllPairs prefix filter" + (" + PPJoin" if args.ppjoin else "")
-                           if args.workload != "tiny" else "all pairs",
-                           l2=(f"flushed before every timed step ({args.l2_flush_mb} MiB write)"
-                               if args.l2_flush_mb else "not flushed (profiling run)"),
-                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                           device_input_bytes=int(input_bytes), inputs_fit_l2=bool(input_bytes < 129e6))}
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": res["cfg"],
+            "l2_between_steps": (f"flushed before every timed step ({args.l2_flush_mb} MiB write)"
+                                 if args.l2_flush_mb else "not flushed (profiling run)"),
+            "parallelism": (f"{world} ranks, each a contiguous probe range of every batch" if world > 1
+                            else "single GPU"),
+            "device_input_bytes": int(input_bytes), "inputs_fit_l2": bool(input_bytes < 129e6)}
     sm = sorted(res["step_ms"])
     line["latency_ms"] = {"p50": float(np.percentile(sm, 50)), "p99": float(np.percentile(sm, 99)),
                           "per": "one batched launch (every instance of the step), device time"}
     gm = res["graph_ms"]
     line["graph_replay_ms_per_step"] = float(np.median(gm)) if gm else None
     line["gpu_launches"] = 2 * res["launches"]
-    line["config"]["granularity"] = res["tune"]
+    line["granularity"] = res["tune"]
+    if served is not None:
+        run = served["runs"][0]
+        line["served"] = {
+            "workload": "continuous batching on the resident 1,000,000-set collection (lognormal mean 12, "
+                        "Zipf 1.0 over 2e6 tokens), t in {0.7, 0.8, 0.9}",
+            "requests": served["requests"], "request_sizes": served["request_sizes"],
+            "latency": served["latency"], "mem_budget_gib": run["budget_gib"],
+            "closed_loop_pairs_per_s": run["closed_loop"]["pairs_per_s"],
+            "p50_ms_at_0.5x": run["open_loop_0.5"]["p50_ms"], "p99_ms_at_0.5x": run["open_loop_0.5"]["p99_ms"],
+            "p50_ms_at_0.9x": run["open_loop_0.9"]["p50_ms"], "p99_ms_at_0.9x": run["open_loop_0.9"]["p99_ms"],
+            "runs": served["runs"]}
     wm = sorted(res["warm_ms"])
     line["warm_l2"] = {"pairs_per_s": pairs_step / (np.median(wm) / 1e3), "p50_ms": float(np.percentile(wm, 50)),
                        "p99_ms": float(np.percentile(wm, 99)), "runs": len(wm)}

@@ -245,11 +245,14 @@ ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batch, ssj_trip
  * 800,000 candidates for small batches; split larger batches).  The caller
  * passes every input and output as device memory, as for
  * ssj_verify_batch_async (SSJ_DEVICE_PTRS is implied).
- * The first call on a device looks up the scratch block's device address
- * (once per device, with that device current); make that first call before
- * any stream capture.  All calls share the one block and it keeps the last
- * call's contents (the counters that must start at zero are cleared on
- * the stream by each call), so calls whose work overlaps on the GPU race:
+ * Every call looks up the scratch block's device address with the
+ * context's device current (so no address outlives a device reset); the
+ * first call on a device may also load the library's device code, so make
+ * that first call before any stream capture.  A NULL stream means the
+ * context's stream, as for ssj_verify_batch_async.  All calls share the
+ * one block and it keeps the last call's contents (the counters that must
+ * start at zero are cleared on the stream by each call), so calls whose
+ * work overlaps on the GPU race:
  * issue them on one stream, or wait for one before starting the next.
  * Device-side checks are read with ssj_device_error.
  */

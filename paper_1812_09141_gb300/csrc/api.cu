@@ -985,7 +985,7 @@ extern "C" ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uin
     }
     if (derr) {
         release();
-        return fail(ctx, SSJ_EDEVICE, "candidate generation: an output capacity was exceeded (code %u)", derr);
+        return fail(ctx, SSJ_EDEVICE, "candidate generation: an output capacity was exceeded or the candidate hash set was full (code %u)", derr);
     }
     const uint64_t packed = *ctx->h_count;
     const uint64_t groups = packed >> 40, total = packed & ((1ull << 40) - 1);
@@ -1573,7 +1573,7 @@ extern "C" ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double*
 namespace ssj {
 
 ssj_status resolve_device_batch(ssj_ctx* ctx, const ssj_batch* batch, VerifyArgs* a, int* device, int* num_sms,
-                                uint32_t* block_threads) {
+                                uint32_t* block_threads, cudaStream_t* ctx_stream) {
     Collection *R, *S;
     ssj_status st = resolve(ctx, batch, &R, &S);
     if (st != SSJ_OK) return st;
@@ -1587,6 +1587,7 @@ ssj_status resolve_device_batch(ssj_ctx* ctx, const ssj_batch* batch, VerifyArgs
     *device = ctx->device;
     *num_sms = ctx->num_sms;
     *block_threads = ctx->block_threads;
+    *ctx_stream = ctx->stream;
     return SSJ_OK;
 }
 

@@ -173,8 +173,10 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 
 // Insert key; true if it was not there.  The table has a power-of-two size
 // at least twice the number of keys ever inserted, so a free slot is always
-// found within the table.
-__device__ __forceinline__ bool hash_insert(unsigned long long* table, uint64_t mask, uint64_t key) {
+// found within the table.  Should the probe loop ever run through the whole
+// table (a sizing bug), the key cannot be stored: ERR_GUARD is set, so the
+// call fails with SSJ_EDEVICE instead of losing the candidate silently.
+__device__ __forceinline__ bool hash_insert(unsigned long long* table, uint64_t mask, uint64_t key, uint32_t* err) {
     uint64_t h = mix64(key) & mask;
     for (uint64_t probe = 0; probe <= mask; ++probe) {
         const unsigned long long prev = atomicCAS(table + h, (unsigned long long)kEmpty, (unsigned long long)key);
@@ -182,7 +184,8 @@ __device__ __forceinline__ bool hash_insert(unsigned long long* table, uint64_t 
         if (prev == key) return false;
         h = (h + 1) & mask;
     }
-    return false;  // unreachable with a table twice the keys
+    atomicOr(err, ERR_GUARD);
+    return false;
 }
 
 struct GenOut {
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(kGenWarps * 32) generate_kernel(Params P, cons
                 if (e < e1) {
                     const uint4 en = post[e];
                     if (entry_ok(P, en, rpos, L, min_size, a)) {
-                        fresh = hash_insert(table, mask, ((uint64_t)rpos << 32) | en.x);
+                        fresh = hash_insert(table, mask, ((uint64_t)rpos << 32) | en.x, O.err);
                         sid = en.w;
                     }
                 }

@@ -10,7 +10,6 @@
 // point instead uses the static scratch array below and never allocates.
 // The paper has no counterpart to this; it is an interface convenience.
 #include <cstdint>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -18,7 +17,7 @@
 
 namespace ssj {
 ssj_status resolve_device_batch(ssj_ctx* ctx, const ssj_batch* batch, VerifyArgs* a, int* device, int* num_sms,
-                                uint32_t* block_threads);
+                                uint32_t* block_threads, cudaStream_t* ctx_stream);
 ssj_status report(ssj_ctx* ctx, ssj_status st, const char* msg);
 void remember_counters(ssj_ctx* ctx, Counters* c);
 }  // namespace ssj
@@ -32,23 +31,16 @@ namespace {
 constexpr size_t kNoallocScratchBytes = 32ull << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-// Device address of g_noalloc_scratch per device.  In host code the array's
-// name only stands in for the symbol, so the address is looked up with
-// cudaGetSymbolAddress once per device, with that device current.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-cudaError_t scratch_address(int device, void** out) {
-    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[device] = p;
-    }
-    *out = g_scratch_addr[device];
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the array's name only stands in for the symbol, so the address is looked
+// up with cudaGetSymbolAddress, with the target device current.  The lookup
+// runs on every call (it costs far less than the launch) so that no address
+// outlives the context it belongs to, e.g. after a device reset.
+cudaError_t scratch_address(void** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -61,7 +53,8 @@ extern "C" ssj_status ssj_verify_batch_noalloc(ssj_ctx* ctx, const ssj_batch* ba
     VerifyArgs a;
     int device = 0, num_sms = 0;
     uint32_t block_threads = 0;
-    ssj_status st = resolve_device_batch(ctx, batch, &a, &device, &num_sms, &block_threads);
+    cudaStream_t ctx_stream = nullptr;
+    ssj_status st = resolve_device_batch(ctx, batch, &a, &device, &num_sms, &block_threads, &ctx_stream);
     if (st != SSJ_OK) return st;
     if (cap && !d_out && !(batch->flags & SSJ_COUNT_ONLY)) return report(ctx, SSJ_EINVAL, "NULL output");
     if (workspace_bytes(batch->n_probes, batch->n_cands, num_sms) > kNoallocScratchBytes)
@@ -72,7 +65,7 @@ extern "C" ssj_status ssj_verify_batch_noalloc(ssj_ctx* ctx, const ssj_batch* ba
     if (cudaGetDevice(&prev) != cudaSuccess) return report(ctx, SSJ_EDEVICE, "cudaGetDevice failed");
     if (prev != device && cudaSetDevice(device) != cudaSuccess) return report(ctx, SSJ_EDEVICE, "cudaSetDevice failed");
     void* scratch = nullptr;
-    cudaError_t e = scratch_address(device, &scratch);
+    cudaError_t e = scratch_address(&scratch);
     if (e == cudaSuccess) {
         a.single.out = d_out;
         a.single.cap = (batch->flags & SSJ_COUNT_ONLY) ? 0 : cap;
@@ -80,7 +73,10 @@ extern "C" ssj_status ssj_verify_batch_noalloc(ssj_ctx* ctx, const ssj_batch* ba
         bind_workspace(a, scratch, batch->n_probes, batch->n_cands, num_sms);
         remember_counters(ctx, a.ctr);
         // launch_verify clears the counters and the count before the kernels run
-        e = launch_verify(a, static_cast<cudaStream_t>(stream), num_sms, block_threads, nullptr);
+        // a NULL stream means the context's stream, as for ssj_verify_batch_async, so that
+        // ssj_device_error (which reads on the context's stream) sees this call's checks
+        const cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx_stream;
+        e = launch_verify(a, s, num_sms, block_threads, nullptr);
     }
     if (prev >= 0 && prev != device) cudaSetDevice(prev);
     if (e != cudaSuccess) return report(ctx, SSJ_EDEVICE, cudaGetErrorString(e));

@@ -151,6 +151,62 @@ def test_uneven_instances_scaled_match_oracle(ctx):
         ssj.ssj_unload_collection(ctx, h)
 
 
+def test_uneven_instances_full_size_match_oracle(ctx):
+    """The full batched workload: 256 uneven self-joins (n log-uniform 500..50,000, mean set size
+    log-uniform 5..500, Zipf s in [0.6, 1.2], t over 0.6..0.95; several hundred million candidates
+    in all) in one launch and in a CUDA-graph replay; every instance's sorted (r, s, overlap) list
+    equals the oracle's on the same feeder batch (the oracle split over probe ranges on every host
+    core)."""
+    import torch
+    dev = torch.device("cuda:0")
+    specs = synth.uneven_instances()
+    assert len(specs) == 256
+    handles, keep, dbs, outs, caps, wants = [], [], [], [], [], []
+    total = 0
+    for ins in specs:
+        c = synth.collection(ins.coll)
+        h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
+        handles.append(h)
+        b = synth.Batch(*ssj.feeder_all(c.offsets, c.tokens, ins.p, ins.q, n_threads=16))
+        total += b.n_cands
+        want = oracle.sort_triples(oracle.verify_batch_threads(c.offsets, c.tokens, c.offsets, c.tokens, True,
+                                                               ins.p, ins.q, b.probe_ids, b.cand_offsets,
+                                                               b.cand_ids))
+        wants.append(want)
+        t = _dev(b, dev)
+        keep.append(t)
+        dbs.append(ssj.DeviceBatch(h, h, ins.p, ins.q, *t, b.n_cands, n_probes=b.n_probes))
+        cap = len(want) + 1024
+        outs.append(torch.zeros(3 * cap, dtype=torch.int32, device=dev))
+        caps.append(cap)
+    assert total > 300_000_000
+    assert sum(len(w) for w in wants) > 0
+    counts = torch.zeros(len(specs), dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    m = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
+    try:
+        for rep in range(2):
+            for o in outs:
+                o.zero_()
+            counts.zero_()
+            torch.cuda.synchronize()
+            if rep == 0:
+                ssj.ssj_multi_launch(ctx, m)
+            else:
+                ssj.ssj_multi_graph_launch(ctx, m)
+            torch.cuda.synchronize()
+            assert ssj.ssj_device_error(ctx) == 0
+            n = counts.cpu().numpy()
+            for i, (o, w) in enumerate(zip(outs, wants)):
+                assert int(n[i]) == len(w), (rep, i, int(n[i]), len(w))
+                got = oracle.sort_triples(o[:3 * int(n[i])].view(-1, 3).cpu().numpy().astype(np.uint32))
+                assert np.array_equal(got, w), (rep, i)
+    finally:
+        ssj.ssj_multi_destroy(ctx, m)
+        for h in handles:
+            ssj.ssj_unload_collection(ctx, h)
+
+
 def test_multi_keeps_collections_loaded(ctx):
     import torch
     c = synth.collection(synth.tiny_self_join(n=100))

@@ -388,29 +388,38 @@ def test_full_short_sets_all_thresholds(ctx):
     ssj.ssj_unload_collection(ctx, h)
 
 
-def test_full_long_sets_sampled(ctx):
-    """50,000 long sets at t = 3/5 (about 1e8 candidates): every reported triple is re-verified by
-    the oracle, and a uniform sample of candidate pairs is checked for membership."""
+def _exact_against_threaded_oracle(ctx, c, h, p, q, b, flags=0):
+    """GPU triples of one batch against the oracle's over the same batch (split over probe ranges
+    on every host core), element by element; returns the oracle's sorted triples."""
+    want = oracle.sort_triples(oracle.verify_batch_threads(c.offsets, c.tokens, c.offsets, c.tokens, True, p, q,
+                                                           b.probe_ids, b.cand_offsets, b.cand_ids))
+    got = gpu(ctx, h, h, p, q, b, flags)
+    assert np.array_equal(got, want), (flags, len(got), len(want))
+    n = ssj.ssj_verify_batch(ctx, h, h, p, q, b.probe_ids, b.cand_offsets, b.cand_ids,
+                             flags=flags | ssj.SSJ_COUNT_ONLY)
+    assert n == len(want)
+    return want
+
+
+def test_full_long_sets_exact(ctx):
+    """50,000 long sets at t = 3/5 (about 9.2e7 candidates): the sorted (r, s, overlap) list of the
+    whole batch equals the oracle's, element by element.  The positional filter rejects every
+    candidate of this collection, so the same collection with 20% of its sets replaced by edited
+    copies (40 tokens changed) is checked the same way: there several hundred candidates pass,
+    with overlaps from about 100 to about 800."""
     c = synth.collection(synth.long_sets())
     h = load(ctx, c, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
-    b = feeder_batch(c, 3, 5)
-    got = gpu(ctx, h, h, 3, 5, b)
-    n = ssj.ssj_verify_batch(ctx, h, h, 3, 5, b.probe_ids, b.cand_offsets, b.cand_ids, flags=ssj.SSJ_COUNT_ONLY)
-    assert n == len(got)
-    assert len(np.unique(got[:, :2], axis=0)) == len(got)
-    rng = np.random.default_rng(0)
-    idx = rng.choice(len(got), size=min(len(got), 20_000), replace=False) if len(got) else []
-    for r, s, o in got[idx]:
-        ok, oo, _, _ = oracle.verify_pair(c.set(r), c.set(s), 3, 5, early=False)
-        assert ok and oo == o
-    # membership of a uniform sample of candidates
-    pair_probe = np.repeat(b.probe_ids, np.diff(b.cand_offsets.astype(np.int64)))
-    pick = rng.choice(b.n_cands, size=50_000, replace=False)
-    keys = set(map(tuple, got[:, :2].tolist()))
-    for m in pick:
-        r, s = int(pair_probe[m]), int(b.cand_ids[m])
-        ok, _, _, _ = oracle.verify_pair(c.set(r), c.set(s), 3, 5)
-        assert ok == ((min(r, s), max(r, s)) in keys)
+    b = feeder_batch(c, 3, 5, threads=16)
+    assert b.n_cands > 50_000_000
+    _exact_against_threaded_oracle(ctx, c, h, 3, 5, b)
+    ssj.ssj_unload_collection(ctx, h)
+    spec = synth.long_sets()
+    spec.plant_frac, spec.plant_edits = 0.2, 40
+    c = synth.collection(spec)
+    h = load(ctx, c, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ)
+    b = feeder_batch(c, 3, 5, threads=16)
+    want = _exact_against_threaded_oracle(ctx, c, h, 3, 5, b)
+    assert len(want) > 500
     ssj.ssj_unload_collection(ctx, h)
 
 

@@ -4,8 +4,10 @@ Some callers cannot let a library allocate device memory during a call (their
 memory all goes through an arena or a caching allocator, or cudaMalloc's
 device synchronisation is unacceptable on their path).  This file checks that
 the variant serving them returns exactly what the allocating entry point
-returns, on two calls in a row that reuse the same static scratch block.  It
-is named to be collected last and works alone in a fresh process too.
+returns, on two calls in a row that reuse the same static scratch block, on
+an explicit stream and on the context's own stream (stream NULL), and that
+those calls leave the device's free memory unchanged.  It is named to be
+collected last and works alone in a fresh process too.
 """
 import numpy as np
 import pytest
@@ -26,6 +28,11 @@ def _device_batch(b, dev):
     return pr, co, ci
 
 
+def _triples(out, n):
+    return ssj.triples_to_array(np.frombuffer(out[:3 * n].cpu().numpy().astype(np.uint32).tobytes(),
+                                              dtype=ssj.TRIPLE_DTYPE))
+
+
 def test_noalloc_matches_allocating_entry_point_on_two_calls():
     import torch
     assert torch.cuda.is_available()
@@ -44,6 +51,7 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls():
         pr, co, ci = ssj.feeder_all(c2.offsets, c2.tokens, 3, 5, n_threads=4)
         cases = [(h1, (1, 2), synth.all_pairs_batch(c1.n)), (h2, (3, 5), synth.Batch(pr, co, ci))]
         stream = torch.cuda.Stream()
+        prepared = []
         for h, (p, q), b in cases:
             want = ssj.triples_to_array(ssj.ssj_verify_batch(ctx, h, h, p, q, b.probe_ids, b.cand_offsets,
                                                              b.cand_ids))
@@ -52,16 +60,34 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls():
             cap = len(want) + 16
             out = torch.zeros(cap * 3, dtype=torch.int32, device=dev)
             cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-            torch.cuda.synchronize()
-            with torch.cuda.stream(stream):
-                ssj.ssj_verify_batch_noalloc(ctx, h, h, p, q, t_pr, t_co, t_ci, b.n_cands, out, cap, cnt,
-                                             stream=stream.cuda_stream)
-            stream.synchronize()
-            n = int(cnt.item())
-            got = ssj.triples_to_array(np.frombuffer(out[:3 * n].cpu().numpy().astype(np.uint32).tobytes(),
-                                                     dtype=ssj.TRIPLE_DTYPE))
-            assert np.array_equal(got, want)
-            assert ssj.ssj_device_error(ctx) == 0
+            prepared.append((h, p, q, b, want, t_pr, t_co, t_ci, cap, out, cnt))
+        # the first call on the device may load the library's device code (and with it
+        # the static scratch block); the free-memory check starts after it
+        h, p, q, b, want, t_pr, t_co, t_ci, cap, out, cnt = prepared[0]
+        ssj.ssj_verify_batch_noalloc(ctx, h, h, p, q, t_pr, t_co, t_ci, b.n_cands, out, cap, cnt)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info(dev)
+        for use_ctx_stream in (False, True):
+            for h, p, q, b, want, t_pr, t_co, t_ci, cap, out, cnt in prepared:
+                out.zero_()
+                cnt.zero_()
+                torch.cuda.synchronize()
+                if use_ctx_stream:
+                    # stream NULL: the context's own stream, which ssj_device_error reads on
+                    ssj.ssj_verify_batch_noalloc(ctx, h, h, p, q, t_pr, t_co, t_ci, b.n_cands, out, cap, cnt)
+                    assert ssj.ssj_device_error(ctx) == 0
+                    torch.cuda.synchronize()
+                else:
+                    with torch.cuda.stream(stream):
+                        ssj.ssj_verify_batch_noalloc(ctx, h, h, p, q, t_pr, t_co, t_ci, b.n_cands, out, cap, cnt,
+                                                     stream=stream.cuda_stream)
+                    stream.synchronize()
+                    assert ssj.ssj_device_error(ctx) == 0
+                n = int(cnt.item())
+                assert np.array_equal(_triples(out, n), want)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info(dev)
+        assert free1 == free0, f"device free memory changed by {free0 - free1} bytes across the calls"
         # a batch whose work queue exceeds the static block is refused before any launch
         t_pr, t_co, t_ci = _device_batch(cases[0][2], dev)
         with pytest.raises(ssj.SsjError) as ei:
