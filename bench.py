@@ -61,6 +61,7 @@ SIM = 0                   # similarity function of every instance (0 Jaccard, 1 
 SIM_NAMES = {"jaccard": 0, "dice": 1, "cosine": 2, "overlap": 3}
 OVERLAP_THRESHOLDS = [(6, 1), (8, 1), (10, 1), (12, 1)]
 REF_STEP_PAIRS = 3_000_000  # candidates per step of the reference (CPU oracle) arm
+INSTANCES = 0               # uneven_instances: 0 = all 256 (--instances, for profiling runs only)
 UNIT = "pairs/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
@@ -73,9 +74,12 @@ def workload(name: str):
     import synth
     if name == "uneven_instances":
         specs = synth.uneven_instances()
+        if INSTANCES:
+            specs = specs[:INSTANCES]  # profiling runs: the first instances only
         colls = [synth.collection(ins.coll) for ins in specs]
         inst = [(i, ins.p, ins.q) for i, ins in enumerate(specs)]
-        cfg = {"workload": name, "description": "256 independent self-joins in one launch: n log-uniform "
+        cfg = {"workload": name if not INSTANCES else f"{name}[:{INSTANCES}]",
+               "description": f"{len(specs)} independent self-joins in one launch: n log-uniform "
                "[500, 50000], mean set size log-uniform [5, 500] (sigma 0.6, clip [2, min(4 mean, 2000)]), "
                "Zipf s uniform [0.6, 1.2] over 1e5 tokens, t uniform over {0.6, ..., 0.95}",
                "instances": len(inst), "n_sets": int(sum(c.n for c in colls)),
@@ -459,11 +463,13 @@ def run_ours(args, rank, world, local_rank):
         g = [int(x) for x in args.granularity.split(",")]
         t, l, w, b = g[:4]
         d = g[4] if len(g) > 4 else 0
+        ix = g[5] if len(g) > 5 else 0
         ssj.ssj_set_granularity(ctx, t, l, w, b)
         ssj.ssj_set_short_pairs(ctx, d)
+        ssj.ssj_set_index_items(ctx, ix)
         multi = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
         tune = {"thread_max_key": t, "lane_max_key": l, "warp_max_key": w, "block_threads": b,
-                "drain_min_live": d, "chosen_by": "--granularity"}
+                "drain_min_live": d, "index_min_cands": ix, "chosen_by": "--granularity"}
     else:
         multi = ssj.ssj_multi_create(ctx, dbs, outs, caps, counts)
         # granularity and block size chosen by the library's autotuner on this launch (untimed)
@@ -472,6 +478,7 @@ def run_ours(args, rank, world, local_rank):
         ssj.ssj_set_granularity(ctx, tune["thread_max_key"], tune["lane_max_key"],
                                 min(tune["warp_max_key"], 1 << 30), tune["block_threads"])
         ssj.ssj_set_short_pairs(ctx, tune["drain_min_live"])
+        ssj.ssj_set_index_items(ctx, tune["index_min_cands"])
 
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -837,11 +844,14 @@ def main():
     ap.add_argument("--sim", default="jaccard", choices=sorted(SIM_NAMES),
                     help="similarity function of every instance (overlap uses thresholds 6, 8, 10, 12)")
     ap.add_argument("--ppjoin", action="store_true", help="PPJoin positional filter in the CPU feeder")
-    ap.add_argument("--granularity", default="", help="thread,lane,warp,block_threads[,drain_min_live]: fixed setting instead of "
-                    "the autotuner's (profiling runs)")
+    ap.add_argument("--granularity", default="", help="thread,lane,warp,block_threads[,drain_min_live[,index_min_cands]]: "
+                    "fixed setting instead of the autotuner's (profiling runs)")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="uneven_instances: verify only the first N instances (profiling runs on a smaller case)")
     args = ap.parse_args()
-    global SIM
+    global SIM, INSTANCES
     SIM = SIM_NAMES[args.sim]
+    INSTANCES = args.instances
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
 

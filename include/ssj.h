@@ -100,9 +100,15 @@ const char* ssj_last_error(ssj_ctx* ctx);
                                       device layout is.  Self-joins only: a batch whose R
                                       and S differ rejects renumbered collections. */
 #define SSJ_VALIDATE 0x2u          /* check that every set is strictly increasing */
-#define SSJ_PIN_L2 0x4u            /* keep the token array L2-resident through an access
-                                      policy window on the library's streams when it fits
-                                      the persisting L2 set-aside of this context */
+#define SSJ_PIN_L2 0x4u            /* keep the token array L2-resident (Section 3.3.1: the
+                                      collection is copied once and read by every batch):
+                                      the context's persisting-L2 set-aside is raised to
+                                      the array's size (up to the device's maximum; a limit
+                                      of this context only, restored when the last pinned
+                                      collection is unloaded) and every verification launch
+                                      that reads the collection carries a persisting
+                                      access-policy window over it (for a launch over
+                                      several collections: the first pinned one) */
 
 /* Load a collection of n_sets sets.  offsets (n_sets+1 entries, host) are
  * nondecreasing with offsets[0] = 0; set i is tokens[offsets[i] ..
@@ -142,6 +148,11 @@ ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, ui
 #define SSJ_FORCE_LANE 0x80u    /* verify every pair with one lane, the probe set held in the
                                    warp's shared memory (Alternative B); probes longer than
                                    1,020 tokens go to the warp path */
+#define SSJ_FORCE_INDEX 0x2000u /* verify every pair with one thread against the probe set held
+                                   as a bitmap over the token values in the thread block's
+                                   shared memory (index items, see ssj_set_index_items); where
+                                   the collections' token values reach 786,432 or more, the
+                                   lane path instead */
 
 /* Similarity function (Table "Similarity Functions", Section 2.2.2), in the
  * flags' bits 8-9; t = p/q.  Each pair is kept iff its overlap o reaches the
@@ -365,12 +376,14 @@ typedef struct {
     uint32_t lane_max_key;    /*   for warp_max_key sends no probe to the block bin, */
     uint32_t warp_max_key;    /*   lane_max_key <= thread_max_key means no lane bin */
     uint32_t block_threads;   /* chosen block size (the block path's window is 8 steps per thread),
-                                 | SSJ_WIDE_REGISTERS for the wide-register variant */
+                                 | SSJ_WIDE_REGISTERS for the wide-register variant,
+                                 | SSJ_BULK_STAGING for bulk-copy staging */
     uint32_t drain_min_live;  /* short pairs still merging that keep a warp on them before the rest
                                  are parked again and lanes refilled (8 .. 24) */
     uint32_t settings_tried;  /* distinct settings timed */
     float best_ms;            /* median device time of one launch with the chosen setting */
     float initial_ms;         /* the same for the setting m had before the call */
+    uint32_t index_min_cands; /* chosen index-item threshold (0: no index items) */
 } ssj_tune_result;
 
 /*
@@ -379,6 +392,7 @@ typedef struct {
  * launches after one untimed launch each) settings of the thread, lane and
  * warp bins' upper keys, of the block size and of the short-pair refill
  * threshold (drain_min_live), by coordinate descent
+ * and of the index-item threshold (ssj_set_index_items)
  * from m's current setting, and keep the fastest in m (later launches, and
  * graphs captured later, use it).  Every setting computes the same results
  * (Section 3.3.2 Alternatives A-C differ in speed only, Section 5.4); the
@@ -460,11 +474,32 @@ ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double* plan_ms, d
  * lane_max_key <= thread_max_key leaves the lane bin empty.
  * block_threads is 128, 256 or 512 (default 256), optionally
  * | SSJ_WIDE_REGISTERS for the verify kernel compiled for three quarters of
- * the CTAs per SM (more registers per thread, fewer spills).  Zero leaves a
- * value unchanged. */
+ * the CTAs per SM (more registers per thread, fewer spills) and
+ * | SSJ_BULK_STAGING (below).  Zero leaves a value unchanged. */
 ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t lane_max_key, uint32_t warp_max_key,
                                uint32_t block_threads);
 #define SSJ_WIDE_REGISTERS 0x10000u
+/* block_threads flag: thread-block and warp items stage their sets in shared
+ * memory by one-dimensional bulk copies on the copy engine (cp.async.bulk,
+ * completion counted on an mbarrier) instead of 16-byte loads by every
+ * thread: the probe set once per item; for thread-block items each
+ * candidate's whole set (when it fits the window buffer) while the previous
+ * candidate merges; for warp items each merge window of the candidate. */
+#define SSJ_BULK_STAGING 0x20000u
+
+/* Index items of later launches of the context (prepared launches take the
+ * value at ssj_multi_create; ssj_multi_autotune tunes it per launch): a probe
+ * with at least min_cands candidates is verified by a whole thread block
+ * that holds the probe set r as a bitmap over the token values in shared
+ * memory (one bit per value: the launch's token values must stay below
+ * 786,432, which frequency renumbering gives for vocabularies of that size;
+ * otherwise the probe keeps its other granularity).  Every thread then
+ * merges one candidate s at a time from s's side, each token of s tested
+ * against r by one bit lookup, with the positional bound on s's remainder
+ * after every 16-byte block (Sections 2.2.3, 3.1; r's tokens are read once
+ * per probe instead of once per pair).  0 turns index items off; the
+ * default is 256.  Every value computes the same results. */
+ssj_status ssj_set_index_items(ssj_ctx* ctx, uint32_t min_cands);
 
 /* Short-pair refill threshold of later launches of the context (prepared
  * launches take it at ssj_multi_create; ssj_multi_autotune tunes it per

@@ -38,6 +38,7 @@ SSJ_FORCE_THREAD = 0x10
 SSJ_FORCE_WARP = 0x20
 SSJ_FORCE_BLOCK = 0x40
 SSJ_FORCE_LANE = 0x80
+SSJ_FORCE_INDEX = 0x2000
 SSJ_SIM_JACCARD = 0x000
 SSJ_SIM_DICE = 0x100
 SSJ_SIM_COSINE = 0x200
@@ -48,6 +49,7 @@ SSJ_JOIN_POSITIONAL = 0x400
 SSJ_KEEP_INPUTS = 0x800
 SSJ_HOST_DIRECT = 0x1000
 SSJ_WIDE_REGISTERS = 0x10000
+SSJ_BULK_STAGING = 0x20000
 # context flags
 SSJ_CTX_PROFILE = 0x1
 
@@ -80,7 +82,8 @@ class ssj_tune_result(ctypes.Structure):
     _fields_ = [("thread_max_key", ctypes.c_uint32), ("lane_max_key", ctypes.c_uint32), ("warp_max_key", ctypes.c_uint32),
                 ("block_threads", ctypes.c_uint32), ("drain_min_live", ctypes.c_uint32),
                 ("settings_tried", ctypes.c_uint32),
-                ("best_ms", ctypes.c_float), ("initial_ms", ctypes.c_float)]
+                ("best_ms", ctypes.c_float), ("initial_ms", ctypes.c_float),
+                ("index_min_cands", ctypes.c_uint32)]
 
 
 class ssj_feeder_opts(ctypes.Structure):
@@ -138,6 +141,7 @@ SIGNATURES = {
     "ssj_results": (_INT, [_VP, _U64, _VP, _U64, _P(_U64)]),
     "ssj_set_granularity": (_INT, [_VP, _U32, _U32, _U32, _U32]),
     "ssj_set_short_pairs": (_INT, [_VP, _U32]),
+    "ssj_set_index_items": (_INT, [_VP, _U32]),
     "ssj_profile_read": (_INT, [_VP, _P(_U32), _P(ctypes.c_double), _P(ctypes.c_double)]),
     "ssj_serve_replay": (_INT, [_VP, _P(ssj_request), _U32, _P(ctypes.c_double), _P(ssj_serve_stats)]),
     "ssj_serve_coprocess": (_INT, [_VP, _U32, _VP, _VP, _U32, _U32, _U32, _U32, _U64, _P(ssj_coprocess_stats)]),
@@ -392,7 +396,7 @@ def ssj_multi_autotune(ctx: int, m: int, stream: int | None = None, reps: int = 
     _check(ctx, lib().ssj_multi_autotune(ctx, m, stream, reps, ctypes.byref(r)))
     return {"thread_max_key": r.thread_max_key, "lane_max_key": r.lane_max_key, "warp_max_key": r.warp_max_key,
             "block_threads": r.block_threads, "drain_min_live": r.drain_min_live,
-            "settings_tried": r.settings_tried,
+            "index_min_cands": r.index_min_cands, "settings_tried": r.settings_tried,
             "best_ms": r.best_ms, "initial_ms": r.initial_ms}
 
 
@@ -450,6 +454,11 @@ def ssj_results(ctx: int, ticket: int, count_only: bool = False):
 def ssj_set_granularity(ctx: int, thread_max_key: int = 0, lane_max_key: int = 0, warp_max_key: int = 0,
                         block_threads: int = 0) -> None:
     _check(ctx, lib().ssj_set_granularity(ctx, thread_max_key, lane_max_key, warp_max_key, block_threads))
+
+
+def ssj_set_index_items(ctx: int, min_cands: int) -> None:
+    """Probes with at least min_cands candidates become index items (0: none)."""
+    _check(ctx, lib().ssj_set_index_items(ctx, min_cands))
 
 
 def ssj_set_short_pairs(ctx: int, drain_min_live: int = 0) -> None:

@@ -57,6 +57,9 @@ struct NvtxScope {
 
 namespace {
 
+// Default of the context's index-item threshold (ssj_set_index_items).
+constexpr uint32_t kIndexMinCandsDefault = 256;
+
 struct Collection {
     uint32_t n_sets = 0;
     uint64_t n_tokens = 0;
@@ -67,6 +70,8 @@ struct Collection {
     uint32_t max_len = 0;        // longest set
     uint32_t vocab = 0;          // largest token on the device + 1
     uint32_t busy = 0;           // submitted batches not yet collected
+    size_t l2_window = 0;        // SSJ_PIN_L2: bytes of the token array kept in the persisting L2 set-aside
+    float l2_hit_ratio = 0.f;    // share of the window the set-aside holds
     DevColl dev() const {
         DevColl d;
         d.toks4 = reinterpret_cast<const uint4*>(d_toks);
@@ -130,6 +135,12 @@ struct ssj_ctx {
     uint32_t lane_max_key = 2048;
     uint32_t warp_max_key = 2048;
     uint32_t block_threads = 256;
+    uint32_t index_min_cands = kIndexMinCandsDefault;  // probes with this many candidates become index items
+    // SSJ_PIN_L2: the context's persisting-L2 set-aside as found (restored when the last pinned
+    // collection is unloaded), whether the library raised it, and the pinned collections
+    size_t l2_limit_found = 0;
+    bool l2_limit_raised = false;
+    uint32_t n_pinned = 0;
     std::string err;
 
     std::map<ssj_coll, Collection> colls;
@@ -294,10 +305,11 @@ ssj_status resolve(ssj_ctx* ctx, const ssj_batch* b, Collection** R, Collection*
     if (b->R != b->S && (ir->second.renumbered || is->second.renumbered))
         return fail(ctx, SSJ_EINVAL, "renumbered collections can only be self-joined");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_EMIT_ALL | SSJ_FORCE_THREAD |
-                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_SIM_MASK | SSJ_KEEP_INPUTS |
-                           SSJ_HOST_DIRECT;
+                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_FORCE_INDEX | SSJ_SIM_MASK |
+                           SSJ_KEEP_INPUTS | SSJ_HOST_DIRECT;
     if (b->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown batch flag");
-    const uint32_t forced = b->flags & (SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE);
+    const uint32_t forced =
+        b->flags & (SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_FORCE_INDEX);
     if (forced & (forced - 1)) return fail(ctx, SSJ_EINVAL, "at most one SSJ_FORCE_* flag");
     *R = &ir->second;
     *S = &is->second;
@@ -312,6 +324,7 @@ uint32_t vflags(uint32_t f) {
     if (f & SSJ_FORCE_WARP) v |= VF_FORCE_WARP;
     if (f & SSJ_FORCE_BLOCK) v |= VF_FORCE_BLOCK;
     if (f & SSJ_FORCE_LANE) v |= VF_FORCE_LANE;
+    if (f & SSJ_FORCE_INDEX) v |= VF_FORCE_INDEX;
     return v;
 }
 
@@ -343,15 +356,36 @@ Instance make_instance(const ssj_batch* b, const Collection& R, const Collection
     return I;
 }
 
+// The context's granularity policy for a launch whose collections' token
+// values are all below vocab_bound; the probe bitmap of index items is sized
+// when index items are on or a batch forces them (and the values fit).
+void apply_policy(const ssj_ctx* ctx, VerifyArgs& a, uint64_t vocab_bound, bool force_index) {
+    a.thread_max_key = ctx->thread_max_key;
+    a.drain_min_live = ctx->drain_min_live;
+    a.lane_max_key = ctx->lane_max_key;
+    a.warp_max_key = ctx->warp_max_key;
+    a.index_min_cands = ctx->index_min_cands;
+    a.index_words = (ctx->index_min_cands || force_index) ? index_words_for(vocab_bound) : 0u;
+}
+
+// The persisting-L2 window of a pinned collection on the launch (none if c is not pinned).
+void set_l2_window(VerifyArgs& a, const Collection& c) {
+    a.l2_base = c.l2_window ? c.d_toks : nullptr;
+    a.l2_bytes = c.l2_window;
+    a.l2_hit_ratio = c.l2_hit_ratio;
+}
+
+uint64_t vocab_bound(const Collection& R, const Collection& S) {
+    return std::max<uint64_t>(std::max<uint64_t>(R.vocab, S.vocab), 1);
+}
+
 VerifyArgs make_args(ssj_ctx* ctx, const ssj_batch* b, const Collection& R, const Collection& S, uint64_t n_cands) {
     VerifyArgs a;
     memset(&a, 0, sizeof(a));
     a.single = make_instance(b, R, S, n_cands);
     a.table = nullptr;
-    a.thread_max_key = ctx->thread_max_key;
-    a.drain_min_live = ctx->drain_min_live;
-    a.lane_max_key = ctx->lane_max_key;
-    a.warp_max_key = ctx->warp_max_key;
+    apply_policy(ctx, a, vocab_bound(R, S), (b->flags & SSJ_FORCE_INDEX) != 0);
+    set_l2_window(a, R.l2_window ? R : S);
     return a;
 }
 
@@ -425,6 +459,16 @@ extern "C" ssj_status ssj_create(const ssj_config* config, ssj_ctx** out) {
     return SSJ_OK;
 }
 
+// The persisting-L2 set-aside back to what the context had before SSJ_PIN_L2
+// raised it, with the persisting lines released.
+void release_l2(ssj_ctx* ctx) {
+    if (!ctx->l2_limit_raised) return;
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, ctx->l2_limit_found);
+    cudaGetLastError();
+    ctx->l2_limit_raised = false;
+}
+
 extern "C" void ssj_destroy(ssj_ctx* ctx) {
     if (!ctx) return;
     {
@@ -453,6 +497,7 @@ extern "C" void ssj_destroy(ssj_ctx* ctx) {
             cudaFreeAsync(kv.second->d_mem, kv.second->stream);
             cudaStreamSynchronize(kv.second->stream);
         }
+    if (ctx->n_pinned) release_l2(ctx);
     for (auto& kv : ctx->colls) {
         cudaFree(kv.second.d_toks);
         cudaFree(kv.second.d_desc);
@@ -476,13 +521,20 @@ extern "C" const char* ssj_last_error(ssj_ctx* ctx) {
 extern "C" ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t lane_max_key,
                                           uint32_t warp_max_key, uint32_t block_threads) {
     if (!ctx) return SSJ_EINVAL;
-    const uint32_t bt = block_threads & ~SSJ_WIDE_REGISTERS;
+    const uint32_t bt = block_threads & ~(SSJ_WIDE_REGISTERS | SSJ_BULK_STAGING);
     if (block_threads && bt != 128 && bt != 256 && bt != 512)
-        return fail(ctx, SSJ_EINVAL, "block_threads must be 128, 256 or 512 (optionally | SSJ_WIDE_REGISTERS)");
+        return fail(ctx, SSJ_EINVAL,
+                    "block_threads must be 128, 256 or 512 (optionally | SSJ_WIDE_REGISTERS | SSJ_BULK_STAGING)");
     if (thread_max_key) ctx->thread_max_key = thread_max_key;
     if (lane_max_key) ctx->lane_max_key = lane_max_key;
     if (warp_max_key) ctx->warp_max_key = warp_max_key;
     if (block_threads) ctx->block_threads = block_threads;
+    return SSJ_OK;
+}
+
+extern "C" ssj_status ssj_set_index_items(ssj_ctx* ctx, uint32_t min_cands) {
+    if (!ctx) return SSJ_EINVAL;
+    ctx->index_min_cands = min_cands;
     return SSJ_OK;
 }
 
@@ -582,22 +634,29 @@ extern "C" ssj_status ssj_load_collection(ssj_ctx* ctx, const uint64_t* offsets,
         return cuda_fail(ctx, e, "layout_scatter");
     }
     if (flags & SSJ_PIN_L2) {
-        // Persisting-L2 window over the token array on the library's streams.  The set-aside is a
-        // per-context limit; it is left as the context found it when the window does not fit.
+        // Persisting-L2 window over the token array, attached to every verify launch that reads
+        // this collection.  The context's persisting set-aside (a limit of this context only, gone
+        // with it) is raised to the array's size, up to the device's maximum, and restored when
+        // the last pinned collection is unloaded.
+        int max_persist = 0, max_window = 0;
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, ctx->device);
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device);
         size_t setaside = 0;
         cudaDeviceGetLimit(&setaside, cudaLimitPersistingL2CacheSize);
         const size_t bytes = 16 * c.n_chunks;
-        if (setaside > 0 && bytes > 0) {
-            cudaStreamAttrValue v;
-            memset(&v, 0, sizeof(v));
-            v.accessPolicyWindow.base_ptr = c.d_toks;
-            v.accessPolicyWindow.num_bytes = std::min(bytes, setaside);
-            v.accessPolicyWindow.hitRatio = 1.0f;
-            v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-            v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-            cudaStreamSetAttribute(ctx->stream, cudaStreamAttributeAccessPolicyWindow, &v);
-            for (auto& s : ctx->slots) cudaStreamSetAttribute(s.stream, cudaStreamAttributeAccessPolicyWindow, &v);
+        const size_t want = std::min(bytes, (size_t)std::max(max_persist, 0));
+        if (setaside < want) {
+            if (!ctx->l2_limit_raised) ctx->l2_limit_found = setaside;
+            if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) {
+                ctx->l2_limit_raised = true;
+                setaside = want;
+            }
+            cudaGetLastError();  // a refused limit leaves the window smaller, not an error
         }
+        c.l2_window = std::min(bytes, (size_t)std::max(max_window, 0));
+        if (setaside == 0) c.l2_window = 0;
+        c.l2_hit_ratio = c.l2_window ? std::min(1.0f, (float)((double)setaside / (double)c.l2_window)) : 0.f;
+        if (c.l2_window) ctx->n_pinned++;
     }
     const ssj_coll h = ctx->next_coll++;
     ctx->colls[h] = c;
@@ -615,6 +674,7 @@ extern "C" ssj_status ssj_unload_collection(ssj_ctx* ctx, ssj_coll coll) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(it->second.d_toks);
     cudaFree(it->second.d_desc);
+    if (it->second.l2_window && --ctx->n_pinned == 0) release_l2(ctx);
     ctx->colls.erase(it);
     return SSJ_OK;
 }
@@ -784,6 +844,9 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
     sh.total_probes = 0;
     sh.total_cands = 0;
     size_t off = align256(sizeof(uint64_t) * n_batches);  // counts first
+    uint64_t launch_vocab = 1;
+    bool launch_force_index = false;
+    const Collection* pinned = nullptr;  // the first pinned collection: its L2 window
     for (uint32_t i = 0; i < n_batches; ++i) {
         const ssj_batch* b = &batches[i];
         if (b->flags & SSJ_DEVICE_PTRS) return fail(ctx, SSJ_EINVAL, "batch %u: host pointers expected", i);
@@ -794,6 +857,9 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
         if (st != SSJ_OK) return st;
         if (caps[i] && !outs[i] && !(b->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "batch %u: NULL output", i);
         table[i] = make_instance(b, *R, *S, n_cands[i]);
+        if (!pinned) pinned = R->l2_window ? R : (S->l2_window ? S : nullptr);
+        launch_vocab = std::max(launch_vocab, vocab_bound(*R, *S));
+        launch_force_index = launch_force_index || (b->flags & SSJ_FORCE_INDEX) != 0;
         table[i].tile_base = sh.n_tiles;
         const uint64_t tiles = ((uint64_t)b->n_probes + 31) / 32;
         if ((uint64_t)sh.n_tiles + tiles > 0x7FFFFFFull) return fail(ctx, SSJ_EINVAL, "too many probes in one call");
@@ -842,10 +908,8 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
     }
     VerifyArgs a;
     memset(&a, 0, sizeof(a));
-    a.thread_max_key = ctx->thread_max_key;
-    a.drain_min_live = ctx->drain_min_live;
-    a.lane_max_key = ctx->lane_max_key;
-    a.warp_max_key = ctx->warp_max_key;
+    apply_policy(ctx, a, launch_vocab, launch_force_index);
+    if (pinned) set_l2_window(a, *pinned);
     bind_workspace(a, ctx->ws, sh, ctx->num_sms);
     a.table = a.table_out;
     CUDA_TRY(ctx, cudaMemcpyAsync(a.table_out, table.data(), sizeof(Instance) * n_batches, cudaMemcpyHostToDevice, s));
@@ -884,7 +948,7 @@ extern "C" ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uin
     NvtxScope nvtx_scope("ssj_self_join");
     if (!ctx || !n_out) return fail(ctx, SSJ_EINVAL, "NULL argument");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_SIM_MASK | SSJ_JOIN_POSITIONAL |
-                           SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE;
+                           SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_FORCE_INDEX;
     if (flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown flag");
     if (cap && !out && !(flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output with cap > 0");
     // threshold and collection checks through the batch path's resolve()
@@ -893,7 +957,8 @@ extern "C" ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uin
     probe_b.R = probe_b.S = coll;
     probe_b.p = p;
     probe_b.q = q;
-    probe_b.flags = flags & (SSJ_SIM_MASK | SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE);
+    probe_b.flags = flags & (SSJ_SIM_MASK | SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE |
+                             SSJ_FORCE_INDEX);
     Collection *R, *S;
     ssj_status st = resolve(ctx, &probe_b, &R, &S);
     if (st != SSJ_OK) return st;
@@ -1069,7 +1134,7 @@ extern "C" ssj_status ssj_verify_groups(ssj_ctx* ctx, const ssj_group_batch* gb,
     NvtxScope nvtx_scope("ssj_verify_groups");
     if (!ctx || !gb || !n_out) return fail(ctx, SSJ_EINVAL, "NULL argument");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_SIM_MASK | SSJ_FORCE_THREAD |
-                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE;
+                           SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_FORCE_INDEX;
     if (gb->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown flag");
     if (cap && !out && !(gb->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output with cap > 0");
     if (!gb->group_offsets || (gb->n_groups && !gb->members) || (gb->n_probe_groups && (!gb->probe_groups ||
@@ -1080,7 +1145,8 @@ extern "C" ssj_status ssj_verify_groups(ssj_ctx* ctx, const ssj_group_batch* gb,
     probe_b.R = probe_b.S = gb->coll;
     probe_b.p = gb->p;
     probe_b.q = gb->q;
-    probe_b.flags = gb->flags & (SSJ_SIM_MASK | SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE);
+    probe_b.flags = gb->flags & (SSJ_SIM_MASK | SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE |
+                                SSJ_FORCE_INDEX);
     Collection *R, *S;
     ssj_status st = resolve(ctx, &probe_b, &R, &S);
     if (st != SSJ_OK) return st;
@@ -1605,6 +1671,8 @@ struct ssj_multi {
     VerifyArgs a;
     LaunchShape shape;
     uint32_t block_threads = 256;
+    uint32_t index_words_fit = 0;  // probe bitmap words the instances' token values need (0: too many)
+    bool force_index = false;      // an instance forces index items
     void* ws = nullptr;
     std::vector<ssj_coll> colls;  // collections marked busy
     cudaStream_t capture_stream = nullptr;
@@ -1624,6 +1692,8 @@ extern "C" ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, u
     sh.total_probes = 0;
     sh.total_cands = 0;
     std::unique_ptr<ssj_multi> m(new ssj_multi());
+    uint64_t vocab = 1;
+    const Collection* pinned = nullptr;  // the first pinned collection: its L2 window
     for (uint32_t i = 0; i < n_batches; ++i) {
         const ssj_batch* b = &batches[i];
         Collection *R, *S;
@@ -1648,16 +1718,18 @@ extern "C" ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, u
         table[i] = I;
         m->colls.push_back(b->R);
         m->colls.push_back(b->S);
+        vocab = std::max(vocab, vocab_bound(*R, *S));
+        m->force_index = m->force_index || (b->flags & SSJ_FORCE_INDEX) != 0;
+        if (!pinned) pinned = R->l2_window ? R : (S->l2_window ? S : nullptr);
     }
     DeviceGuard g(ctx->device);
     const size_t bytes = workspace_bytes(sh, ctx->num_sms);
     cudaError_t e = cudaMalloc(&m->ws, bytes);
     if (e != cudaSuccess) return fail(ctx, SSJ_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     memset(&m->a, 0, sizeof(m->a));
-    m->a.thread_max_key = ctx->thread_max_key;
-    m->a.drain_min_live = ctx->drain_min_live;
-    m->a.lane_max_key = ctx->lane_max_key;
-    m->a.warp_max_key = ctx->warp_max_key;
+    apply_policy(ctx, m->a, vocab, m->force_index);
+    if (pinned) set_l2_window(m->a, *pinned);
+    m->index_words_fit = index_words_for(vocab);
     m->block_threads = ctx->block_threads;
     bind_workspace(m->a, m->ws, sh, ctx->num_sms);
     m->a.table = m->a.table_out;
@@ -1669,7 +1741,7 @@ extern "C" ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, u
             return cuda_fail(ctx, e, "instance table upload");
         }
     }
-    e = prepare_verify(ctx->block_threads);
+    e = prepare_verify(ctx->block_threads, m->a.index_words);
     if (e != cudaSuccess) {
         cudaFree(m->ws);
         return cuda_fail(ctx, e, "prepare_verify");
@@ -1741,13 +1813,15 @@ namespace {
 // Median device time (ms) of reps launches of m with the given granularity,
 // after one untimed launch; negative on a CUDA error (*err receives it).
 float time_setting(ssj_ctx* ctx, const ssj_multi* m, uint32_t tmax, uint32_t lmax, uint32_t wmax, uint32_t bt,
-                   uint32_t dml, uint32_t reps, cudaStream_t s, cudaEvent_t* ev, cudaError_t* err) {
+                   uint32_t dml, uint32_t imin, uint32_t reps, cudaStream_t s, cudaEvent_t* ev, cudaError_t* err) {
     VerifyArgs a = m->a;
     a.thread_max_key = tmax;
     a.lane_max_key = lmax;
     a.warp_max_key = wmax;
     a.drain_min_live = dml;
-    cudaError_t e = prepare_verify(bt);
+    a.index_min_cands = imin;
+    a.index_words = (imin || m->force_index) ? m->index_words_fit : 0u;
+    cudaError_t e = prepare_verify(bt, a.index_words);
     if (e == cudaSuccess) e = launch_verify(a, s, ctx->num_sms, bt, nullptr);
     std::vector<float> ms;
     for (uint32_t i = 0; e == cudaSuccess && i < reps; ++i) {
@@ -1790,16 +1864,21 @@ extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* strea
     static const uint32_t kLane[] = {1, 256, 512, 1024, 2048};
     static const uint32_t kWarp[] = {256, 512, 1024, 2048, 4096, 0xFFFFFFFFu};
     static const uint32_t kBlock[] = {128, 256, 512, 128 | SSJ_WIDE_REGISTERS, 256 | SSJ_WIDE_REGISTERS,
-                                      512 | SSJ_WIDE_REGISTERS};
+                                      512 | SSJ_WIDE_REGISTERS, 256 | SSJ_BULK_STAGING, 512 | SSJ_BULK_STAGING,
+                                      256 | SSJ_WIDE_REGISTERS | SSJ_BULK_STAGING,
+                                      512 | SSJ_WIDE_REGISTERS | SSJ_BULK_STAGING};
     static const uint32_t kMinLive[] = {8, 12, 16, 20, 24};
-    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, uint32_t>, float> seen;
+    // index-item threshold: 0 sends no probe to index items
+    static const uint32_t kIndexMin[] = {0, 32, 64, 128, 256, 512, 1024, 4096};
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t>, float> seen;
     cudaError_t err = cudaSuccess;
     uint32_t bd = m->a.drain_min_live ? m->a.drain_min_live : 16;
+    uint32_t bi = m->index_words_fit ? m->a.index_min_cands : 0u;
     auto cost = [&](uint32_t t, uint32_t l, uint32_t w, uint32_t b) -> float {
-        auto key = std::make_tuple(t, l, w, b, bd);
+        auto key = std::make_tuple(t, l, w, b, bd, bi);
         auto it = seen.find(key);
         if (it != seen.end()) return it->second;
-        const float v = time_setting(ctx, m, t, l, w, b, bd, reps, s, ev, &err);
+        const float v = time_setting(ctx, m, t, l, w, b, bd, bi, reps, s, ev, &err);
         seen[key] = v;
         return v;
     };
@@ -1838,6 +1917,13 @@ extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* strea
             const float v = cost(bt, bl, bw, bb);
             if (v < best) best = v; else bd = keep;
         }
+        for (uint32_t x : kIndexMin) {
+            if (err != cudaSuccess || (x && !m->index_words_fit)) break;
+            const uint32_t keep = bi;
+            bi = x;
+            const float v = cost(bt, bl, bw, bb);
+            if (v < best) best = v; else bi = keep;
+        }
         if (!(best < 0.98f * before)) break;  // no gain worth another sweep
     }
     cudaEventDestroy(ev[0]);
@@ -1851,8 +1937,10 @@ extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* strea
     m->a.lane_max_key = bl;
     m->a.warp_max_key = bw;
     m->a.drain_min_live = bd;
+    m->a.index_min_cands = bi;
+    m->a.index_words = (bi || m->force_index) ? m->index_words_fit : 0u;
     m->block_threads = bb;
-    CUDA_TRY(ctx, prepare_verify(bb));
+    CUDA_TRY(ctx, prepare_verify(bb, m->a.index_words));
     if (m->exec) {
         cudaGraphExecDestroy(m->exec);
         m->exec = nullptr;
@@ -1866,6 +1954,7 @@ extern "C" ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* strea
     out->warp_max_key = bw;
     out->block_threads = bb;
     out->drain_min_live = bd;
+    out->index_min_cands = bi;
     out->best_ms = best;
     out->initial_ms = first;
     out->settings_tried = (uint32_t)seen.size();

@@ -26,6 +26,7 @@ enum : uint32_t {
     VF_FORCE_BLOCK = 16u,
     VF_SELF_JOIN = 32u,
     VF_FORCE_LANE = 64u,
+    VF_FORCE_INDEX = 128u,
 };
 
 // One join instance of a launch: its collections, grouped candidate list,
@@ -64,7 +65,9 @@ enum : uint32_t {
 // Work item for warp-, lane- or block-per-pair verification: n candidates of
 // probe set r starting at candidate index c0, in instance inst.  In the warp
 // list, mode 0 is one warp per pair, mode 1 one lane per pair (r in shared
-// memory).
+// memory).  In the block list, mode 0 is one thread block per pair, mode 1
+// an index item: the whole block holds r as a bitmap over the token values
+// and every thread verifies one candidate at a time against it.
 struct WorkItem {
     uint32_t r;
     uint32_t n;
@@ -115,6 +118,8 @@ constexpr uint32_t kWarpItemCands = 8;   // most candidates per warp work item
 constexpr uint32_t kBlockItemCands = 16; // most candidates per block work item
 constexpr uint32_t kLaneItemCands = 128; // most candidates per lane work item
 constexpr uint32_t kLaneMinCands = 16;   // fewest candidates of a probe sent to the lane bin
+constexpr uint32_t kIndexMaxWords = 24576;  // largest probe bitmap (32-bit words, 96 KiB): token values below 786,432
+constexpr uint32_t kIndexItemCands = 8192;  // most candidates per index item
 
 // Kernel arguments of one launch (passed by value).
 struct VerifyArgs {
@@ -140,7 +145,23 @@ struct VerifyArgs {
     uint32_t lane_max_key;        // 2|r| <= this (and r fits, >= kLaneMinCands candidates): one lane per pair
     uint32_t warp_max_key;        // 2|r| <= this: one warp per pair; above: one block
     uint32_t drain_min_live;      // short-pair pass 2 re-parks below this many live lanes (0: default 16)
+    uint32_t index_words;         // probe bitmap words (every token value of the launch's collections below
+                                  // 32 * index_words); 0: no index items
+    uint32_t index_min_cands;     // probes with at least this many candidates become index items (0: none)
+    uint32_t index_item_cands;    // candidates per index item
+    uint32_t bulk_stage;          // block and warp items stage sets by bulk copies (cp.async.bulk)
+    // host side only: an L2 access-policy window (persisting) for the verify kernel's launch, or none
+    const void* l2_base;
+    uint64_t l2_bytes;
+    float l2_hit_ratio;
 };
+
+// Bitmap words for index items over collections whose token values are all
+// below vocab_bound (0 when that exceeds kIndexMaxWords); a multiple of 4.
+inline uint32_t index_words_for(uint64_t vocab_bound) {
+    const uint64_t w = ((vocab_bound + 31) / 32 + 3) & ~3ull;
+    return (w == 0 || w > kIndexMaxWords) ? 0u : (uint32_t)w;
+}
 
 // Sizes of one launch, from which the workspace is carved.
 struct LaunchShape {
@@ -163,10 +184,12 @@ void bind_workspace(VerifyArgs& a, void* ws, uint32_t n_probes, uint64_t n_cands
 // block_threads flag selecting the verify kernel variant compiled for three
 // quarters of the CTAs per SM (more registers per thread, fewer spills).
 constexpr uint32_t kWideRegisters = SSJ_WIDE_REGISTERS;
+// block_threads flag: block and warp items stage the sets by bulk copies.
+constexpr uint32_t kBulkStaging = SSJ_BULK_STAGING;
 
 // Set the verify kernel's launch attributes for this device (done by the
 // first launch anyway; call before capturing a launch into a graph).
-cudaError_t prepare_verify(uint32_t block_threads);
+cudaError_t prepare_verify(uint32_t block_threads, uint32_t index_words = 0);
 
 // Enqueue the whole verification (counter clear, plan, verify) on st.
 // ev (optional, 3 events): recorded before the plan kernel, between plan and

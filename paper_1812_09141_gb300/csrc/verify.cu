@@ -16,7 +16,15 @@
 //   * verify_kernel, persistent (one wave of CTAs over the SMs):
 //       phase 1 - block items: one CTA per pair, Intersect Path across the
 //                 whole CTA (Alternative C, Sections 4.2.2-4.2.3), r kept in
-//                 shared memory for the item's candidates;
+//                 shared memory for the item's candidates; and index items:
+//                 the CTA holds r as a bitmap over the token values (one bit
+//                 per value, in shared memory) and every thread walks one
+//                 candidate s at a time through the merge, s side by s side:
+//                 each token of s is tested against r by one bit lookup, so
+//                 r's tokens are read once per item instead of once per
+//                 pair (Alternative B with the probe in shared memory,
+//                 Section 3.3.2; the s-side positional bound of Section
+//                 2.2.3 after every 16-byte block);
 //       phase 2 - warp items: one warp per pair, 32-lane merge path, r kept
 //                 in the warp's shared memory for the item's candidates;
 //       phase 3 - short pairs, one pair per thread (Alternatives A/B), 32
@@ -40,6 +48,7 @@
 //   counted (output count).
 #include <atomic>
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "arith.h"
@@ -96,6 +105,73 @@ __device__ __forceinline__ bool in_bounds(uint64_t idx, uint64_t n, uint32_t* er
 __device__ __forceinline__ uint4 ld_block(const uint4* base, uint64_t idx, uint64_t lim, uint32_t* err) {
     if (!in_bounds(idx, lim, err)) return make_uint4(0u, 0u, 0u, 0u);
     return __ldg(base + idx);
+}
+
+// ---------------------------------------------------------------------------
+// One-dimensional bulk copies global -> shared memory (cp.async.bulk on the
+// copy engine, completion counted in bytes on an mbarrier), used to stage
+// the probe set and candidate sets of block and warp items.  Addresses and
+// sizes are multiples of 16 bytes (sets start on 16-byte chunks).  Waits are
+// bounded: one thread polls the barrier for at most about a second of SM
+// clocks and reports a timeout (ERR_GUARD) instead of spinning forever.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// The calling thread arrives on bar expecting `bytes` more bytes, then asks
+// the copy engine for `bytes` bytes from src to dst (previous generic-proxy
+// accesses of dst are ordered before the copy by the proxy fence).
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Poll bar until the phase with the given parity has completed; false (and
+// ERR_GUARD) if that takes more than about a second.
+constexpr long long kBulkWaitCycles = 2000000000ll;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done = 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kBulkWaitCycles) {
+            atomicOr(err, ERR_GUARD);
+            return false;
+        }
+        __nanosleep(20);
+    }
+}
+
+// Chunks [c_lo, c_hi) of a token array (16 bytes each) into dst by one bulk
+// copy on bar; the checked build tests both ends against the array's and
+// the buffer's extents and skips the copy (arriving without bytes) when one
+// is out of range.
+__device__ __forceinline__ void bulk_stage(uint32_t* dst, const uint4* set4, uint32_t c_lo, uint32_t c_hi, uint64_t lim,
+                                           uint32_t dst_blocks, uint64_t* bar, uint32_t* err) {
+    const uint32_t n = c_hi - c_lo;
+    if (n == 0 || !in_bounds(c_hi - 1, lim, err) || !in_bounds(n - 1, dst_blocks, err)) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+        return;
+    }
+    bulk_copy(dst, set4 + c_lo, 16u * n, bar);
 }
 
 // A parked pair with its merge state.
@@ -240,13 +316,18 @@ __device__ __forceinline__ void lane_merge(const uint32_t* A, uint32_t rw, const
 // -------------------------------------------------------------------------
 // Warp-cooperative merge of one pair (all 32 lanes, uniform arguments).
 // If r_staged, abuf holds all of r (abuf[k] = r[k]); otherwise abuf is a
-// window buffer.  bbuf is the s window buffer.
+// window buffer.  bbuf is the s window buffer, filled per window by the
+// lanes' 16-byte loads or, with wbar (bulk staging), by one bulk copy on the
+// warp's barrier (phase parity *wph); a copy that does not complete sets
+// *failed and ends the merge.
 // -------------------------------------------------------------------------
 __device__ uint32_t warp_merge(const uint4* __restrict__ r4, uint32_t nr, const uint4* __restrict__ s4, uint32_t ns,
                                uint32_t req, bool early, bool r_staged, uint32_t* abuf, uint32_t* bbuf, int lane,
+                               uint64_t* wbar, uint32_t* wph, uint64_t slim, uint32_t* err, bool* failed,
                                bool* rejected CHK_PARAMS) {
     uint32_t i0 = 0, j0 = 0, o = 0;
     *rejected = false;
+    *failed = false;
     for (;;) {
         const uint32_t left = min(nr - i0, ns - j0);
         if (early && o + left < req) { *rejected = true; break; }
@@ -261,7 +342,20 @@ __device__ uint32_t warp_merge(const uint4* __restrict__ r4, uint32_t nr, const 
             stage<32>(r4, i0, rw, abuf, lane, CHK_RLIM, kWarpABuf / 4, CHK_ERR);
             A = abuf + (i0 & 3u);
         }
-        stage<32>(s4, j0, sw, bbuf, lane, CHK_SLIM, kWarpBBuf / 4, CHK_ERR);
+        if (wbar) {  // bulk staging: the window of s by one bulk copy, lane 0 waits
+            uint32_t ok = 1;
+            if (lane == 0) {
+                bulk_stage(bbuf, s4, j0 >> 2, (j0 + sw + 3) >> 2, slim, kWarpBBuf / 4, wbar, err);
+                ok = mbar_wait(wbar, *wph, err) ? 1u : 0u;
+            }
+            *wph ^= 1u;
+            if (!__shfl_sync(kFull, ok, 0)) {
+                *failed = true;
+                break;
+            }
+        } else {
+            stage<32>(s4, j0, sw, bbuf, lane, CHK_SLIM, kWarpBBuf / 4, CHK_ERR);
+        }
         __syncwarp();
         const uint32_t* B = bbuf + (j0 & 3u);
         const uint32_t d = min((uint32_t)lane * kWarpD, Wc), de = min(d + kWarpD, Wc);
@@ -281,19 +375,25 @@ __device__ uint32_t warp_merge(const uint4* __restrict__ r4, uint32_t nr, const 
 
 // -------------------------------------------------------------------------
 // Block-cooperative merge of one pair (Alternative C).  r is staged whole in
-// rbuf when it fits (r_staged), else per window in wbuf_r.
+// rbuf when it fits (r_staged), else per window in wbuf_r; s is staged whole
+// in wbuf_s by the caller (s_staged: bulk staging) or per window.
 // -------------------------------------------------------------------------
 template <int BT>
 struct BlockSmem {
+    uint64_t bar[3];  // bulk staging: r, and the two candidate buffers
     uint32_t red[BT / 32];
     uint32_t end_i, end_j;
     uint32_t item;
+    uint32_t next;       // index items: next candidate of the item
+    uint32_t staged[2];  // bulk staging: candidate buffer b holds the whole set s of its candidate
+    uint32_t ok;         // bulk staging: the last wait completed
 };
 
 template <int BT>
 __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const uint4* __restrict__ s4,
                                 uint32_t ns, uint32_t req, bool early, const uint32_t* rbuf, bool r_staged,
-                                uint32_t* wbuf_r, uint32_t* wbuf_s, BlockSmem<BT>* sm, bool* rejected CHK_PARAMS) {
+                                uint32_t* wbuf_r, uint32_t* wbuf_s, bool s_staged, BlockSmem<BT>* sm,
+                                bool* rejected CHK_PARAMS) {
     constexpr uint32_t W = BT * kBlockD;
     const int tid = threadIdx.x;
     uint32_t i0 = 0, j0 = 0, o = 0;
@@ -312,9 +412,14 @@ __device__ uint32_t block_merge(const uint4* __restrict__ r4, uint32_t nr, const
             stage<BT>(r4, i0, rw, wbuf_r, tid, CHK_RLIM, (W + 16) / 4, CHK_ERR);
             A = wbuf_r + (i0 & 3u);
         }
-        stage<BT>(s4, j0, sw, wbuf_s, tid, CHK_SLIM, (W + 16) / 4, CHK_ERR);
+        const uint32_t* B;
+        if (s_staged) {  // all of s is in wbuf_s already (bulk copy)
+            B = wbuf_s + j0;
+        } else {
+            stage<BT>(s4, j0, sw, wbuf_s, tid, CHK_SLIM, (W + 16) / 4, CHK_ERR);
+            B = wbuf_s + (j0 & 3u);
+        }
         __syncthreads();
-        const uint32_t* B = wbuf_s + (j0 & 3u);
         const uint32_t d = min((uint32_t)tid * kBlockD, Wc), de = min(d + kBlockD, Wc);
         uint32_t c = 0, ie = 0, je = 0;
         if (d < de) lane_merge<kBlockD>(A, rw, B, sw, d, de, &c, &ie, &je);
@@ -416,11 +521,21 @@ __device__ __noinline__ uint32_t drain_parked(ContEntry* cont, uint32_t n_cont, 
         if (!fin) lean_step(rc, rn, sc, sn, rb, sb, rcur, scur, remr, rems, o, req, early, fin, rej, rlim, slim, CHK_ERR);
         if (!fin) lean_step(rc, rn, sc, sn, rb, sb, rcur, scur, remr, rems, o, req, early, fin, rej, rlim, slim, CHK_ERR);
     }
-    if (have && fin && (!early || (!rej && o >= req))) {
-        const Instance& I = table[inst];
-        const unsigned long long idx = atomicAdd(I.count, 1ull);
-        if (!(I.flags & VF_COUNT_ONLY))
-            emit_triple(I.out, I.cap, (I.flags & VF_SELF_JOIN) != 0, idx, rid_of_slot[slot], sid, o);
+    // survivors: one atomic per instance among the warp's lanes (lanes may hold different instances)
+    const bool pass = have && fin && (!early || (!rej && o >= req));
+    const uint32_t pmask = __ballot_sync(kFull, pass);
+    if (pmask) {
+        const uint32_t grp = __match_any_sync(kFull, inst) & pmask;  // passing lanes of my instance
+        if (pass) {
+            const Instance& I = table[inst];
+            const int leader = __ffs(grp) - 1;
+            unsigned long long b0 = 0;
+            if (lane == leader) b0 = atomicAdd(I.count, (unsigned long long)__popc(grp));
+            b0 = __shfl_sync(grp, b0, leader);
+            if (!(I.flags & VF_COUNT_ONLY))
+                emit_triple(I.out, I.cap, (I.flags & VF_SELF_JOIN) != 0, b0 + __popc(grp & lt_mask),
+                            rid_of_slot[slot], sid, o);
+        }
     }
     const bool again = have && !fin;
     const uint32_t amask = __ballot_sync(kFull, again);
@@ -536,16 +651,220 @@ __device__ __noinline__ void lane_item(const Instance& I, const WorkItem& wi, ui
     }
 }
 
+// Bit of token value x in the probe bitmap (words bm[0, n_words)).
+__device__ __forceinline__ uint32_t bm_bit(const uint32_t* bm, uint32_t x, uint32_t n_words, uint32_t* err) {
+    const uint32_t w = x >> 5;
+    if (!in_bounds(w, n_words, err)) return 0u;
+    return (bm[w] >> (x & 31u)) & 1u;
+}
+
+// Set (or, with clear, zero the words of) the bits of r's tokens; r's
+// padding repeats its last token, so whole blocks are used.
+template <int BT>
+__device__ __forceinline__ void bm_mark(uint32_t* bm, const uint4* r4, uint32_t nr, uint64_t rlim, uint32_t n_words,
+                                        bool clear, int tid, uint32_t* err) {
+    for (uint32_t c = tid; c < ((nr + 3) >> 2); c += BT) {
+        const uint4 b = ld_block(r4, c, rlim, err);
+        const uint32_t v[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t w = v[k] >> 5;
+            if (!in_bounds(w, n_words, err)) continue;
+            if (clear) bm[w] = 0u;
+            else atomicOr(bm + w, 1u << (v[k] & 31u));
+        }
+    }
+}
+
+// Asynchronous 16-byte copy global -> shared memory (cp.async, cached in L2
+// only) and its per-thread groups.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One index item: candidates [c0, c0 + n) of probe r, verified by every
+// thread of the CTA, one candidate per thread at a time.  r is held as a
+// bitmap over the token values (bm, all zero on entry and on return).  A
+// candidate s is merged against r from the s side: block by block (16
+// bytes, 4 tokens), each token tested by one bit lookup, so the state after
+// a block is the merge's state after s's token j: o matches, |s| - j tokens
+// of s left.  The merge stops when o + (|s| - j) falls below the required
+// overlap (the positional bound of Section 2.2.3 with the s side's
+// remainder; never stricter than the merge's bound, so no passing pair is
+// lost) or when s's block reaches r's last token (no later token of s can
+// match); a pair that is not rejected runs to that point, so its overlap is
+// exactly |r n s|.
+//
+// The walk is software-pipelined so that no thread waits on a load it has
+// just issued.  Each warp prepares its candidates 32 at a time: their ids
+// are loaded, kIndexWait iterations later their descriptors, kIndexWait
+// iterations later again the required overlap and the length filter decide
+// which enter the warp's queue (shared memory).  An idle lane takes the next
+// queued candidate; each iteration it asks for one more block of s (cp.async
+// into its own ring of kIndexRing blocks in shared memory, at most
+// kIndexRing blocks ahead of its walk) and merges the block it asked for
+// kIndexWait iterations before.
+constexpr uint32_t kIndexRing = 4;   // blocks of s per thread in the ring
+constexpr uint32_t kIndexQueue = 64; // prepared candidates per warp
+constexpr int kIndexWait = 2;        // iterations between a load and its first read
+
+template <int BT>
+__device__ __noinline__ void index_item(const Instance& I, const WorkItem& wi, uint32_t nr, const uint4* r4,
+                                        uint64_t rlim, uint32_t* bm, uint32_t n_words, uint4* rings,
+                                        uint4* queues, BlockSmem<BT>* sm, uint32_t* err) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t flags = I.flags;
+    const bool emit_all = (flags & VF_EMIT_ALL) != 0, early = !emit_all;
+    const bool self_join = (flags & VF_SELF_JOIN) != 0;
+    uint4* ring = rings + (size_t)tid * kIndexRing;
+    uint4* queue = queues + (size_t)warp * kIndexQueue;
+    if (tid == 0) sm->next = 0;
+    bm_mark<BT>(bm, r4, nr, rlim, n_words, false, tid, err);
+    // r's last token (the padding repeats it in the last block's last lane)
+    const uint32_t rmax = nr ? ld_block(r4, (nr - 1) >> 2, rlim, err).w : 0u;
+    __syncthreads();
+
+    // candidate preparation (warp-uniform stage machine; stage 0 takes 32 candidates)
+    uint32_t pstage = 0, page = 0, qhead = 0, qtail = 0;  // warp-uniform (queue cursors free-running)
+    bool pdone = false;                                    // warp-uniform: no candidates left to take
+    bool p_ok = false;
+    uint32_t p_id = 0;
+    uint2 p_desc = make_uint2(0u, 0u);
+    // the lane's pair: next block to merge (jb) and to ask for (jr) of its nblk blocks, ring slot of
+    // its block 0 (rb), blocks asked for in the last iterations (hist, one bit per iteration)
+    bool active = false;
+    uint32_t s_id = 0, rems = 0, req = 0, o = 0, jb = 0, jr = 0, nblk = 0, rb = 0, hist = 0;
+    const uint4* s4 = nullptr;
+    uint64_t slim = 0;
+    for (;;) {
+        // ---- preparation
+        if (pstage == 0) {
+            if (!pdone && qtail - qhead + 32 <= kIndexQueue) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&sm->next, 32u);
+                base = __shfl_sync(kFull, base, 0);
+                if (base + 32 >= wi.n) pdone = true;
+                const uint32_t my = base + (uint32_t)lane;
+                p_ok = my < wi.n && in_bounds(wi.c0 + my, I.n_cands, err);
+                if (p_ok) p_id = I.cand_ids[wi.c0 + my];
+                if (base < wi.n) {
+                    pstage = 1;
+                    page = 0;
+                }
+            }
+        } else if (++page >= (uint32_t)kIndexWait) {
+            page = 0;
+            if (pstage == 1) {
+                if (p_ok && p_id >= I.s_n_sets) {
+                    atomicOr(err, ERR_CAND_ID);
+                    p_ok = false;
+                }
+                if (p_ok && self_join && p_id == wi.r) p_ok = false;
+                if (p_ok) p_desc = I.s_desc[p_id];
+                pstage = 2;
+            } else {
+                uint32_t q = 0;
+                if (p_ok) {
+                    q = required_overlap(I.sim, I.p, I.den, I.magic, nr, p_desc.y);
+                    p_ok = emit_all || (nr + p_desc.y > 0 && q <= min(nr, p_desc.y));  // length filter
+                }
+                const uint32_t m = __ballot_sync(kFull, p_ok);
+                if (p_ok) queue[(qtail + __popc(m & lt_mask)) % kIndexQueue] = make_uint4(p_id, p_desc.x, p_desc.y, q);
+                qtail += __popc(m);
+                pstage = 0;
+                __syncwarp();
+            }
+        }
+        // ---- idle lanes take queued candidates
+        const uint32_t idle = __ballot_sync(kFull, !active);
+        if (idle && qtail != qhead) {
+            const uint32_t k = min((uint32_t)__popc(idle), qtail - qhead);
+            const uint32_t rank = __popc(idle & lt_mask);
+            if (!active && rank < k) {
+                const uint4 e = queue[(qhead + rank) % kIndexQueue];
+                rb = (rb + jr) & (kIndexRing - 1);  // continue the lane's ring after its last request
+                active = true;
+                s_id = e.x;
+                rems = e.z;
+                req = e.w;
+                o = 0;
+                jb = 0;
+                jr = 0;
+                hist = 0;
+                nblk = (rems + 3) >> 2;
+                s4 = I.s_toks4 + e.y;
+                slim = I.s_n_chunks - e.y;
+            }
+            qhead += k;
+            __syncwarp();
+        }
+        // ---- ask for one more block; merge the one asked for kIndexWait iterations ago
+        uint32_t asked = 0;
+        if (active && jr < nblk && jr < jb + kIndexRing) {
+            if (in_bounds(jr, slim, err)) cp_async16(ring + ((rb + jr) & (kIndexRing - 1)), s4 + jr);
+            ++jr;
+            asked = 1;
+        }
+        cp_async_commit();
+        hist = (hist << 1) | asked;
+        cp_async_wait<kIndexWait>();  // every block asked for before the last kIndexWait iterations is in
+        bool done = false, rej = false;
+        if (active) {
+            const uint32_t landed = jr - __popc(hist & ((1u << kIndexWait) - 1u));
+            if (rems == 0 || nr == 0) {
+                done = true;  // an empty side: overlap 0
+            } else if (jb < landed) {
+                const uint4 sc = ring[(rb + jb) & (kIndexRing - 1)];
+                const uint32_t nv = min(rems, 4u);
+                const uint32_t bw = bm_bit(bm, sc.w, n_words, err);
+                // the lanes past nv valid tokens repeat the last one (sc.w): subtract them again
+                o += bm_bit(bm, sc.x, n_words, err) + bm_bit(bm, sc.y, n_words, err) +
+                     bm_bit(bm, sc.z, n_words, err) + bw - (4u - nv) * bw;
+                rems -= nv;
+                ++jb;
+                done = rems == 0 || sc.w >= rmax;  // no later token of s can match
+                rej = !done && early && o + rems < req;
+                done = done || rej;
+            }
+        }
+        const bool pass = done && (emit_all || (!rej && o >= req));
+        const uint32_t pmask = __ballot_sync(kFull, pass);
+        if (pmask) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(I.count, (unsigned long long)__popc(pmask));
+            if (!(flags & VF_COUNT_ONLY)) {
+                b0 = __shfl_sync(kFull, b0, 0);
+                if (pass) emit_triple(I.out, I.cap, self_join, b0 + __popc(pmask & lt_mask), wi.r, s_id, o);
+            }
+        }
+        if (done) active = false;
+        if (pdone && pstage == 0 && qhead == qtail && !__any_sync(kFull, active)) break;
+    }
+    cp_async_wait<0>();  // the ring's last copies (asked for past a pair's end) are in
+    __syncthreads();     // every thread is done with the bitmap
+    bm_mark<BT>(bm, r4, nr, rlim, n_words, true, tid, err);
+    __syncthreads();
+}
+
 // Granularity of a probe with |r| = nr and n candidates: 0 thread per pair,
 // 1 warp per pair, 2 block per pair, 3 lane per pair with r in the warp's
 // shared memory (Alternative B; needs r to fit and enough candidates to
-// occupy the lanes).
+// occupy the lanes), 4 index items (probes with many candidates, when the
+// launch's token values fit the probe bitmap).
 __device__ __forceinline__ uint32_t probe_bin(const VerifyArgs& a, uint32_t flags, uint32_t nr, uint64_t n) {
     const bool lane_ok = nr + 4 <= kWarpRCap;
+    if (flags & VF_FORCE_INDEX) return a.index_words ? 4u : (lane_ok ? 3u : 1u);
     if (flags & VF_FORCE_BLOCK) return 2;
     if (flags & VF_FORCE_WARP) return 1;
     if (flags & VF_FORCE_THREAD) return 0;
     if (flags & VF_FORCE_LANE) return lane_ok ? 3u : 1u;
+    if (a.index_words && a.index_min_cands && n >= a.index_min_cands) return 4;
     const uint64_t key = 2ull * nr;  // |r|+|s| at |s| = |r|
     if (key <= a.thread_max_key) return 0;
     if (key <= a.lane_max_key && lane_ok && n >= kLaneMinCands) return 3;
@@ -683,9 +1002,10 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
         const unsigned long long ttotal = __shfl_sync(kFull, tincl, 31);
         const unsigned long long tpadded = (ttotal + 31) & ~31ull;
         // work item counts (lane items share the warp item list, marked by mode 1)
-        const uint32_t wc = bin == 3 ? a.lane_item_cands : a.warp_item_cands, bc = a.block_item_cands;
+        const uint32_t wc = bin == 3 ? a.lane_item_cands : a.warp_item_cands;
+        const uint32_t bc = bin == 4 ? a.index_item_cands : a.block_item_cands;
         const unsigned long long wn = (bin == 1 || bin == 3) ? (n + wc - 1) / wc : 0;
-        const unsigned long long bn = (bin == 2) ? (n + bc - 1) / bc : 0;
+        const unsigned long long bn = (bin == 2 || bin == 4) ? (n + bc - 1) / bc : 0;
         unsigned long long wincl = wn, bincl = bn;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -806,7 +1126,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(VerifyArgs a) {
             bi.n = (uint32_t)min((uint64_t)bc, c0 + n - s0);
             bi.c0 = s0;
             bi.inst = inst;
-            bi.pad = 0;
+            bi.pad = bin == 4 ? 1u : 0u;
             a.block_items[bbase + it] = bi;
         }
     }
@@ -822,6 +1142,7 @@ template <int BT, int MINB>
 __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ BlockSmem<BT> bsm;
+    __shared__ uint64_t s_wbar[BT / 32];  // bulk staging: one barrier per warp for phase 2
     constexpr uint32_t kBlockWin = BT * kBlockD;
     constexpr int kWarps = BT / 32;
 
@@ -850,6 +1171,15 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
         uint32_t* rbuf = smem;                                // kBlockRCap + 16
         uint32_t* wr = smem + kBlockRCap + 16;                // kBlockWin + 16
         uint32_t* ws = wr + kBlockWin + 16;                   // kBlockWin + 16
+        uint32_t* bm = smem;                                  // index items' probe bitmap (a.index_words)
+        bool bm_zero = false;                                 // CTA-uniform: bm holds zeros only
+        uint32_t r_phase = 0;                                 // bulk staging: parity of bar[0]'s next phase
+        uint32_t ph[2] = {0u, 0u};                            // the same for the candidate buffers' barriers
+        if (a.bulk_stage) {
+            if (tid == 0)
+                for (int k = 0; k < 3; ++k) mbar_init(&bsm.bar[k], 1);
+            __syncthreads();
+        }
         for (uint32_t round = 0;; ++round) {
             if (tid == 0) bsm.item = round == 0 ? blockIdx.x : gridDim.x + atomicAdd(&a.ctr->block_cursor, 1u);
             __syncthreads();
@@ -866,12 +1196,72 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
             const uint2 dr = I.r_desc[bi.r];
             const uint32_t nr = dr.y;
             const uint4* r4 = I.r_toks4 + dr.x;
+            if (bi.pad == 1) {  // index item (uniform over the CTA)
+                if (!bm_zero) {  // the bitmap shares its memory with the block-merge buffers
+                    uint4* b4 = reinterpret_cast<uint4*>(bm);
+                    for (uint32_t k = tid; k < a.index_words / 4; k += BT) b4[k] = make_uint4(0u, 0u, 0u, 0u);
+                    __syncthreads();
+                    bm_zero = true;
+                }
+                uint4* rings = reinterpret_cast<uint4*>(bm + a.index_words);
+                index_item<BT>(I, bi, nr, r4, I.r_n_chunks - dr.x, bm, a.index_words, rings, rings + BT * kIndexRing,
+                               &bsm, &a.ctr->err);
+                continue;
+            }
+            bm_zero = false;
             const bool r_staged = nr + 4 <= kBlockRCap;
-            if (r_staged) {
-                stage<BT>(r4, 0, nr, rbuf, tid, I.r_n_chunks - dr.x, (kBlockRCap + 16) / 4, &a.ctr->err);
+            const uint64_t rlim = I.r_n_chunks - dr.x;
+            // bulk staging (a.bulk_stage): r by one bulk copy; each candidate's whole s by one bulk
+            // copy into buffer m & 1 (wr / ws), issued while the previous candidate merges
+            const bool bulk = a.bulk_stage && r_staged;
+            uint32_t* sbuf[2] = {wr, ws};
+            // thread 0: stage candidate m's s if it will be merged and fits a buffer
+            auto prefetch = [&](uint32_t m) -> uint32_t {
+                if (m >= bi.n || !in_bounds(bi.c0 + m, I.n_cands, &a.ctr->err)) return 0u;
+                const uint32_t sx = I.cand_ids[bi.c0 + m];
+                if (sx >= I.s_n_sets || (self_join && sx == bi.r)) return 0u;
+                const uint2 dx = I.s_desc[sx];
+                const uint32_t rq = required_overlap(I.sim, I.p, I.den, I.magic, nr, dx.y);
+                if (!emit_all && (nr + dx.y == 0 || rq > min(nr, dx.y))) return 0u;
+                if (dx.y == 0 || dx.y + 4 > kBlockWin + 16) return 0u;
+                bulk_stage(sbuf[m & 1], I.s_toks4 + dx.x, 0u, (dx.y + 3) >> 2, I.s_n_chunks - dx.x,
+                           (kBlockWin + 16) / 4, &bsm.bar[1 + (m & 1)], &a.ctr->err);
+                return 1u;
+            };
+            if (bulk) {
+                if (tid == 0) {
+                    bulk_stage(rbuf, r4, 0u, (nr + 3) >> 2, rlim, (kBlockRCap + 16) / 4, &bsm.bar[0], &a.ctr->err);
+                    bsm.staged[0] = prefetch(0);
+                    bsm.staged[1] = 0u;
+                    bsm.ok = mbar_wait(&bsm.bar[0], r_phase, &a.ctr->err) ? 1u : 0u;
+                    if (!bsm.ok && bsm.staged[0]) mbar_wait(&bsm.bar[1], ph[0], &a.ctr->err);  // own copy in flight
+                }
+                r_phase ^= 1u;
+                __syncthreads();
+                if (!bsm.ok) return;  // (uniform) a copy did not complete: reported, the CTA stops
+            } else if (r_staged) {
+                stage<BT>(r4, 0, nr, rbuf, tid, rlim, (kBlockRCap + 16) / 4, &a.ctr->err);
                 __syncthreads();
             }
             for (uint32_t m = 0; m < bi.n; ++m) {
+                bool s_whole = false;
+                if (bulk) {
+                    // candidate m - 1 is merged (its buffer is free again); stage m + 1 into it
+                    s_whole = bsm.staged[m & 1] != 0;
+                    __syncthreads();
+                    if (tid == 0) {
+                        bsm.staged[(m + 1) & 1] = prefetch(m + 1);
+                        if (s_whole) {
+                            bsm.ok = mbar_wait(&bsm.bar[1 + (m & 1)], ph[m & 1], &a.ctr->err) ? 1u : 0u;
+                            bsm.staged[m & 1] = 0u;  // consumed
+                            if (!bsm.ok && bsm.staged[(m + 1) & 1])  // own copy in flight
+                                mbar_wait(&bsm.bar[1 + ((m + 1) & 1)], ph[(m + 1) & 1], &a.ctr->err);
+                        }
+                    }
+                    if (s_whole) ph[m & 1] ^= 1u;
+                    __syncthreads();
+                    if (s_whole && !bsm.ok) return;  // (uniform) reported, the CTA stops
+                }
                 if (!in_bounds(bi.c0 + m, I.n_cands, &a.ctr->err)) break;
                 const uint32_t s = I.cand_ids[bi.c0 + m];
                 if (s >= I.s_n_sets) {
@@ -884,8 +1274,8 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 const uint32_t req = required_overlap(I.sim, I.p, I.den, I.magic, nr, ns);
                 if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
                 bool rej;
-                const uint32_t o = block_merge<BT>(r4, nr, I.s_toks4 + ds.x, ns, req, early, rbuf, r_staged, wr, ws,
-                                                   &bsm, &rej
+                const uint32_t o = block_merge<BT>(r4, nr, I.s_toks4 + ds.x, ns, req, early, rbuf, r_staged, wr,
+                                                   bulk ? sbuf[m & 1] : ws, s_whole, &bsm, &rej
                                                    CHK_ARGS(I.r_n_chunks - dr.x, I.s_n_chunks - ds.x, &a.ctr->err));
                 const bool pass = emit_all || (!rej && o >= req);
                 if (pass && tid == 0) {
@@ -894,6 +1284,18 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 }
             }
             __syncthreads();  // rbuf reuse
+            if (bulk) {
+                // a copy issued for a candidate the loop did not reach (it stopped at a bad index
+                // of the checked build): wait for it so the barrier phases stay in step
+                const uint32_t left0 = bsm.staged[0], left1 = bsm.staged[1];
+                if (tid == 0) {
+                    if (left0) mbar_wait(&bsm.bar[1], ph[0], &a.ctr->err);
+                    if (left1) mbar_wait(&bsm.bar[2], ph[1], &a.ctr->err);
+                }
+                if (left0) ph[0] ^= 1u;
+                if (left1) ph[1] ^= 1u;
+                __syncthreads();
+            }
         }
     }
 
@@ -902,6 +1304,13 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
         WarpOut wout;
         uint32_t* abuf = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem) + warp * kWarpSliceBytes);
         uint32_t* bbuf = abuf + kWarpABuf;
+        // bulk staging: the warp's own barrier (phase parity wph, warp-uniform)
+        uint64_t* wbar = a.bulk_stage ? &s_wbar[warp] : nullptr;
+        uint32_t wph = 0;
+        if (wbar) {
+            if (lane == 0) mbar_init(wbar, 1);
+            __syncwarp();
+        }
         for (uint32_t round = 0;; ++round) {
             uint32_t it = 0;
             if (lane == 0) {
@@ -921,7 +1330,16 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
             const uint32_t nr = dr.y;
             const uint4* r4 = I.r_toks4 + dr.x;
             const bool r_staged = nr + 4 <= kWarpRCap;
-            if (r_staged) {
+            if (r_staged && wbar) {  // r by one bulk copy, lane 0 waits
+                uint32_t ok = 1;
+                if (lane == 0) {
+                    bulk_stage(abuf, r4, 0u, (nr + 3) >> 2, I.r_n_chunks - dr.x, kWarpABuf / 4, wbar, &a.ctr->err);
+                    ok = mbar_wait(wbar, wph, &a.ctr->err) ? 1u : 0u;
+                }
+                wph ^= 1u;
+                if (!__shfl_sync(kFull, ok, 0)) return;  // reported; the warp stops
+                __syncwarp();
+            } else if (r_staged) {
                 stage<32>(r4, 0, nr, abuf, lane, I.r_n_chunks - dr.x, kWarpABuf / 4, &a.ctr->err);
                 __syncwarp();
             }
@@ -942,10 +1360,12 @@ __global__ void __launch_bounds__(BT, MINB) verify_kernel(VerifyArgs a) {
                 const uint32_t ns = ds.y;
                 const uint32_t req = required_overlap(I.sim, I.p, I.den, I.magic, nr, ns);
                 if (!emit_all && (nr + ns == 0 || req > min(nr, ns))) continue;  // length filter
-                bool rej;
+                bool rej, failed;
                 const uint32_t o =
-                    warp_merge(r4, nr, I.s_toks4 + ds.x, ns, req, early, r_staged, abuf, bbuf, lane,
+                    warp_merge(r4, nr, I.s_toks4 + ds.x, ns, req, early, r_staged, abuf, bbuf, lane, wbar, &wph,
+                               I.s_n_chunks - ds.x, &a.ctr->err, &failed,
                                &rej CHK_ARGS(I.r_n_chunks - dr.x, I.s_n_chunks - ds.x, &a.ctr->err));
+                if (failed) return;  // (warp-uniform) reported; the warp stops
                 const bool pass = emit_all || (!rej && o >= req);
                 if (pass) {
                     if (flags & VF_COUNT_ONLY) {
@@ -1104,13 +1524,18 @@ static uint64_t item_cap(uint64_t n_probes, uint64_t n_cands, uint32_t per_item)
 // number of dynamic-scheduling atomics.  (Estimates: 32 resident warps and
 // 4 resident CTAs per SM.)
 static void item_sizes(uint64_t n_cands, int num_sms, uint32_t* per_warp_item, uint32_t* per_block_item,
-                       uint32_t* per_lane_item) {
+                       uint32_t* per_lane_item, uint32_t* per_index_item) {
     const uint64_t warps = 32ull * (uint64_t)num_sms, ctas = 4ull * (uint64_t)num_sms;
     uint64_t w = n_cands / (64 * warps), b = n_cands / (64 * ctas), l = n_cands / (8 * warps);
     *per_warp_item = (uint32_t)(w < 1 ? 1 : (w > kWarpItemCands ? kWarpItemCands : w));
     *per_block_item = (uint32_t)(b < 1 ? 1 : (b > kBlockItemCands ? kBlockItemCands : b));
     l = l < 32 ? 32 : (l > kLaneItemCands ? kLaneItemCands : l);
     *per_lane_item = (uint32_t)(l & ~31ull);
+    // index items: a few per CTA of the wave, at least one block's worth of candidates (never
+    // fewer than a block item, so the block list's capacity covers them)
+    uint64_t x = n_cands / (4 * ctas);
+    x = x < 512 ? 512 : (x > kIndexItemCands ? kIndexItemCands : x);
+    *per_index_item = (uint32_t)(x < *per_block_item ? *per_block_item : x);
 }
 
 static uint64_t pair_cap(const LaunchShape& sh) { return sh.total_cands + 32ull * sh.n_tiles + 32; }
@@ -1125,8 +1550,8 @@ LaunchShape single_shape(uint32_t n_probes, uint64_t n_cands) {
 }
 
 size_t workspace_bytes(const LaunchShape& sh, int num_sms) {
-    uint32_t wc, bc, lc;
-    item_sizes(sh.total_cands, num_sms, &wc, &bc, &lc);
+    uint32_t wc, bc, lc, ic;
+    item_sizes(sh.total_cands, num_sms, &wc, &bc, &lc, &ic);
     const uint64_t slots = 32ull * sh.n_tiles + 1, pc = pair_cap(sh);
     return align256(sizeof(Counters)) + align256(sizeof(Instance) * ((size_t)sh.n_inst + 1)) +
            align256(sizeof(uint2) * slots) + align256(sizeof(uint32_t) * slots) +
@@ -1141,7 +1566,8 @@ size_t workspace_bytes(uint32_t n_probes, uint64_t n_cands, int num_sms) {
 
 void bind_workspace(VerifyArgs& a, void* ws, const LaunchShape& sh, int num_sms) {
     char* p = static_cast<char*>(ws);
-    item_sizes(sh.total_cands, num_sms, &a.warp_item_cands, &a.block_item_cands, &a.lane_item_cands);
+    item_sizes(sh.total_cands, num_sms, &a.warp_item_cands, &a.block_item_cands, &a.lane_item_cands,
+               &a.index_item_cands);
     const uint64_t slots = 32ull * sh.n_tiles + 1;
     a.n_inst = sh.n_inst;
     a.n_tiles = sh.n_tiles;
@@ -1171,35 +1597,53 @@ void bind_workspace(VerifyArgs& a, void* ws, uint32_t n_probes, uint64_t n_cands
     bind_workspace(a, ws, single_shape(n_probes, n_cands), num_sms);
 }
 
+// Dynamic shared memory of the verify kernel: the largest of the block
+// phase's buffers, the per-warp slices of phases 2 and 3, and the index
+// items' probe bitmap (index_words words; it overlaps the others).
 template <int BT>
-static size_t verify_smem_bytes() {
+static size_t verify_smem_bytes(uint32_t index_words) {
     constexpr uint32_t kBlockWin = BT * kBlockD;
     const size_t block_phase = sizeof(uint32_t) * (kBlockRCap + 16 + 2 * (kBlockWin + 16));
     const size_t warp_phases = (size_t)(BT / 32) * kWarpSliceBytes;
-    return block_phase > warp_phases ? block_phase : warp_phases;
+    // index items: the bitmap, then each thread's block ring, then each warp's candidate queue
+    const size_t bitmap = index_words ? sizeof(uint32_t) * (size_t)index_words +
+                                            sizeof(uint4) * ((size_t)BT * kIndexRing + (size_t)(BT / 32) * kIndexQueue)
+                                      : 0;
+    size_t m = block_phase > warp_phases ? block_phase : warp_phases;
+    return bitmap > m ? bitmap : m;
 }
 
-// CTAs per SM of the persistent kernel, per device (the attribute and the
-// occupancy query run once per device and variant).
+// CTAs per SM of the persistent kernel for a dynamic shared-memory size, per
+// device: the size attribute is raised once per device and variant to the
+// largest size any launch uses, the occupancy query runs once per size
+// (sizes come in 4 KiB steps above the fixed part).
 template <int BT, int MINB>
-static cudaError_t resident_ctas(int* per_sm) {
+static cudaError_t resident_ctas(size_t smem, int* per_sm) {
     constexpr int kMaxDev = 64;
-    static std::atomic<int> cache[kMaxDev];
+    constexpr int kSteps = 64;
+    static std::atomic<int> attr_set[kMaxDev];
+    static std::atomic<int> cache[kMaxDev][kSteps];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < kMaxDev && cache[dev].load() > 0) {
-        *per_sm = cache[dev].load();
+    const size_t base = verify_smem_bytes<BT>(0);
+    const size_t step = smem > base ? (smem - base + 4095) / 4096 : 0;
+    const bool cacheable = dev >= 0 && dev < kMaxDev && step < (size_t)kSteps;
+    if (cacheable && cache[dev][step].load() > 0) {
+        *per_sm = cache[dev][step].load();
         return cudaSuccess;
     }
-    const size_t smem = verify_smem_bytes<BT>();
-    e = cudaFuncSetAttribute(verify_kernel<BT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (!(dev >= 0 && dev < kMaxDev && attr_set[dev].load())) {
+        const size_t most = verify_smem_bytes<BT>(kIndexMaxWords);
+        e = cudaFuncSetAttribute(verify_kernel<BT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < kMaxDev) attr_set[dev].store(1);
+    }
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, verify_kernel<BT, MINB>, BT, smem);
     if (e != cudaSuccess) return e;
     if (n < 1) n = 1;
-    if (dev >= 0 && dev < kMaxDev) cache[dev].store(n);
+    if (cacheable) cache[dev][step].store(n);
     *per_sm = n;
     return cudaSuccess;
 }
@@ -1207,19 +1651,40 @@ static cudaError_t resident_ctas(int* per_sm) {
 template <int BT, int MINB>
 static cudaError_t launch_bt(const VerifyArgs& a, cudaStream_t st, int num_sms) {
     int per_sm = 0;
-    cudaError_t e = resident_ctas<BT, MINB>(&per_sm);
+    const size_t smem = verify_smem_bytes<BT>(a.index_words);
+    cudaError_t e = resident_ctas<BT, MINB>(smem, &per_sm);
     if (e != cudaSuccess) return e;
-    verify_kernel<BT, MINB><<<num_sms * per_sm, BT, verify_smem_bytes<BT>(), st>>>(a);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(num_sms * per_sm));
+    cfg.blockDim = dim3(BT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (a.l2_base && a.l2_bytes) {
+        // the collection's tokens persist in the L2 set-aside during this launch
+        memset(attr, 0, sizeof(attr));
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow.base_ptr = const_cast<void*>(a.l2_base);
+        attr[0].val.accessPolicyWindow.num_bytes = a.l2_bytes;
+        attr[0].val.accessPolicyWindow.hitRatio = a.l2_hit_ratio;
+        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    e = cudaLaunchKernelEx(&cfg, verify_kernel<BT, MINB>, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 // block_threads: 128, 256 or 512, optionally | kWideRegisters (the variant
 // budgeted for three quarters of the CTAs per SM, with more registers per
-// thread).
+// thread) and | kBulkStaging (a launch argument, not a variant).
 template <class F>
 static cudaError_t dispatch_variant(uint32_t block_threads, F&& f) {
     const bool wide = (block_threads & kWideRegisters) != 0;
-    switch (block_threads & ~kWideRegisters) {
+    switch (block_threads & ~(kWideRegisters | kBulkStaging)) {
         case 128: return wide ? f.template operator()<128, 6>() : f.template operator()<128, 8>();
         case 512: return wide ? f.template operator()<512, 1>() : f.template operator()<512, 2>();
         default: return wide ? f.template operator()<256, 3>() : f.template operator()<256, 4>();
@@ -1227,10 +1692,11 @@ static cudaError_t dispatch_variant(uint32_t block_threads, F&& f) {
 }
 
 struct PrepareVariant {
+    uint32_t index_words;
     template <int BT, int MINB>
     cudaError_t operator()() const {
         int per_sm = 0;
-        return resident_ctas<BT, MINB>(&per_sm);
+        return resident_ctas<BT, MINB>(verify_smem_bytes<BT>(index_words), &per_sm);
     }
 };
 
@@ -1244,7 +1710,9 @@ struct LaunchVariant {
     }
 };
 
-cudaError_t prepare_verify(uint32_t block_threads) { return dispatch_variant(block_threads, PrepareVariant{}); }
+cudaError_t prepare_verify(uint32_t block_threads, uint32_t index_words) {
+    return dispatch_variant(block_threads, PrepareVariant{index_words});
+}
 
 cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uint32_t block_threads,
                           cudaEvent_t* ev) {
@@ -1260,7 +1728,7 @@ cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uin
     }
     // the plan kernel also runs for empty batches: it clears the instances' counts
     {
-        // one round of tiles per CTA and round (kPlanThreads / 32 tiles), one wave of CTAs
+        // at most one wave of CTAs; a CTA takes up to kPlanThreads / 32 tiles per round
         static int plan_ctas_per_sm = 0;  // resident CTAs per SM (same value from every thread)
         if (plan_ctas_per_sm == 0) {
             int n = 0;
@@ -1268,8 +1736,10 @@ cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uin
                 n = 4;
             plan_ctas_per_sm = n;
         }
+        // one tile per CTA while tiles are fewer than a wave of CTAs (a tile's candidates are copied
+        // by the whole CTA, so few tiles still fill the GPU), else a wave with several tiles each
         const int threads = kPlanThreads;
-        uint64_t blocks = ((uint64_t)a.n_tiles * 32 + threads - 1) / threads;
+        uint64_t blocks = a.n_tiles;
         const uint64_t max_blocks = (uint64_t)num_sms * (uint64_t)plan_ctas_per_sm;
         if (blocks > max_blocks) blocks = max_blocks;
         if (blocks < 1) blocks = 1;
@@ -1278,7 +1748,9 @@ cudaError_t launch_verify(const VerifyArgs& a, cudaStream_t st, int num_sms, uin
         if (e != cudaSuccess) return e;
     }
     if (ev) cudaEventRecord(ev[1], st);
-    e = dispatch_variant(block_threads, LaunchVariant{a, st, num_sms});
+    VerifyArgs va = a;
+    va.bulk_stage = (block_threads & kBulkStaging) ? 1u : 0u;
+    e = dispatch_variant(block_threads, LaunchVariant{va, st, num_sms});
     if (ev) cudaEventRecord(ev[2], st);
     return e;
 }

@@ -80,7 +80,8 @@ def test_self_join_raw_tokens_count_only_device_and_sorted(ctx):
         with pytest.raises(ssj.SsjError) as ei:
             ssj.ssj_self_join(ctx, h, 3, 5, 0, cap=max(len(want) - 1, 1))
         assert ei.value.status == ssj.SSJ_ENOMEM
-        for gran in (ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_LANE, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK):
+        for gran in (ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_LANE, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK,
+                     ssj.SSJ_FORCE_INDEX):
             g, _ = ssj.ssj_self_join(ctx, h, 3, 5, gran)
             assert np.array_equal(ssj.triples_to_array(g), want), gran
     finally:

@@ -21,7 +21,8 @@ spec = synth.long_sets(n=600)
 spec.plant_frac, spec.plant_edits = 0.3, 10
 c = synth.collection(spec)
 h = ssj.ssj_load_collection(ctx, c.offsets, c.tokens)
-for gran in (0, ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_LANE, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK):
+for gran in (0, ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_LANE, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK,
+             ssj.SSJ_FORCE_INDEX):
     pr, co, ci = ssj.feeder_all(c.offsets, c.tokens, 3, 5, n_threads=4)
     got = ssj.triples_to_array(ssj.ssj_verify_batch(ctx, h, h, 3, 5, pr, co, ci, flags=gran))
     want = oracle.sort_triples(oracle.allpairs_self(c.offsets, c.tokens, 3, 5)[0])

@@ -15,7 +15,8 @@ from paper_1812_09141_gb300 import _build
 
 pytestmark = pytest.mark.gpu
 
-GRANULARITIES = [0, ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_LANE, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK]
+GRANULARITIES = [0, ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_LANE, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK,
+                 ssj.SSJ_FORCE_INDEX]
 T_ALL = [(19, 20), (9, 10), (17, 20), (4, 5), (3, 4), (7, 10), (13, 20), (3, 5)]
 
 
@@ -231,6 +232,116 @@ def test_set_tails_and_extreme_token_values(ctx):
             assert np.array_equal(gpu(ctx, h, h, 1, 2, b, ssj.SSJ_EMIT_ALL | gran), every), gran
     finally:
         ssj.ssj_unload_collection(ctx, h)
+
+
+def test_index_items_where_token_values_fit(ctx):
+    """Index items hold the probe as a bitmap over token values, so they run only where every
+    token value of the launch fits the bitmap: renumbered collections, or collections whose raw
+    values are small.  Each workload here fits; it is checked with SSJ_FORCE_INDEX, with index
+    items chosen by the candidate threshold (every probe: threshold 1), and with SSJ_EMIT_ALL
+    (every overlap), against the oracle: planted all-pairs and long-set collections renumbered,
+    empty / one-token / long edge sets and every tail shape with small raw values, and R x S
+    batches between two collections of small raw values."""
+    rng = np.random.default_rng(21)
+    work = []
+    c = planted_tiny(n=900)
+    work.append((c, c, True, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ, synth.all_pairs_batch(c.n),
+                 [(4, 5), (3, 5), (1, 10)]))
+    spec = synth.long_sets(n=1500)
+    spec.plant_frac, spec.plant_edits = 0.3, 20
+    c = synth.collection(spec)
+    work.append((c, c, True, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ, feeder_batch(c, 3, 5), [(3, 5), (4, 5)]))
+    sets = [[], [7], [7], [1, 2, 3], [1, 2, 3], list(range(0, 6000, 2)), list(range(0, 6000, 2)),
+            list(range(0, 5000, 2)) + [5001], list(range(1, 4000, 3)), list(range(100, 400)),
+            list(range(100, 399)) + [1000], [0], [0, 1], [31, 32], [31], [32, 33, 63, 64, 65]]
+    for n in range(1, 14):
+        base = np.sort(rng.choice(40, size=n, replace=False)).tolist()
+        sets.append(base)
+        sets.append(sorted(set(base[:-1] + [60_000 - n])))
+        sets.append(sorted(set(base + [base[-1] + 1])) if base[-1] + 1 < 40 else base[:-1] + [41])
+    for k in (31, 33, 127, 129, 1023, 1025, 4093):
+        base = np.sort(rng.choice(20_000, size=k, replace=False))
+        other = base.copy()
+        other[rng.integers(0, k)] = 20_001 + k
+        sets.append(base.tolist())
+        sets.append(np.unique(other).tolist())
+    c = synth.from_lists(sets)
+    work.append((c, c, True, ssj.SSJ_VALIDATE, synth.all_pairs_batch(c.n), [(1, 1), (9, 10), (1, 2), (1, 100)]))
+    small = lambda n, seed: synth.from_lists(
+        [np.unique(np.random.default_rng(seed + i).integers(0, 3000, size=int(k))).tolist()
+         for i, k in enumerate(np.random.default_rng(seed).integers(1, 120, size=n))])
+    cR, cS = small(400, 1000), small(300, 5000)
+    work.append((cR, cS, False, ssj.SSJ_VALIDATE, synth.random_batch(9, cR.n, cS.n, 2000, 60),
+                 [(1, 10), (1, 3), (3, 5)]))
+    for cR, cS, selfj, lf, b, ths in work:
+        hR = load(ctx, cR, lf)
+        hS = hR if selfj else load(ctx, cS, lf)
+        try:
+            for p, q in ths:
+                want = ora(cR, cS, selfj, p, q, b)
+                assert np.array_equal(gpu(ctx, hR, hS, p, q, b, ssj.SSJ_FORCE_INDEX), want), (p, q)
+                ssj.ssj_set_index_items(ctx, 1)
+                try:
+                    assert np.array_equal(gpu(ctx, hR, hS, p, q, b), want), (p, q)
+                finally:
+                    ssj.ssj_set_index_items(ctx, 256)
+            p, q = ths[0]
+            every = ora(cR, cS, selfj, p, q, b, flags=oracle.EMIT_ALL)
+            assert np.array_equal(gpu(ctx, hR, hS, p, q, b, ssj.SSJ_FORCE_INDEX | ssj.SSJ_EMIT_ALL), every)
+            assert ssj.ssj_device_error(ctx) == 0
+        finally:
+            ssj.ssj_unload_collection(ctx, hR)
+            if not selfj:
+                ssj.ssj_unload_collection(ctx, hS)
+
+
+@pytest.mark.parametrize("bt", [256 | ssj.SSJ_BULK_STAGING, 512 | ssj.SSJ_BULK_STAGING,
+                                128 | ssj.SSJ_WIDE_REGISTERS | ssj.SSJ_BULK_STAGING])
+def test_bulk_staging_block_and_warp_items(ctx, bt):
+    """Thread-block and warp items with their sets staged by bulk copies (SSJ_BULK_STAGING): long
+    sets (raw and renumbered) at two thresholds, every overlap (SSJ_EMIT_ALL), and edge sets whose
+    lengths straddle the whole-set buffers (sets of up to 6,000 tokens take the windowed path),
+    against the oracle."""
+    ssj.ssj_set_granularity(ctx, 0, 0, 0, bt)
+    try:
+        spec = synth.long_sets(n=1500)
+        spec.plant_frac, spec.plant_edits = 0.3, 20
+        c = synth.collection(spec)
+        for lf in (ssj.SSJ_VALIDATE, ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ):
+            h = load(ctx, c, lf)
+            for p, q in [(3, 5), (4, 5)]:
+                b = feeder_batch(c, p, q)
+                want = ora(c, c, True, p, q, b)
+                assert len(want) > 0
+                for gran in (ssj.SSJ_FORCE_BLOCK, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_LANE, 0):
+                    assert np.array_equal(gpu(ctx, h, h, p, q, b, gran), want), (lf, p, q, gran)
+            every = ora(c, c, True, 3, 5, b, flags=oracle.EMIT_ALL)
+            for gran in (ssj.SSJ_FORCE_BLOCK, ssj.SSJ_FORCE_WARP):
+                assert np.array_equal(gpu(ctx, h, h, 3, 5, b, gran | ssj.SSJ_EMIT_ALL), every), gran
+            assert ssj.ssj_device_error(ctx) == 0
+            ssj.ssj_unload_collection(ctx, h)
+        rng = np.random.default_rng(31)
+        sets = [[], [7], [7, 9], list(range(0, 6000, 2)), list(range(0, 6000, 2)), list(range(1, 6000, 3))]
+        for k in (1, 3, 4, 5, 255, 256, 257, 1019, 1020, 1021, 2043, 2044, 2045, 2061, 4091, 4092, 4093):
+            base = np.sort(rng.choice(12_000, size=k, replace=False))
+            other = base.copy()
+            other[rng.integers(0, k)] = 12_001 + k
+            sets.append(base.tolist())
+            sets.append(np.unique(other).tolist())
+        c = synth.from_lists(sets)
+        h = load(ctx, c)
+        b = synth.all_pairs_batch(c.n)
+        for p, q in [(1, 1), (9, 10), (1, 3)]:
+            want = oracle.sort_triples(oracle.bruteforce_self(c.offsets, c.tokens, p, q))
+            for gran in (ssj.SSJ_FORCE_BLOCK, ssj.SSJ_FORCE_WARP):
+                assert np.array_equal(gpu(ctx, h, h, p, q, b, gran), want), (p, q, gran)
+        every = ora(c, c, True, 1, 3, b, flags=oracle.EMIT_ALL)
+        for gran in (ssj.SSJ_FORCE_BLOCK, ssj.SSJ_FORCE_WARP):
+            assert np.array_equal(gpu(ctx, h, h, 1, 3, b, gran | ssj.SSJ_EMIT_ALL), every), gran
+        assert ssj.ssj_device_error(ctx) == 0
+        ssj.ssj_unload_collection(ctx, h)
+    finally:
+        ssj.ssj_set_granularity(ctx, 0, 0, 0, 256)
 
 
 def test_empty_and_degenerate_batches(ctx):

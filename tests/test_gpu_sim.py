@@ -13,7 +13,8 @@ from paper_1812_09141_gb300 import _build
 
 pytestmark = pytest.mark.gpu
 
-GRANULARITIES = [0, ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_LANE, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK]
+GRANULARITIES = [0, ssj.SSJ_FORCE_THREAD, ssj.SSJ_FORCE_LANE, ssj.SSJ_FORCE_WARP, ssj.SSJ_FORCE_BLOCK,
+                 ssj.SSJ_FORCE_INDEX]
 SIM_FLAGS = {oracle.DICE: ssj.SSJ_SIM_DICE, oracle.COSINE: ssj.SSJ_SIM_COSINE, oracle.OVERLAP: ssj.SSJ_SIM_OVERLAP}
 THRESHOLDS = {oracle.DICE: [(9, 10), (4, 5), (3, 5)], oracle.COSINE: [(19, 20), (4, 5), (3, 5)],
               oracle.OVERLAP: [(5, 1), (12, 1), (23, 2)]}
