@@ -651,13 +651,6 @@ __device__ __noinline__ void lane_item(const Instance& I, const WorkItem& wi, ui
     }
 }
 
-// Bit of token value x in the probe bitmap (words bm[0, n_words)).
-__device__ __forceinline__ uint32_t bm_bit(const uint32_t* bm, uint32_t x, uint32_t n_words, uint32_t* err) {
-    const uint32_t w = x >> 5;
-    if (!in_bounds(w, n_words, err)) return 0u;
-    return (bm[w] >> (x & 31u)) & 1u;
-}
-
 // Set (or, with clear, zero the words of) the bits of r's tokens; r's
 // padding repeats its last token, so whole blocks are used.
 template <int BT>
@@ -701,17 +694,27 @@ __device__ __forceinline__ void cp_async_wait() {
 // exactly |r n s|.
 //
 // The walk is software-pipelined so that no thread waits on a load it has
-// just issued.  Each warp prepares its candidates 32 at a time: their ids
-// are loaded, kIndexWait iterations later their descriptors, kIndexWait
-// iterations later again the required overlap and the length filter decide
-// which enter the warp's queue (shared memory).  An idle lane takes the next
-// queued candidate; each iteration it asks for one more block of s (cp.async
-// into its own ring of kIndexRing blocks in shared memory, at most
-// kIndexRing blocks ahead of its walk) and merges the block it asked for
-// kIndexWait iterations before.
+// just issued, and its common path is short.  Each warp prepares its
+// candidates 32 at a time: their ids are loaded, one round later their
+// descriptors, one round later again the required overlap and the length
+// filter decide which enter the warp's queue (shared memory).  A round is
+// kIndexSteps walk steps followed by one maintenance step (preparation,
+// survivors out, idle lanes refilled from the queue).  In a walk step a lane
+// asks for one more block of s (cp.async into its own ring of kIndexRing
+// blocks in shared memory, at most kIndexRing blocks ahead of its walk) and
+// merges a block it asked for in an earlier step.
 constexpr uint32_t kIndexRing = 4;   // blocks of s per thread in the ring
 constexpr uint32_t kIndexQueue = 64; // prepared candidates per warp
-constexpr int kIndexWait = 2;        // iterations between a load and its first read
+constexpr int kIndexSteps = 4;       // walk steps per round
+
+// Bit of token value x in the probe bitmap, as one shift-and-mask of the
+// word (the funnel shift takes the shift amount modulo 32).
+__device__ __forceinline__ uint32_t bm_test(const uint32_t* bm, uint32_t x, uint32_t n_words, uint32_t* err) {
+    const uint32_t w = x >> 5;
+    if (!in_bounds(w, n_words, err)) return 0u;
+    const uint32_t word = bm[w];
+    return __funnelshift_r(word, word, x) & 1u;
+}
 
 template <int BT>
 __device__ __noinline__ void index_item(const Instance& I, const WorkItem& wi, uint32_t nr, const uint4* r4,
@@ -730,19 +733,59 @@ __device__ __noinline__ void index_item(const Instance& I, const WorkItem& wi, u
     const uint32_t rmax = nr ? ld_block(r4, (nr - 1) >> 2, rlim, err).w : 0u;
     __syncthreads();
 
-    // candidate preparation (warp-uniform stage machine; stage 0 takes 32 candidates)
-    uint32_t pstage = 0, page = 0, qhead = 0, qtail = 0;  // warp-uniform (queue cursors free-running)
-    bool pdone = false;                                    // warp-uniform: no candidates left to take
+    // candidate preparation (warp-uniform stage: 0 takes 32 candidates, 1 loads descriptors,
+    // 2 filters and queues); queue cursors are free-running
+    uint32_t pstage = 0, qhead = 0, qtail = 0;
+    bool pdone = false;  // warp-uniform: no candidates left to take
     bool p_ok = false;
     uint32_t p_id = 0;
     uint2 p_desc = make_uint2(0u, 0u);
-    // the lane's pair: next block to merge (jb) and to ask for (jr) of its nblk blocks, ring slot of
-    // its block 0 (rb), blocks asked for in the last iterations (hist, one bit per iteration)
-    bool active = false;
-    uint32_t s_id = 0, rems = 0, req = 0, o = 0, jb = 0, jr = 0, nblk = 0, rb = 0, hist = 0;
+    // the lane's pair: next block to merge (jb) and to ask for (jr), ring slot of its block 0
+    // (rb); a finished pair keeps s_id / o until the maintenance step sends it out
+    bool active = false, out = false;
+    uint32_t s_id = 0, rems = 0, req = 0, o = 0, jb = 0, jr = 0, rb = 0;
     const uint4* s4 = nullptr;
     uint64_t slim = 0;
     for (;;) {
+        // ---- walk steps
+#pragma unroll
+        for (int step = 0; step < kIndexSteps; ++step) {
+            const uint32_t avail = jr;      // blocks asked for in earlier steps
+            const uint32_t ahead = jr - jb;  // asked for, not yet merged (rems counts tokens from block jb)
+            if (active && ahead < kIndexRing && 4 * ahead < rems) {
+                if (in_bounds(jr, slim, err)) cp_async16(ring + ((rb + jr) & (kIndexRing - 1)), s4 + jr);
+                ++jr;
+            }
+            cp_async_commit();
+            cp_async_wait<1>();  // every block asked for before this step is in
+            if (active && jb < avail) {
+                const uint4 sc = ring[(rb + jb) & (kIndexRing - 1)];
+                const uint32_t nv = min(rems, 4u);
+                const uint32_t bw = bm_test(bm, sc.w, n_words, err);
+                // the lanes past nv valid tokens repeat the last one (sc.w): subtract them again
+                o += bm_test(bm, sc.x, n_words, err) + bm_test(bm, sc.y, n_words, err) +
+                     bm_test(bm, sc.z, n_words, err) + bw - (4u - nv) * bw;
+                rems -= nv;
+                ++jb;
+                const bool end = rems == 0 || sc.w >= rmax;  // no later token of s can match
+                const bool rej = !end && early && o + rems < req;
+                if (end || rej) {
+                    active = false;
+                    out = emit_all || (!rej && o >= req);
+                }
+            }
+        }
+        // ---- maintenance: survivors out
+        const uint32_t pmask = __ballot_sync(kFull, out);
+        if (pmask) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(I.count, (unsigned long long)__popc(pmask));
+            if (!(flags & VF_COUNT_ONLY)) {
+                b0 = __shfl_sync(kFull, b0, 0);
+                if (out) emit_triple(I.out, I.cap, self_join, b0 + __popc(pmask & lt_mask), wi.r, s_id, o);
+            }
+            out = false;
+        }
         // ---- preparation
         if (pstage == 0) {
             if (!pdone && qtail - qhead + 32 <= kIndexQueue) {
@@ -753,33 +796,27 @@ __device__ __noinline__ void index_item(const Instance& I, const WorkItem& wi, u
                 const uint32_t my = base + (uint32_t)lane;
                 p_ok = my < wi.n && in_bounds(wi.c0 + my, I.n_cands, err);
                 if (p_ok) p_id = I.cand_ids[wi.c0 + my];
-                if (base < wi.n) {
-                    pstage = 1;
-                    page = 0;
-                }
+                if (base < wi.n) pstage = 1;
             }
-        } else if (++page >= (uint32_t)kIndexWait) {
-            page = 0;
-            if (pstage == 1) {
-                if (p_ok && p_id >= I.s_n_sets) {
-                    atomicOr(err, ERR_CAND_ID);
-                    p_ok = false;
-                }
-                if (p_ok && self_join && p_id == wi.r) p_ok = false;
-                if (p_ok) p_desc = I.s_desc[p_id];
-                pstage = 2;
-            } else {
-                uint32_t q = 0;
-                if (p_ok) {
-                    q = required_overlap(I.sim, I.p, I.den, I.magic, nr, p_desc.y);
-                    p_ok = emit_all || (nr + p_desc.y > 0 && q <= min(nr, p_desc.y));  // length filter
-                }
-                const uint32_t m = __ballot_sync(kFull, p_ok);
-                if (p_ok) queue[(qtail + __popc(m & lt_mask)) % kIndexQueue] = make_uint4(p_id, p_desc.x, p_desc.y, q);
-                qtail += __popc(m);
-                pstage = 0;
-                __syncwarp();
+        } else if (pstage == 1) {
+            if (p_ok && p_id >= I.s_n_sets) {
+                atomicOr(err, ERR_CAND_ID);
+                p_ok = false;
             }
+            if (p_ok && self_join && p_id == wi.r) p_ok = false;
+            if (p_ok) p_desc = I.s_desc[p_id];
+            pstage = 2;
+        } else {
+            uint32_t q = 0;
+            if (p_ok) {
+                q = required_overlap(I.sim, I.p, I.den, I.magic, nr, p_desc.y);
+                p_ok = emit_all || (nr + p_desc.y > 0 && q <= min(nr, p_desc.y));  // length filter
+            }
+            const uint32_t m = __ballot_sync(kFull, p_ok);
+            if (p_ok) queue[(qtail + __popc(m & lt_mask)) % kIndexQueue] = make_uint4(p_id, p_desc.x, p_desc.y, q);
+            qtail += __popc(m);
+            pstage = 0;
+            __syncwarp();
         }
         // ---- idle lanes take queued candidates
         const uint32_t idle = __ballot_sync(kFull, !active);
@@ -789,62 +826,24 @@ __device__ __noinline__ void index_item(const Instance& I, const WorkItem& wi, u
             if (!active && rank < k) {
                 const uint4 e = queue[(qhead + rank) % kIndexQueue];
                 rb = (rb + jr) & (kIndexRing - 1);  // continue the lane's ring after its last request
-                active = true;
                 s_id = e.x;
                 rems = e.z;
                 req = e.w;
                 o = 0;
                 jb = 0;
                 jr = 0;
-                hist = 0;
-                nblk = (rems + 3) >> 2;
                 s4 = I.s_toks4 + e.y;
                 slim = I.s_n_chunks - e.y;
+                if (rems == 0 || nr == 0) {
+                    out = emit_all;  // an empty side: overlap 0
+                } else {
+                    active = true;
+                }
             }
             qhead += k;
             __syncwarp();
         }
-        // ---- ask for one more block; merge the one asked for kIndexWait iterations ago
-        uint32_t asked = 0;
-        if (active && jr < nblk && jr < jb + kIndexRing) {
-            if (in_bounds(jr, slim, err)) cp_async16(ring + ((rb + jr) & (kIndexRing - 1)), s4 + jr);
-            ++jr;
-            asked = 1;
-        }
-        cp_async_commit();
-        hist = (hist << 1) | asked;
-        cp_async_wait<kIndexWait>();  // every block asked for before the last kIndexWait iterations is in
-        bool done = false, rej = false;
-        if (active) {
-            const uint32_t landed = jr - __popc(hist & ((1u << kIndexWait) - 1u));
-            if (rems == 0 || nr == 0) {
-                done = true;  // an empty side: overlap 0
-            } else if (jb < landed) {
-                const uint4 sc = ring[(rb + jb) & (kIndexRing - 1)];
-                const uint32_t nv = min(rems, 4u);
-                const uint32_t bw = bm_bit(bm, sc.w, n_words, err);
-                // the lanes past nv valid tokens repeat the last one (sc.w): subtract them again
-                o += bm_bit(bm, sc.x, n_words, err) + bm_bit(bm, sc.y, n_words, err) +
-                     bm_bit(bm, sc.z, n_words, err) + bw - (4u - nv) * bw;
-                rems -= nv;
-                ++jb;
-                done = rems == 0 || sc.w >= rmax;  // no later token of s can match
-                rej = !done && early && o + rems < req;
-                done = done || rej;
-            }
-        }
-        const bool pass = done && (emit_all || (!rej && o >= req));
-        const uint32_t pmask = __ballot_sync(kFull, pass);
-        if (pmask) {
-            unsigned long long b0 = 0;
-            if (lane == 0) b0 = atomicAdd(I.count, (unsigned long long)__popc(pmask));
-            if (!(flags & VF_COUNT_ONLY)) {
-                b0 = __shfl_sync(kFull, b0, 0);
-                if (pass) emit_triple(I.out, I.cap, self_join, b0 + __popc(pmask & lt_mask), wi.r, s_id, o);
-            }
-        }
-        if (done) active = false;
-        if (pdone && pstage == 0 && qhead == qtail && !__any_sync(kFull, active)) break;
+        if (pdone && pstage == 0 && qhead == qtail && !__any_sync(kFull, active || out)) break;
     }
     cp_async_wait<0>();  // the ring's last copies (asked for past a pair's end) are in
     __syncthreads();     // every thread is done with the bitmap

@@ -239,10 +239,11 @@ def test_autotuned_launch_matches_oracle(ctx):
     rep = []
     res = _run_multi(ctx, cases, graph_reps=1, tune=rep)
     (t,) = rep
-    assert t["block_threads"] & ~ssj.SSJ_WIDE_REGISTERS in (128, 256, 512)
+    assert t["block_threads"] & ~(ssj.SSJ_WIDE_REGISTERS | ssj.SSJ_BULK_STAGING) in (128, 256, 512)
     assert t["thread_max_key"] in (32, 64, 128, 256, 512, 1024, 2048, 4096)
     assert t["warp_max_key"] >= t["thread_max_key"]
     assert t["drain_min_live"] in (8, 12, 16, 20, 24)
+    assert t["index_min_cands"] in (0, 32, 64, 128, 256, 512, 1024, 4096)
     assert t["settings_tried"] >= 3 and 0 < t["best_ms"] <= t["initial_ms"]
     for r in res:
         for i, (got, w) in enumerate(zip(r, wants)):
