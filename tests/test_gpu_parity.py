@@ -531,6 +531,18 @@ def test_full_long_sets_exact(ctx):
     b = feeder_batch(c, 3, 5, threads=16)
     want = _exact_against_threaded_oracle(ctx, c, h, 3, 5, b)
     assert len(want) > 500
+    # the same candidates as three host batches in one ssj_verify_batches call: large enough that
+    # the call runs two launches, the second group's copies overlapping the first group's kernels
+    co = b.cand_offsets.astype(np.int64)
+    cuts = [0, b.n_probes // 5, b.n_probes // 2, b.n_probes]
+    parts = []
+    for a, z in zip(cuts[:-1], cuts[1:]):
+        parts.append((h, h, 3, 5, b.probe_ids[a:z], (co[a:z + 1] - co[a]).astype(np.uint64),
+                      b.cand_ids[co[a]:co[z]], 0))
+    res = ssj.ssj_verify_batches(ctx, parts, caps=[len(want) + 16] * 3)
+    got = ssj.triples_to_array(np.concatenate(res))
+    assert np.array_equal(got, want)
+    assert ssj.ssj_device_error(ctx) == 0
     ssj.ssj_unload_collection(ctx, h)
 
 
