@@ -438,7 +438,7 @@ def run_ours(args, rank, world, local_rank):
     ctx = ssj.ssj_create(local_rank, flags=ssj.SSJ_CTX_PROFILE, stream=stream.cuda_stream)
     # renumbering by frequency is for self-joins; an R x S join keeps the raw token order
     rs_join = any(isinstance(k, tuple) for k, _, _ in inst)
-    load_flags = ssj.SSJ_VALIDATE | (0 if rs_join else ssj.SSJ_RENUMBER_BY_FREQ)
+    load_flags = ssj.SSJ_VALIDATE | (0 if rs_join else ssj.SSJ_RENUMBER_BY_FREQ) | (ssj.SSJ_PIN_L2 if args.pin_l2 else 0)
     handles = [ssj.ssj_load_collection(ctx, c.offsets, c.tokens, load_flags) for c in colls]
 
     def hpair(k):
@@ -846,6 +846,8 @@ def main():
     ap.add_argument("--ppjoin", action="store_true", help="PPJoin positional filter in the CPU feeder")
     ap.add_argument("--granularity", default="", help="thread,lane,warp,block_threads[,drain_min_live[,index_min_cands]]: "
                     "fixed setting instead of the autotuner's (profiling runs)")
+    ap.add_argument("--pin-l2", action="store_true",
+                    help="load the collections with SSJ_PIN_L2 (persisting-L2 window over the token array)")
     ap.add_argument("--instances", type=int, default=0,
                     help="uneven_instances: verify only the first N instances (profiling runs on a smaller case)")
     args = ap.parse_args()
@@ -897,7 +899,8 @@ def main():
                                  if args.l2_flush_mb else "not flushed (profiling run)"),
             "parallelism": (f"{world} ranks, each a contiguous probe range of every batch" if world > 1
                             else "single GPU"),
-            "device_input_bytes": int(input_bytes), "inputs_fit_l2": bool(input_bytes < 129e6)}
+            "device_input_bytes": int(input_bytes), "inputs_fit_l2": bool(input_bytes < 129e6),
+            "l2_pinned": bool(args.pin_l2)}
     sm = sorted(res["step_ms"])
     line["latency_ms"] = {"p50": float(np.percentile(sm, 50)), "p99": float(np.percentile(sm, 99)),
                           "per": "one batched launch (every instance of the step), device time"}

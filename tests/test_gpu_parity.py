@@ -344,6 +344,41 @@ def test_bulk_staging_block_and_warp_items(ctx, bt):
         ssj.ssj_set_granularity(ctx, 0, 0, 0, 256)
 
 
+def test_pinned_collections_match_oracle():
+    """Collections loaded with SSJ_PIN_L2 (the context's persisting-L2 set-aside raised, a
+    persisting window on every launch that reads them) give the oracle's join through the
+    synchronous call and a batched launch; unloading the pinned collections restores the
+    set-aside and the context keeps working."""
+    import torch
+    pctx = ssj.ssj_create(0)
+    try:
+        spec = synth.long_sets(n=3000)
+        spec.plant_frac, spec.plant_edits = 0.3, 20
+        cl = synth.collection(spec)
+        cs = synth.collection(synth.short_sets(n=30_000))
+        fl = ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ | ssj.SSJ_PIN_L2
+        hl, hs = load(pctx, cl, fl), load(pctx, cs, fl)
+        bl, bs = feeder_batch(cl, 3, 5), feeder_batch(cs, 7, 10)
+        wl = oracle.sort_triples(oracle.allpairs_self(cl.offsets, cl.tokens, 3, 5)[0])
+        ws = oracle.sort_triples(oracle.allpairs_self(cs.offsets, cs.tokens, 7, 10)[0])
+        assert len(wl) > 0 and len(ws) > 0
+        for gran in (0, ssj.SSJ_FORCE_INDEX, ssj.SSJ_FORCE_THREAD):
+            assert np.array_equal(gpu(pctx, hl, hl, 3, 5, bl, gran), wl), gran
+            assert np.array_equal(gpu(pctx, hs, hs, 7, 10, bs, gran), ws), gran
+        res = ssj.ssj_verify_batches(pctx, [(hl, hl, 3, 5, bl.probe_ids, bl.cand_offsets, bl.cand_ids, 0),
+                                            (hs, hs, 7, 10, bs.probe_ids, bs.cand_offsets, bs.cand_ids, 0)])
+        assert np.array_equal(ssj.triples_to_array(res[0]), wl)
+        assert np.array_equal(ssj.triples_to_array(res[1]), ws)
+        assert ssj.ssj_device_error(pctx) == 0
+        ssj.ssj_unload_collection(pctx, hl)
+        ssj.ssj_unload_collection(pctx, hs)
+        h2 = load(pctx, cs)  # not pinned, after the set-aside was restored
+        assert np.array_equal(gpu(pctx, h2, h2, 7, 10, bs), ws)
+        torch.cuda.synchronize()
+    finally:
+        ssj.ssj_destroy(pctx)
+
+
 def test_empty_and_degenerate_batches(ctx):
     c = planted_tiny(n=50)
     h = load(ctx, c)
