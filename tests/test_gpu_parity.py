@@ -355,7 +355,9 @@ def test_pinned_collections_match_oracle():
         spec = synth.long_sets(n=3000)
         spec.plant_frac, spec.plant_edits = 0.3, 20
         cl = synth.collection(spec)
-        cs = synth.collection(synth.short_sets(n=30_000))
+        spec_s = synth.short_sets(n=30_000)
+        spec_s.plant_frac, spec_s.plant_edits = 0.2, 2
+        cs = synth.collection(spec_s)
         fl = ssj.SSJ_VALIDATE | ssj.SSJ_RENUMBER_BY_FREQ | ssj.SSJ_PIN_L2
         hl, hs = load(pctx, cl, fl), load(pctx, cs, fl)
         bl, bs = feeder_batch(cl, 3, 5), feeder_batch(cs, 7, 10)
