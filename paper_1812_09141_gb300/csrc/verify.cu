@@ -760,18 +760,21 @@ __device__ __noinline__ void index_item(const Instance& I, const WorkItem& wi, u
             cp_async_wait<1>();  // every block asked for before this step is in
             if (active && jb < avail) {
                 const uint4 sc = ring[(rb + jb) & (kIndexRing - 1)];
-                const uint32_t nv = min(rems, 4u);
                 const uint32_t bw = bm_test(bm, sc.w, n_words, err);
-                // the lanes past nv valid tokens repeat the last one (sc.w): subtract them again
                 o += bm_test(bm, sc.x, n_words, err) + bm_test(bm, sc.y, n_words, err) +
-                     bm_test(bm, sc.z, n_words, err) + bw - (4u - nv) * bw;
-                rems -= nv;
+                     bm_test(bm, sc.z, n_words, err) + bw;
                 ++jb;
-                const bool end = rems == 0 || sc.w >= rmax;  // no later token of s can match
-                const bool rej = !end && early && o + rems < req;
-                if (end || rej) {
+                if (rems <= 4 || sc.w >= rmax) {  // s's last block, or no later token of s can match
+                    if (rems < 4) o -= (4u - rems) * bw;  // the lanes past s's end repeat its last token
+                    rems = 0;
                     active = false;
-                    out = emit_all || (!rej && o >= req);
+                    out = emit_all || o >= req;
+                } else {
+                    rems -= 4;
+                    if (early && o + rems < req) {
+                        active = false;
+                        out = emit_all;
+                    }
                 }
             }
         }
