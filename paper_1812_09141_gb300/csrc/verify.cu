@@ -727,19 +727,32 @@ __device__ __noinline__ void index_item(const Instance& I, const WorkItem& wi, u
     const bool self_join = (flags & VF_SELF_JOIN) != 0;
     uint4* ring = rings + (size_t)tid * kIndexRing;
     uint4* queue = queues + (size_t)warp * kIndexQueue;
-    if (tid == 0) sm->next = 0;
+    // candidate preparation (warp-uniform stage: 0 takes 32 candidates, 1 loads descriptors,
+    // 2 filters and queues); queue cursors are free-running.  Warp w's first batch is
+    // candidates [32w, 32w + 32): its ids and descriptors are loaded while r's bits are set,
+    // so the walk starts one round after the item does; later batches are taken from the
+    // item's cursor, which starts after the first batches.
+    uint32_t pstage = 0, qhead = 0, qtail = 0;
+    bool pdone = 32u * (BT / 32) >= wi.n;  // warp-uniform: no candidates left to take
+    const uint32_t my0 = 32u * (uint32_t)warp + (uint32_t)lane;
+    bool p_ok = my0 < wi.n && in_bounds(wi.c0 + my0, I.n_cands, err);
+    uint32_t p_id = p_ok ? I.cand_ids[wi.c0 + my0] : 0u;
+    uint2 p_desc = make_uint2(0u, 0u);
+    if (tid == 0) sm->next = 32u * (BT / 32);
     bm_mark<BT>(bm, r4, nr, rlim, n_words, false, tid, err);
     // r's last token (the padding repeats it in the last block's last lane)
     const uint32_t rmax = nr ? ld_block(r4, (nr - 1) >> 2, rlim, err).w : 0u;
+    if (32u * (uint32_t)warp < wi.n) {  // warp-uniform: the first batch's descriptors
+        if (p_ok && p_id >= I.s_n_sets) {
+            atomicOr(err, ERR_CAND_ID);
+            p_ok = false;
+        }
+        if (p_ok && self_join && p_id == wi.r) p_ok = false;
+        if (p_ok) p_desc = I.s_desc[p_id];
+        pstage = 2;
+    }
     __syncthreads();
 
-    // candidate preparation (warp-uniform stage: 0 takes 32 candidates, 1 loads descriptors,
-    // 2 filters and queues); queue cursors are free-running
-    uint32_t pstage = 0, qhead = 0, qtail = 0;
-    bool pdone = false;  // warp-uniform: no candidates left to take
-    bool p_ok = false;
-    uint32_t p_id = 0;
-    uint2 p_desc = make_uint2(0u, 0u);
     // the lane's pair: next block to merge (jb) and to ask for (jr), ring slot of its block 0
     // (rb); a finished pair keeps s_id / o until the maintenance step sends it out
     bool active = false, out = false;
