@@ -473,8 +473,9 @@ ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double* plan_ms, d
  * granularity verifies pairs of any length), they change the speed only;
  * lane_max_key <= thread_max_key leaves the lane bin empty.
  * block_threads is 128, 256 or 512 (default 256), optionally
- * | SSJ_WIDE_REGISTERS for the verify kernel compiled for three quarters of
- * the CTAs per SM (more registers per thread, fewer spills) and
+ * | SSJ_WIDE_REGISTERS for the verify kernel compiled for fewer CTAs per SM
+ * (7 instead of 8 of 128 threads, 3 instead of 4 of 256, 1 instead of 2 of
+ * 512: more registers per thread, fewer spills) and
  * | SSJ_BULK_STAGING (below).  Zero leaves a value unchanged. */
 ssj_status ssj_set_granularity(ssj_ctx* ctx, uint32_t thread_max_key, uint32_t lane_max_key, uint32_t warp_max_key,
                                uint32_t block_threads);

@@ -1694,13 +1694,14 @@ static cudaError_t launch_bt(const VerifyArgs& a, cudaStream_t st, int num_sms) 
 }
 
 // block_threads: 128, 256 or 512, optionally | kWideRegisters (the variant
-// budgeted for three quarters of the CTAs per SM, with more registers per
-// thread) and | kBulkStaging (a launch argument, not a variant).
+// budgeted for fewer CTAs per SM, with more registers per thread: 7 of 8
+// CTAs of 128 threads, 3 of 4 of 256, 1 of 2 of 512) and | kBulkStaging (a
+// launch argument, not a variant).
 template <class F>
 static cudaError_t dispatch_variant(uint32_t block_threads, F&& f) {
     const bool wide = (block_threads & kWideRegisters) != 0;
     switch (block_threads & ~(kWideRegisters | kBulkStaging)) {
-        case 128: return wide ? f.template operator()<128, 6>() : f.template operator()<128, 8>();
+        case 128: return wide ? f.template operator()<128, 7>() : f.template operator()<128, 8>();
         case 512: return wide ? f.template operator()<512, 1>() : f.template operator()<512, 2>();
         default: return wide ? f.template operator()<256, 3>() : f.template operator()<256, 4>();
     }
