@@ -213,10 +213,12 @@ ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* ou
 
 /*
  * Verify n_batches host batches (independent joins: own collections,
- * thresholds, functions) synchronously in ONE batched launch: all inputs
- * are copied to the device together (from pinned memory at the copy
- * engines' rate), one plan and one verify kernel cover every batch, then
- * the counts and results come back.  outs[i] / caps[i]: host room for
+ * thresholds, functions) synchronously in batched launches: one plan and
+ * one verify kernel cover every batch of a group.  A call with fewer than
+ * 2^25 candidates is one group; a larger one is cut into two consecutive
+ * groups of batches with about equal candidate counts, and the inputs of
+ * the second group are copied (from pinned memory at the copy engines'
+ * rate, on a second stream) while the first group's kernels run.  Then the counts and results come back.  outs[i] / caps[i]: host room for
  * batch i's triples; n_outs[i] receives its result count.  Host pointers
  * only (SSJ_DEVICE_PTRS is rejected; see ssj_multi_create for device
  * batches).  Flags per batch as for ssj_verify_batch.  If a count exceeds

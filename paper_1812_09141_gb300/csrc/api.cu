@@ -59,8 +59,11 @@ namespace {
 
 // Default of the context's index-item threshold (ssj_set_index_items).
 constexpr uint32_t kIndexMinCandsDefault = 256;
-// ssj_verify_batches splits calls with at least this many candidates into two launches.
-constexpr uint64_t kSplitCands = 1ull << 25;
+// ssj_verify_batches runs a call as one launch per kSplitCands candidates, up to kMaxGroups
+// (on the 256-instance workload, four groups measured slower than two: 1.39e10 against
+// 1.45e10 pairs/s end to end; each launch adds its own fill and drain).
+constexpr uint64_t kSplitCands = 1ull << 24;
+constexpr uint32_t kMaxGroups = 2;
 
 struct Collection {
     uint32_t n_sets = 0;
@@ -155,10 +158,10 @@ struct ssj_ctx {
     void* io = nullptr;
     size_t io_bytes = 0;
     uint64_t* h_count = nullptr;  // pinned
-    uint32_t* h_err = nullptr;    // pinned, two words
+    uint32_t* h_err = nullptr;    // pinned, kMaxGroups words
     // ssj_verify_batches: the stream and event that carry the second group's input copies
     cudaStream_t copy_stream = nullptr;
-    cudaEvent_t copy_done = nullptr;
+    cudaEvent_t copy_done[kMaxGroups] = {};
     cudaEvent_t call_start = nullptr;
     Counters* last_ctr = nullptr;
     // kernel timing (SSJ_CTX_PROFILE): events around plan and verify of each launch
@@ -439,7 +442,8 @@ extern "C" ssj_status ssj_create(const ssj_config* config, ssj_ctx** out) {
         ctx->own_stream = true;
     }
     if (cudaMallocHost(reinterpret_cast<void**>(&ctx->h_count), sizeof(uint64_t)) != cudaSuccess) return SSJ_EDEVICE;
-    if (cudaMallocHost(reinterpret_cast<void**>(&ctx->h_err), 2 * sizeof(uint32_t)) != cudaSuccess) return SSJ_EDEVICE;
+    if (cudaMallocHost(reinterpret_cast<void**>(&ctx->h_err), kMaxGroups * sizeof(uint32_t)) != cudaSuccess)
+        return SSJ_EDEVICE;
     cudaMemPoolProps props;
     memset(&props, 0, sizeof(props));
     props.allocType = cudaMemAllocationTypePinned;
@@ -513,7 +517,8 @@ extern "C" void ssj_destroy(ssj_ctx* ctx) {
     cudaFreeHost(ctx->h_count);
     cudaFreeHost(ctx->h_err);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-    if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
+    for (cudaEvent_t ev : ctx->copy_done)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->call_start) cudaEventDestroy(ctx->call_start);
 
     for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
@@ -882,46 +887,53 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
         const uint64_t cap = (b->flags & SSJ_COUNT_ONLY) ? 0 : std::min(caps[i], n_cands[i]);
         off += align256(sizeof(ssj_triple) * std::max<uint64_t>(cap, 1));
     }
-    // Large calls run as two launches over two groups of batches (split near half the
-    // candidates): the second group's host-to-device copies, on a second stream, overlap the
-    // first group's kernels.
-    uint32_t split = n_batches;
-    if (n_batches >= 2 && sh.total_cands >= kSplitCands) {
+    // Large calls run as up to kMaxGroups launches over consecutive groups of batches with about
+    // equal candidate counts: each later group's host-to-device copies, on a second stream,
+    // overlap the earlier groups' kernels.
+    uint32_t groups = (uint32_t)std::min<uint64_t>(
+        {(uint64_t)kMaxGroups, (uint64_t)n_batches, std::max<uint64_t>(sh.total_cands / kSplitCands, 1)});
+    uint32_t gstart[kMaxGroups + 1];
+    {
+        uint32_t g = 0;
         uint64_t acc = 0;
-        split = 1;
-        for (uint32_t i = 0; i + 1 < n_batches; ++i) {
+        gstart[0] = 0;
+        for (uint32_t i = 0; i < n_batches && g + 1 < groups; ++i) {
             acc += n_cands[i];
-            split = i + 1;
-            if (2 * acc >= sh.total_cands) break;
+            if (acc * groups >= (uint64_t)(g + 1) * sh.total_cands && i + 1 < n_batches) gstart[++g] = i + 1;
         }
+        groups = g + 1;  // (a group is never empty)
+        gstart[groups] = n_batches;
     }
-    LaunchShape shp[2];
-    for (int gi = 0; gi < 2; ++gi) {
-        shp[gi].n_inst = 0;
-        shp[gi].n_tiles = 0;
-        shp[gi].total_probes = 0;
-        shp[gi].total_cands = 0;
+    LaunchShape shp[kMaxGroups];
+    size_t ws_off[kMaxGroups + 1];
+    ws_off[0] = 0;
+    for (uint32_t gi = 0; gi < groups; ++gi) {
+        LaunchShape& q = shp[gi];
+        q.n_inst = 0;
+        q.n_tiles = 0;
+        q.total_probes = 0;
+        q.total_cands = 0;
+        for (uint32_t i = gstart[gi]; i < gstart[gi + 1]; ++i) {
+            table[i].tile_base = q.n_tiles;
+            q.n_inst += 1;
+            q.n_tiles += (uint32_t)(((uint64_t)batches[i].n_probes + 31) / 32);
+            q.total_probes += batches[i].n_probes;
+            q.total_cands += n_cands[i];
+        }
+        ws_off[gi + 1] = ws_off[gi] + align256(workspace_bytes(q, ctx->num_sms));
     }
-    for (uint32_t i = 0; i < n_batches; ++i) {
-        LaunchShape& q = shp[i < split ? 0 : 1];
-        table[i].tile_base = q.n_tiles;
-        q.n_inst += 1;
-        q.n_tiles += (uint32_t)(((uint64_t)batches[i].n_probes + 31) / 32);
-        q.total_probes += batches[i].n_probes;
-        q.total_cands += n_cands[i];
-    }
-    const size_t ws0 = align256(workspace_bytes(shp[0], ctx->num_sms));
-    const size_t ws_total = ws0 + (split < n_batches ? workspace_bytes(shp[1], ctx->num_sms) : 0);
+    const size_t ws_total = ws_off[groups];
     DeviceGuard g(ctx->device);
     ssj_status st = ensure_device_buffer(ctx, &ctx->io, &ctx->io_bytes, off);
     if (st != SSJ_OK) return st;
     st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, ws_total);
     if (st != SSJ_OK) return st;
     cudaStream_t s = ctx->stream;
-    cudaStream_t cs = s;  // the second group's copies
-    if (split < n_batches) {
+    cudaStream_t cs = s;  // the later groups' copies
+    if (groups > 1) {
         if (!ctx->copy_stream) CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-        if (!ctx->copy_done) CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming));
+        for (uint32_t gi = 0; gi < kMaxGroups; ++gi)
+            if (!ctx->copy_done[gi]) CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->copy_done[gi], cudaEventDisableTiming));
         if (!ctx->call_start) CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->call_start, cudaEventDisableTiming));
         cs = ctx->copy_stream;
         // the copy stream starts after everything already queued on the context's stream
@@ -930,8 +942,12 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
     }
     char* base = static_cast<char*>(ctx->io);
     uint64_t* d_counts = reinterpret_cast<uint64_t*>(base);
-    for (uint32_t i = 0; i < n_batches; ++i) {
-        const cudaStream_t cp = i < split ? s : cs;
+    for (uint32_t i = 0, gi = 0; i < n_batches; ++i) {
+        if (i == gstart[gi + 1]) {  // group gi's copies are all queued
+            if (gi > 0) CUDA_TRY(ctx, cudaEventRecord(ctx->copy_done[gi], cs));
+            ++gi;
+        }
+        const cudaStream_t cp = gi == 0 ? s : cs;
         const ssj_batch* b = &batches[i];
         char* p = base + io_off[i];
         uint32_t* d_probe = reinterpret_cast<uint32_t*>(p); p += align256(4ull * std::max<uint32_t>(b->n_probes, 1));
@@ -956,17 +972,16 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
         I.cap = (b->flags & SSJ_COUNT_ONLY) ? 0 : std::min(caps[i], n_cands[i]);
         I.count = reinterpret_cast<unsigned long long*>(d_counts + i);
     }
-    if (split < n_batches) CUDA_TRY(ctx, cudaEventRecord(ctx->copy_done, cs));
-    const int groups = split < n_batches ? 2 : 1;
-    for (int gi = 0; gi < groups; ++gi) {
-        const uint32_t lo = gi == 0 ? 0 : split, hi = gi == 0 ? split : n_batches;
+    if (groups > 1) CUDA_TRY(ctx, cudaEventRecord(ctx->copy_done[groups - 1], cs));
+    for (uint32_t gi = 0; gi < groups; ++gi) {
+        const uint32_t lo = gstart[gi], hi = gstart[gi + 1];
         VerifyArgs a;
         memset(&a, 0, sizeof(a));
         apply_policy(ctx, a, launch_vocab, launch_force_index);
         if (pinned) set_l2_window(a, *pinned);
-        bind_workspace(a, static_cast<char*>(ctx->ws) + (gi == 0 ? 0 : ws0), shp[gi], ctx->num_sms);
+        bind_workspace(a, static_cast<char*>(ctx->ws) + ws_off[gi], shp[gi], ctx->num_sms);
         a.table = a.table_out;
-        if (gi == 1) CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->copy_done, 0));  // the group's inputs are in
+        if (gi > 0) CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->copy_done[gi], 0));  // the group's inputs are in
         CUDA_TRY(ctx, cudaMemcpyAsync(a.table_out, table.data() + lo, sizeof(Instance) * (hi - lo),
                                       cudaMemcpyHostToDevice, s));
         ctx->last_ctr = a.ctr;
@@ -977,7 +992,8 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
     std::vector<uint64_t> counts(n_batches);
     CUDA_TRY(ctx, cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint64_t) * n_batches, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    const uint32_t derr = ctx->h_err[0] | (groups == 2 ? ctx->h_err[1] : 0u);
+    uint32_t derr = 0;
+    for (uint32_t gi = 0; gi < groups; ++gi) derr |= ctx->h_err[gi];
     if (derr) return device_check_status(ctx, derr);
     bool short_cap = false;
     for (uint32_t i = 0; i < n_batches; ++i) {
