@@ -697,7 +697,8 @@ __device__ __forceinline__ void cp_async_wait() {
 // just issued, and its common path is short.  Each warp prepares its
 // candidates 32 at a time: their ids are loaded, one round later their
 // descriptors, one round later again the required overlap and the length
-// filter decide which enter the warp's queue (shared memory).  A round is
+// filter decide which enter the warp's queue (shared memory), and the next
+// batch's ids are loaded in that same step.  A round is
 // kIndexSteps walk steps followed by one maintenance step (preparation,
 // survivors out, idle lanes refilled from the queue).  In a walk step a lane
 // asks for one more block of s (cp.async into its own ring of kIndexRing
@@ -802,19 +803,9 @@ __device__ __noinline__ void index_item(const Instance& I, const WorkItem& wi, u
             }
             out = false;
         }
-        // ---- preparation
-        if (pstage == 0) {
-            if (!pdone && qtail - qhead + 32 <= kIndexQueue) {
-                uint32_t base = 0;
-                if (lane == 0) base = atomicAdd(&sm->next, 32u);
-                base = __shfl_sync(kFull, base, 0);
-                if (base + 32 >= wi.n) pdone = true;
-                const uint32_t my = base + (uint32_t)lane;
-                p_ok = my < wi.n && in_bounds(wi.c0 + my, I.n_cands, err);
-                if (p_ok) p_id = I.cand_ids[wi.c0 + my];
-                if (base < wi.n) pstage = 1;
-            }
-        } else if (pstage == 1) {
+        // ---- preparation (a batch queued here makes room for the next one to be taken in the
+        // same step, so a batch is taken every second round)
+        if (pstage == 1) {
             if (p_ok && p_id >= I.s_n_sets) {
                 atomicOr(err, ERR_CAND_ID);
                 p_ok = false;
@@ -823,16 +814,30 @@ __device__ __noinline__ void index_item(const Instance& I, const WorkItem& wi, u
             if (p_ok) p_desc = I.s_desc[p_id];
             pstage = 2;
         } else {
-            uint32_t q = 0;
-            if (p_ok) {
-                q = required_overlap(I.sim, I.p, I.den, I.magic, nr, p_desc.y);
-                p_ok = emit_all || (nr + p_desc.y > 0 && q <= min(nr, p_desc.y));  // length filter
+            if (pstage == 2) {
+                uint32_t q = 0;
+                if (p_ok) {
+                    q = required_overlap(I.sim, I.p, I.den, I.magic, nr, p_desc.y);
+                    p_ok = emit_all || (nr + p_desc.y > 0 && q <= min(nr, p_desc.y));  // length filter
+                }
+                const uint32_t m = __ballot_sync(kFull, p_ok);
+                if (p_ok) queue[(qtail + __popc(m & lt_mask)) % kIndexQueue] = make_uint4(p_id, p_desc.x, p_desc.y, q);
+                qtail += __popc(m);
+                pstage = 0;
+                __syncwarp();
             }
-            const uint32_t m = __ballot_sync(kFull, p_ok);
-            if (p_ok) queue[(qtail + __popc(m & lt_mask)) % kIndexQueue] = make_uint4(p_id, p_desc.x, p_desc.y, q);
-            qtail += __popc(m);
-            pstage = 0;
-            __syncwarp();
+            if (pstage == 0) {
+                if (!pdone && qtail - qhead + 32 <= kIndexQueue) {
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(&sm->next, 32u);
+                    base = __shfl_sync(kFull, base, 0);
+                    if (base + 32 >= wi.n) pdone = true;
+                    const uint32_t my = base + (uint32_t)lane;
+                    p_ok = my < wi.n && in_bounds(wi.c0 + my, I.n_cands, err);
+                    if (p_ok) p_id = I.cand_ids[wi.c0 + my];
+                    if (base < wi.n) pstage = 1;
+                }
+            }
         }
         // ---- idle lanes take queued candidates
         const uint32_t idle = __ballot_sync(kFull, !active);
