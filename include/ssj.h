@@ -173,7 +173,10 @@ ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, ui
 #define SSJ_HOST_DIRECT 0x1000u     /* ssj_verify_batches: host arrays in pinned memory that the
                                        device can address are read by the kernels directly over
                                        the host link (NVLink-C2C on Grace systems) instead of
-                                       being copied first; other arrays are copied */
+                                       being copied first; other arrays are copied.  Calls of
+                                       2^25 or more candidates do this by default */
+#define SSJ_HOST_STAGED 0x4000u     /* ssj_verify_batches: copy this batch's pinned inputs to the
+                                       device before the kernels run, even in a large call */
 #define SSJ_JOIN_POSITIONAL 0x400u  /* ssj_self_join: drop a candidate at a matching prefix token
                                        when min(i, j) + 1 + min(|r|-i-1, |s|-j-1) (i, j: the token's
                                        positions) is below the pair's equivalent overlap */
@@ -215,11 +218,14 @@ ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* ou
  * Verify n_batches host batches (independent joins: own collections,
  * thresholds, functions) synchronously in batched launches: one plan and
  * one verify kernel cover every batch of a group.  A call with fewer than
- * 2^25 candidates is one group; a larger one is cut into two consecutive
- * groups of batches with about equal candidate counts, and the inputs of
- * the second group are copied (from pinned memory at the copy engines'
- * rate, on a second stream) while the first group's kernels run.  Then the counts and results come back.  outs[i] / caps[i]: host room for
- * batch i's triples; n_outs[i] receives its result count.  Host pointers
+ * 2^25 candidates is one group, its inputs copied to the device first.  A
+ * larger call is cut into two consecutive groups of batches with about
+ * equal candidate counts: its inputs in pinned host memory are read by the
+ * kernels directly over the host link (SSJ_HOST_DIRECT) unless a batch sets
+ * SSJ_HOST_STAGED, and the inputs that are copied are copied for the second
+ * group on a second stream while the first group's kernels run.  Then the
+ * counts and results come back.  outs[i] / caps[i]: host room for batch i's
+ * triples; n_outs[i] receives its result count.  Host pointers
  * only (SSJ_DEVICE_PTRS is rejected; see ssj_multi_create for device
  * batches).  Flags per batch as for ssj_verify_batch.  If a count exceeds
  * its cap, the first caps[i] triples are written and SSJ_ENOMEM is returned

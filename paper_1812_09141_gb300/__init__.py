@@ -39,6 +39,7 @@ SSJ_FORCE_WARP = 0x20
 SSJ_FORCE_BLOCK = 0x40
 SSJ_FORCE_LANE = 0x80
 SSJ_FORCE_INDEX = 0x2000
+SSJ_HOST_STAGED = 0x4000
 SSJ_SIM_JACCARD = 0x000
 SSJ_SIM_DICE = 0x100
 SSJ_SIM_COSINE = 0x200

@@ -64,6 +64,10 @@ constexpr uint32_t kIndexMinCandsDefault = 256;
 // 1.45e10 pairs/s end to end; each launch adds its own fill and drain).
 constexpr uint64_t kSplitCands = 1ull << 24;
 constexpr uint32_t kMaxGroups = 2;
+// ...and reads inputs in pinned host memory directly over the host link (no staging copy) in
+// calls of at least this many candidates: on the 256-instance workload, 1.62e10-1.67e10 pairs/s
+// end to end against 1.09e10-1.45e10 with staged copies.
+constexpr uint64_t kDirectCands = 1ull << 25;
 
 struct Collection {
     uint32_t n_sets = 0;
@@ -315,7 +319,7 @@ ssj_status resolve(ssj_ctx* ctx, const ssj_batch* b, Collection** R, Collection*
         return fail(ctx, SSJ_EINVAL, "renumbered collections can only be self-joined");
     const uint32_t known = SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | SSJ_EMIT_ALL | SSJ_FORCE_THREAD |
                            SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_FORCE_INDEX | SSJ_SIM_MASK |
-                           SSJ_KEEP_INPUTS | SSJ_HOST_DIRECT;
+                           SSJ_KEEP_INPUTS | SSJ_HOST_DIRECT | SSJ_HOST_STAGED;
     if (b->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown batch flag");
     const uint32_t forced =
         b->flags & (SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_FORCE_INDEX);
@@ -955,9 +959,12 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
         uint32_t* d_cand = reinterpret_cast<uint32_t*>(p);  p += align256(4ull * std::max<uint64_t>(n_cands[i], 1));
         // SSJ_HOST_DIRECT: pinned arrays the device can address are read by the kernels
         // themselves (over the host link), with no staging copy
-        const void* dv_probe = (b->flags & SSJ_HOST_DIRECT) ? device_view(b->probe_ids) : nullptr;
-        const void* dv_offs = (b->flags & SSJ_HOST_DIRECT) ? device_view(b->cand_offsets) : nullptr;
-        const void* dv_cand = (b->flags & SSJ_HOST_DIRECT) ? device_view(b->cand_ids) : nullptr;
+        // (calls of 2^25+ candidates read pinned inputs directly unless the batch asks for staging)
+        const bool direct = (b->flags & SSJ_HOST_DIRECT) ||
+                            (sh.total_cands >= kDirectCands && !(b->flags & SSJ_HOST_STAGED));
+        const void* dv_probe = direct ? device_view(b->probe_ids) : nullptr;
+        const void* dv_offs = direct ? device_view(b->cand_offsets) : nullptr;
+        const void* dv_cand = direct ? device_view(b->cand_ids) : nullptr;
         if (b->n_probes && !dv_probe)
             CUDA_TRY(ctx, cudaMemcpyAsync(d_probe, b->probe_ids, 4ull * b->n_probes, cudaMemcpyHostToDevice, cp));
         if (b->n_probes && !dv_offs)

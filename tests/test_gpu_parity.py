@@ -580,6 +580,15 @@ def test_full_long_sets_exact(ctx):
     got = ssj.triples_to_array(np.concatenate(res))
     assert np.array_equal(got, want)
     assert ssj.ssj_device_error(ctx) == 0
+    # the same call with the inputs in pinned host memory: the kernels read them over the host
+    # link (the default for a call this large), or, with SSJ_HOST_STAGED, they are copied first
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    pinned = [(hh, hs, p, q, pin(pr), pin(po), pin(pc), 0) for hh, hs, p, q, pr, po, pc, _ in parts]
+    for fl in (0, ssj.SSJ_HOST_STAGED):
+        res = ssj.ssj_verify_batches(ctx, [x[:7] + (fl,) for x in pinned], caps=[len(want) + 16] * 3)
+        assert np.array_equal(ssj.triples_to_array(np.concatenate(res)), want), fl
+    assert ssj.ssj_device_error(ctx) == 0
     ssj.ssj_unload_collection(ctx, h)
 
 
