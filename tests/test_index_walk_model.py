@@ -1,9 +1,9 @@
 """The walk the index items run, restated on the host and checked against exact set
 intersection (CPU only).  The probe r is a bitmap over token values; the candidate s is laid
 out in 4-token blocks whose padding repeats its last token.  A step tests the four tokens of s's
-current block against the bitmap (minus the repeated padding lanes), then stops when no token of
-s is left or the block's last token reaches r's last token (no later token of s can match), and
-otherwise rejects once the overlap so far plus the tokens of s left falls below req.  The
+current block against the bitmap, then stops at s's last block (subtracting the repeated padding
+lanes there) or when the block's last token reaches r's last token (no later token of s can
+match), and otherwise rejects once the overlap so far plus the tokens of s left falls below req.  The
 claims the kernel relies on: a pair that is not rejected ends with o = |r ∩ s| exactly, a pair
 whose overlap reaches req is never rejected, and the walk reads no more blocks of s than
 needed to pass r's last token."""
@@ -28,12 +28,13 @@ def index_walk(r, s, req=0, early=False):
         return 0, False, 0
     for blk in blocks(s):
         read += 1
-        nv = min(rems, 4)
         bits = [1 if x in bitmap else 0 for x in blk]
-        o += sum(bits) - (4 - nv) * bits[3]
-        rems -= nv
-        if rems == 0 or blk[3] >= rmax:
+        o += sum(bits)
+        if rems <= 4 or blk[3] >= rmax:  # s's last block, or no later token of s can match
+            if rems < 4:
+                o -= (4 - rems) * bits[3]  # the lanes past s's end repeat its last token
             return o, False, read
+        rems -= 4
         if early and o + rems < req:
             return o, True, read
     return o, False, read
