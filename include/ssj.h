@@ -138,7 +138,9 @@ ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, ui
                                    Section 3.2, "output count") */
 #define SSJ_SORTED 0x2u         /* return triples sorted by (r, s) */
 #define SSJ_DEVICE_PTRS 0x4u    /* probe_ids, cand_offsets, cand_ids and the output array are
-                                   DEVICE pointers (same device as the context) */
+                                   DEVICE pointers (same device as the context), each aligned to
+                                   its element size (4 bytes for ids and triples, 8 for
+                                   cand_offsets and counts; SSJ_EINVAL otherwise) */
 #define SSJ_EMIT_ALL 0x8u       /* diagnostic: emit every listed pair (except self pairs of a
                                    self-join) with its exact overlap, no threshold test and no
                                    early termination */
@@ -173,7 +175,8 @@ ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t* n_sets, ui
 #define SSJ_HOST_DIRECT 0x1000u     /* ssj_verify_batches: host arrays in pinned memory that the
                                        device can address are read by the kernels directly over
                                        the host link (NVLink-C2C on Grace systems) instead of
-                                       being copied first; other arrays are copied.  Calls of
+                                       being copied first; other arrays (pageable, or off
+                                       their element alignment) are copied.  Calls of
                                        2^25 or more candidates do this by default */
 #define SSJ_HOST_STAGED 0x4000u     /* ssj_verify_batches: copy this batch's pinned inputs to the
                                        device before the kernels run, even in a large call */
@@ -239,7 +242,8 @@ ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches, uint32_t n
  * for the context's stream) and return without waiting.  All batch arrays,
  * d_out (cap triples) and d_count (one uint64, receives the number of
  * result pairs, which may exceed cap) are DEVICE pointers that must stay
- * valid until the stream reaches this work; SSJ_DEVICE_PTRS is implied.
+ * valid until the stream reaches this work; SSJ_DEVICE_PTRS is implied
+ * (with its alignment rule: d_count 8 bytes, d_out 4).
  * The work queue is taken from the context's workspace, which grows (with
  * a device allocation) only when a batch is larger than any before; call
  * ssj_reserve first to keep allocations out of a timed or captured region.

@@ -258,10 +258,27 @@ ssj_status ensure_pinned(ssj_ctx* ctx, T** buf, uint64_t* have, uint64_t need) {
     return SSJ_OK;
 }
 
+// The kernels load probe ids and candidate ids as 4-byte words and offsets
+// and counts as 8-byte words, and store result triples field by field (4
+// bytes).  An address the device reads or writes off that alignment would
+// fault the context, so such arrays are refused (device memory) or staged
+// (pinned host memory).
+bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+ssj_status check_device_alignment(ssj_ctx* ctx, const ssj_batch* b, const void* out, const void* count) {
+    if (!aligned_to(b->probe_ids, 4) || !aligned_to(b->cand_offsets, 8) || !aligned_to(b->cand_ids, 4) ||
+        !aligned_to(out, 4) || !aligned_to(count, 8))
+        return fail(ctx, SSJ_EINVAL,
+                    "device arrays must be aligned to their element size (4 bytes for ids and triples, 8 for "
+                    "cand_offsets and counts)");
+    return SSJ_OK;
+}
+
 // Device address of pinned host memory the device can read directly, or
-// NULL (pageable memory, or no mapping).
-const void* device_view(const void* p) {
-    if (!p) return nullptr;
+// NULL (pageable memory, no mapping, or an address off the element alignment
+// a, which is then staged by a copy).
+const void* device_view(const void* p, uintptr_t a) {
+    if (!p || !aligned_to(p, a)) return nullptr;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
@@ -726,6 +743,8 @@ extern "C" ssj_status ssj_verify_batch_async(ssj_ctx* ctx, const ssj_batch* batc
         return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
     if (batch->n_cands && !batch->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
     if (cap && !d_out && !(batch->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output");
+    st = check_device_alignment(ctx, batch, d_out, d_count);
+    if (st != SSJ_OK) return st;
     DeviceGuard g(ctx->device);
     st = ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(batch->n_probes, batch->n_cands, ctx->num_sms));
     if (st != SSJ_OK) return st;
@@ -809,6 +828,8 @@ extern "C" ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj
         if (batch->n_probes && (!batch->probe_ids || !batch->cand_offsets))
             return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
         if (n_cands && !batch->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
+        st = check_device_alignment(ctx, batch, out, nullptr);
+        if (st != SSJ_OK) return st;
         a = make_args(ctx, batch, *R, *S, n_cands);
         a.single.probe_ids = batch->probe_ids;
         a.single.cand_offsets = batch->cand_offsets;
@@ -962,9 +983,9 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
         // (calls of 2^25+ candidates read pinned inputs directly unless the batch asks for staging)
         const bool direct = (b->flags & SSJ_HOST_DIRECT) ||
                             (sh.total_cands >= kDirectCands && !(b->flags & SSJ_HOST_STAGED));
-        const void* dv_probe = direct ? device_view(b->probe_ids) : nullptr;
-        const void* dv_offs = direct ? device_view(b->cand_offsets) : nullptr;
-        const void* dv_cand = direct ? device_view(b->cand_ids) : nullptr;
+        const void* dv_probe = direct ? device_view(b->probe_ids, 4) : nullptr;
+        const void* dv_offs = direct ? device_view(b->cand_offsets, 8) : nullptr;
+        const void* dv_cand = direct ? device_view(b->cand_ids, 4) : nullptr;
         if (b->n_probes && !dv_probe)
             CUDA_TRY(ctx, cudaMemcpyAsync(d_probe, b->probe_ids, 4ull * b->n_probes, cudaMemcpyHostToDevice, cp));
         if (b->n_probes && !dv_offs)
@@ -1031,6 +1052,8 @@ extern "C" ssj_status ssj_self_join(ssj_ctx* ctx, ssj_coll coll, uint32_t p, uin
                            SSJ_FORCE_THREAD | SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_FORCE_INDEX;
     if (flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown flag");
     if (cap && !out && !(flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output with cap > 0");
+    if ((flags & SSJ_DEVICE_PTRS) && !aligned_to(out, 4))
+        return fail(ctx, SSJ_EINVAL, "device output must be aligned to 4 bytes");
     // threshold and collection checks through the batch path's resolve()
     ssj_batch probe_b;
     memset(&probe_b, 0, sizeof(probe_b));
@@ -1217,6 +1240,8 @@ extern "C" ssj_status ssj_verify_groups(ssj_ctx* ctx, const ssj_group_batch* gb,
                            SSJ_FORCE_WARP | SSJ_FORCE_BLOCK | SSJ_FORCE_LANE | SSJ_FORCE_INDEX;
     if (gb->flags & ~known) return fail(ctx, SSJ_EINVAL, "unknown flag");
     if (cap && !out && !(gb->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "NULL output with cap > 0");
+    if ((gb->flags & SSJ_DEVICE_PTRS) && !aligned_to(out, 4))
+        return fail(ctx, SSJ_EINVAL, "device output must be aligned to 4 bytes");
     if (!gb->group_offsets || (gb->n_groups && !gb->members) || (gb->n_probe_groups && (!gb->probe_groups ||
         !gb->cand_offsets)))
         return fail(ctx, SSJ_EINVAL, "NULL group arrays");
@@ -1502,7 +1527,10 @@ extern "C" ssj_status ssj_submit(ssj_ctx* ctx, const ssj_batch* batch, uint64_t*
     const bool dev = (batch->flags & SSJ_DEVICE_PTRS) != 0;
     const bool count_only = (batch->flags & SSJ_COUNT_ONLY) != 0;
     uint64_t n_cands = batch->n_cands;
-    if (!dev) {
+    if (dev) {
+        st = check_device_alignment(ctx, batch, nullptr, nullptr);
+        if (st != SSJ_OK) return st;
+    } else {
         lk.unlock();  // validation reads only the caller's arrays and immutable collection sizes
         st = validate_host_batch(ctx, batch, &n_cands);
         lk.lock();
@@ -1718,14 +1746,17 @@ extern "C" ssj_status ssj_profile_read(ssj_ctx* ctx, uint32_t* launches, double*
 
 namespace ssj {
 
-ssj_status resolve_device_batch(ssj_ctx* ctx, const ssj_batch* batch, VerifyArgs* a, int* device, int* num_sms,
-                                uint32_t* block_threads, cudaStream_t* ctx_stream) {
+ssj_status resolve_device_batch(ssj_ctx* ctx, const ssj_batch* batch, const void* out, const void* count,
+                                VerifyArgs* a, int* device, int* num_sms, uint32_t* block_threads,
+                                cudaStream_t* ctx_stream) {
     Collection *R, *S;
     ssj_status st = resolve(ctx, batch, &R, &S);
     if (st != SSJ_OK) return st;
     if (batch->n_probes && (!batch->probe_ids || !batch->cand_offsets))
         return fail(ctx, SSJ_EINVAL, "NULL batch arrays");
     if (batch->n_cands && !batch->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
+    st = check_device_alignment(ctx, batch, out, count);
+    if (st != SSJ_OK) return st;
     *a = make_args(ctx, batch, *R, *S, batch->n_cands);
     a->single.probe_ids = batch->probe_ids;
     a->single.cand_offsets = batch->cand_offsets;
@@ -1782,6 +1813,8 @@ extern "C" ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, u
         if (b->n_probes && (!b->probe_ids || !b->cand_offsets)) return fail(ctx, SSJ_EINVAL, "batch %u: NULL arrays", i);
         if (b->n_cands && !b->cand_ids) return fail(ctx, SSJ_EINVAL, "batch %u: NULL cand_ids", i);
         if (caps[i] && !d_outs[i] && !(b->flags & SSJ_COUNT_ONLY)) return fail(ctx, SSJ_EINVAL, "batch %u: NULL output", i);
+        st = check_device_alignment(ctx, b, d_outs[i], d_counts + i);
+        if (st != SSJ_OK) return st;
         Instance I = make_instance(b, *R, *S, b->n_cands);
         I.probe_ids = b->probe_ids;
         I.cand_offsets = b->cand_offsets;

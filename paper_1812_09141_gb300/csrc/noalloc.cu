@@ -16,8 +16,9 @@
 #include "ssj_internal.h"
 
 namespace ssj {
-ssj_status resolve_device_batch(ssj_ctx* ctx, const ssj_batch* batch, VerifyArgs* a, int* device, int* num_sms,
-                                uint32_t* block_threads, cudaStream_t* ctx_stream);
+ssj_status resolve_device_batch(ssj_ctx* ctx, const ssj_batch* batch, const void* out, const void* count,
+                                VerifyArgs* a, int* device, int* num_sms, uint32_t* block_threads,
+                                cudaStream_t* ctx_stream);
 ssj_status report(ssj_ctx* ctx, ssj_status st, const char* msg);
 void remember_counters(ssj_ctx* ctx, Counters* c);
 }  // namespace ssj
@@ -54,7 +55,7 @@ extern "C" ssj_status ssj_verify_batch_noalloc(ssj_ctx* ctx, const ssj_batch* ba
     int device = 0, num_sms = 0;
     uint32_t block_threads = 0;
     cudaStream_t ctx_stream = nullptr;
-    ssj_status st = resolve_device_batch(ctx, batch, &a, &device, &num_sms, &block_threads, &ctx_stream);
+    ssj_status st = resolve_device_batch(ctx, batch, d_out, d_count, &a, &device, &num_sms, &block_threads, &ctx_stream);
     if (st != SSJ_OK) return st;
     if (cap && !d_out && !(batch->flags & SSJ_COUNT_ONLY)) return report(ctx, SSJ_EINVAL, "NULL output");
     if (workspace_bytes(batch->n_probes, batch->n_cands, num_sms) > kNoallocScratchBytes)

@@ -149,3 +149,78 @@ def test_context_survives_rejected_batches(coll):
         assert np.array_equal(ssj.triples_to_array(ssj.ssj_results(ctx, t)), want)
     finally:
         ssj.ssj_destroy(ctx)
+
+
+def test_misaligned_arrays_never_reach_the_kernels(coll):
+    """The kernels load ids as 4-byte and offsets and counts as 8-byte words and store triples
+    field by field.  Device arrays off that alignment are refused with SSJ_EINVAL before any
+    launch, on every entry point that takes them; pinned host arrays off it are copied instead
+    of read over the host link, and give the oracle's results.  The context keeps working."""
+    import torch
+    dev = torch.device("cuda:0")
+    ctx = ssj.ssj_create(0)
+    try:
+        h = ssj.ssj_load_collection(ctx, coll.offsets, coll.tokens)
+        b = synth.all_pairs_batch(coll.n)
+        want = oracle.sort_triples(oracle.bruteforce_self(coll.offsets, coll.tokens, 4, 5))
+        assert len(want) > 0
+        # device arrays with room for a shifted copy; each shifted address is off its alignment
+        pr = torch.zeros(b.n_probes + 4, dtype=torch.int32, device=dev)
+        co = torch.zeros(b.n_probes + 3, dtype=torch.int64, device=dev)
+        ci = torch.zeros(b.n_cands + 4, dtype=torch.int32, device=dev)
+        out = torch.zeros(3 * len(want) + 8, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+        pr[:b.n_probes] = torch.from_numpy(b.probe_ids.astype(np.int32)).to(dev)
+        co[:b.n_probes + 1] = torch.from_numpy(b.cand_offsets.astype(np.int64)).to(dev)
+        ci[:b.n_cands] = torch.from_numpy(b.cand_ids.astype(np.int32)).to(dev)
+        torch.cuda.synchronize()
+        good = (pr.data_ptr(), co.data_ptr(), ci.data_ptr())
+        cap = len(want)
+        for k, shift in ((0, 2), (1, 4), (2, 2)):
+            arrays = list(good)
+            arrays[k] += shift
+            args = (h, h, 4, 5, *arrays)
+            with pytest.raises(ssj.SsjError) as ei:
+                ssj.ssj_verify_batch(ctx, *args, flags=ssj.SSJ_DEVICE_PTRS, out=out, cap=cap,
+                                     n_cands=b.n_cands, n_probes=b.n_probes)
+            assert ei.value.status == ssj.SSJ_EINVAL, k
+            with pytest.raises(ssj.SsjError) as ei:
+                ssj.ssj_verify_batch_async(ctx, *args, b.n_cands, out, cap, cnt, n_probes=b.n_probes)
+            assert ei.value.status == ssj.SSJ_EINVAL, k
+            with pytest.raises(ssj.SsjError) as ei:
+                ssj.ssj_multi_create(ctx, [ssj.DeviceBatch(*args, b.n_cands, n_probes=b.n_probes)], [out],
+                                     [cap], cnt)
+            assert ei.value.status == ssj.SSJ_EINVAL, k
+        # an output off 4 bytes, a count off 8
+        for o, c in ((out.data_ptr() + 2, cnt), (out, cnt.data_ptr() + 4)):
+            with pytest.raises(ssj.SsjError) as ei:
+                ssj.ssj_verify_batch_async(ctx, h, h, 4, 5, *good, b.n_cands, o, cap, c, n_probes=b.n_probes)
+            assert ei.value.status == ssj.SSJ_EINVAL
+        with pytest.raises(ssj.SsjError) as ei:
+            ssj.ssj_self_join(ctx, h, 4, 5, flags=ssj.SSJ_DEVICE_PTRS, out=out.data_ptr() + 2, cap=cap)
+        assert ei.value.status == ssj.SSJ_EINVAL
+        # the aligned arrays work on the same context
+        n = ssj.ssj_verify_batch(ctx, h, h, 4, 5, *good, flags=ssj.SSJ_DEVICE_PTRS, out=out, cap=cap,
+                                 n_cands=b.n_cands, n_probes=b.n_probes)
+        got = out[:3 * n].view(-1, 3).cpu().numpy().astype(np.uint32)
+        assert np.array_equal(oracle.sort_triples(got), want)
+
+        # pinned host arrays off their alignment, with the kernels asked to read pinned inputs
+        # directly: they are copied, and the results are exact
+        def pinned_off(a, mod, rem):
+            a = np.ascontiguousarray(a)
+            buf = torch.empty(a.nbytes + 64, dtype=torch.uint8).pin_memory().numpy()
+            shift = (rem - buf.ctypes.data) % mod
+            v = buf[shift:shift + a.nbytes].view(a.dtype)
+            v[...] = a
+            assert v.ctypes.data % mod == rem
+            assert np.ascontiguousarray(v, dtype=a.dtype).ctypes.data == v.ctypes.data  # passed as is
+            return v
+        hp = pinned_off(b.probe_ids.astype(np.uint32), 4, 2)
+        ho = pinned_off(b.cand_offsets.astype(np.uint64), 8, 4)
+        hc = pinned_off(b.cand_ids.astype(np.uint32), 4, 2)
+        res = ssj.ssj_verify_batches(ctx, [(h, h, 4, 5, hp, ho, hc, ssj.SSJ_HOST_DIRECT)], caps=[cap + 16])
+        assert np.array_equal(ssj.triples_to_array(res[0]), want)
+        assert ssj.ssj_device_error(ctx) == 0
+    finally:
+        ssj.ssj_destroy(ctx)

@@ -94,5 +94,13 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls():
             ssj.ssj_verify_batch_noalloc(ctx, h1, h1, 1, 2, t_pr, t_co, t_ci, 10 ** 9, None, 0,
                                          torch.zeros(1, dtype=torch.int64, device=dev), flags=ssj.SSJ_COUNT_ONLY)
         assert ei.value.status == ssj.SSJ_EINVAL
+        # so is a device array off its element alignment (offsets 8 bytes, the count 8, the rest 4)
+        h, p, q, b, want, t_pr, t_co, t_ci, cap, out, cnt = prepared[0]
+        for args in ((t_pr, t_co.data_ptr() + 4, t_ci, out, cnt), (t_pr.data_ptr() + 2, t_co, t_ci, out, cnt),
+                     (t_pr, t_co, t_ci, out.data_ptr() + 2, cnt), (t_pr, t_co, t_ci, out, cnt.data_ptr() + 4)):
+            with pytest.raises(ssj.SsjError) as ei:
+                ssj.ssj_verify_batch_noalloc(ctx, h, h, p, q, *args[:3], b.n_cands, args[3], cap, args[4],
+                                             n_probes=b.n_probes)
+            assert ei.value.status == ssj.SSJ_EINVAL
     finally:
         ssj.ssj_destroy(ctx)
