@@ -112,13 +112,14 @@ const char* ssj_last_error(ssj_ctx* ctx);
 
 /* Load a collection of n_sets sets.  offsets (n_sets+1 entries, host) are
  * nondecreasing with offsets[0] = 0; set i is tokens[offsets[i] ..
- * offsets[i+1]) (host).  Each set must hold fewer than 2^31 tokens.
+ * offsets[i+1]) (host).  n_sets is below 2^31 and each set must hold
+ * fewer than 2^31 tokens.
  * The data are copied; the caller may free them on return.
  * Device layout: tokens padded so that every set starts on a 16-byte
  * boundary (the padding repeats the set's last token), plus one 8-byte (start, length)
  * descriptor per set.  Empty sets are allowed and never match.
  * Errors: SSJ_EINVAL (NULL pointers, decreasing offsets, unsorted set with
- * SSJ_VALIDATE, unknown flag), SSJ_ENOMEM, SSJ_EDEVICE. */
+ * SSJ_VALIDATE, unknown flag, n_sets of 2^31 or more), SSJ_ENOMEM, SSJ_EDEVICE. */
 ssj_status ssj_load_collection(ssj_ctx* ctx, const uint64_t* offsets, const uint32_t* tokens,
                                uint32_t n_sets, uint32_t flags, ssj_coll* out);
 
@@ -188,7 +189,7 @@ typedef struct {
     ssj_coll R, S;                /* R == S: self-join */
     uint32_t p, q;                /* threshold t = p/q, 0 < p <= q < 2^31 (SSJ_SIM_OVERLAP:
                                      0 < p, q < 2^31); Jaccard unless flags select another function */
-    uint32_t n_probes;
+    uint32_t n_probes;            /* below 2^31 (SSJ_EINVAL otherwise) */
     const uint32_t* probe_ids;    /* n_probes ids into R */
     const uint64_t* cand_offsets; /* n_probes+1 nondecreasing offsets, cand_offsets[0] = 0 */
     const uint32_t* cand_ids;     /* cand_offsets[n_probes] ids into S; probe k is paired with

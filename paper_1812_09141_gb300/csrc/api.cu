@@ -329,6 +329,8 @@ ssj_status resolve(ssj_ctx* ctx, const ssj_batch* b, Collection** R, Collection*
     } else if (b->p == 0 || b->p > b->q || b->q >= (1u << 31)) {
         return fail(ctx, SSJ_EINVAL, "threshold must be 0 < p <= q < 2^31");
     }
+    // sizes derived from n_probes (n_probes + 1 offsets, 32-probe tiles) stay within 32 bits
+    if (b->n_probes >= (1u << 31)) return fail(ctx, SSJ_EINVAL, "n_probes must be below 2^31");
     auto ir = ctx->colls.find(b->R);
     auto is = ctx->colls.find(b->S);
     if (ir == ctx->colls.end() || is == ctx->colls.end()) return fail(ctx, SSJ_ENOTFOUND, "unknown collection");
@@ -589,6 +591,8 @@ extern "C" ssj_status ssj_load_collection(ssj_ctx* ctx, const uint64_t* offsets,
     NvtxScope nvtx_scope("ssj_load_collection");
     if (!ctx || !offsets || !out) return fail(ctx, SSJ_EINVAL, "NULL argument");
     if (flags & ~(SSJ_RENUMBER_BY_FREQ | SSJ_VALIDATE | SSJ_PIN_L2)) return fail(ctx, SSJ_EINVAL, "unknown load flag");
+    // a self-join probes every set, and batches hold fewer than 2^31 probes
+    if (n_sets >= (1u << 31)) return fail(ctx, SSJ_EINVAL, "n_sets must be below 2^31");
     if (offsets[0] != 0) return fail(ctx, SSJ_EINVAL, "offsets[0] must be 0");
     for (uint32_t i = 0; i < n_sets; ++i)
         if (offsets[i + 1] < offsets[i]) return fail(ctx, SSJ_EINVAL, "offsets decrease at set %u", i);

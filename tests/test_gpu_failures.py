@@ -224,3 +224,25 @@ def test_misaligned_arrays_never_reach_the_kernels(coll):
         assert ssj.ssj_device_error(ctx) == 0
     finally:
         ssj.ssj_destroy(ctx)
+
+
+def test_sizes_beyond_32_bit_arithmetic_are_refused(coll):
+    """A batch of 2^31 or more probes and a collection of 2^31 or more sets are refused before any
+    array is read or any memory is sized from them (the n + 1 offsets and 32-probe tiles derived
+    from those counts stay within 32 bits); the context keeps working."""
+    ctx = ssj.ssj_create(0)
+    try:
+        h = ssj.ssj_load_collection(ctx, coll.offsets, coll.tokens)
+        one = np.zeros(4, dtype=np.uint64)
+        b = ssj.ssj_batch(h, h, 4, 5, 1 << 31, one.ctypes.data, one.ctypes.data, one.ctypes.data, 0, 0)
+        n_out = ctypes.c_uint64()
+        assert ssj.lib().ssj_verify_batch(ctx, ctypes.byref(b), None, 0, ctypes.byref(n_out)) == ssj.SSJ_EINVAL
+        assert "2^31" in ssj.ssj_last_error(ctx)
+        handle = ctypes.c_uint32()
+        assert ssj.lib().ssj_load_collection(ctx, one.ctypes.data, one.ctypes.data, 1 << 31, 0,
+                                             ctypes.byref(handle)) == ssj.SSJ_EINVAL
+        b = synth.all_pairs_batch(coll.n)
+        got = ssj.triples_to_array(ssj.ssj_verify_batch(ctx, h, h, 4, 5, b.probe_ids, b.cand_offsets, b.cand_ids))
+        assert np.array_equal(got, oracle.sort_triples(oracle.bruteforce_self(coll.offsets, coll.tokens, 4, 5)))
+    finally:
+        ssj.ssj_destroy(ctx)
