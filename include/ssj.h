@@ -194,9 +194,11 @@ typedef struct {
     const uint64_t* cand_offsets; /* n_probes+1 nondecreasing offsets, cand_offsets[0] = 0 */
     const uint32_t* cand_ids;     /* cand_offsets[n_probes] ids into S; probe k is paired with
                                      cand_ids[cand_offsets[k] .. cand_offsets[k+1]) */
-    uint64_t n_cands;             /* cand_offsets[n_probes].  Required with SSJ_DEVICE_PTRS (the
-                                     host does not read device offsets; the device checks it);
-                                     with host pointers 0 means "take it from cand_offsets" */
+    uint64_t n_cands;             /* cand_offsets[n_probes], below 2^40 (also summed over the
+                                     batches of one call or prepared launch).  Required with
+                                     SSJ_DEVICE_PTRS (the host does not read device offsets; the
+                                     device checks it); with host pointers 0 means "take it from
+                                     cand_offsets" */
     uint32_t flags;               /* SSJ_COUNT_ONLY | SSJ_SORTED | SSJ_DEVICE_PTRS | ... | SSJ_SIM_* */
 } ssj_batch;
 

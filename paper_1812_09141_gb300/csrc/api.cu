@@ -68,6 +68,9 @@ constexpr uint32_t kMaxGroups = 2;
 // calls of at least this many candidates: on the 256-instance workload, 1.62e10-1.67e10 pairs/s
 // end to end against 1.09e10-1.45e10 with staged copies.
 constexpr uint64_t kDirectCands = 1ull << 25;
+// Candidates of one batch, and of one call or prepared launch: 2^40 ids are 4 TiB, beyond any
+// device's memory, and keep every workspace size computed from the count far from 64-bit wrap.
+constexpr uint64_t kMaxCands = 1ull << 40;
 
 struct Collection {
     uint32_t n_sets = 0;
@@ -314,6 +317,7 @@ ssj_status validate_host_batch(ssj_ctx* ctx, const ssj_batch* b, uint64_t* n_can
     }
     if (b->cand_offsets[0] != 0) return fail(ctx, SSJ_EINVAL, "cand_offsets[0] must be 0");
     const uint64_t nc = b->cand_offsets[b->n_probes];
+    if (nc >= kMaxCands) return fail(ctx, SSJ_EINVAL, "n_cands must be below 2^40");
     if (b->n_cands && b->n_cands != nc) return fail(ctx, SSJ_EINVAL, "n_cands != cand_offsets[n_probes]");
     if (nc && !b->cand_ids) return fail(ctx, SSJ_EINVAL, "NULL cand_ids");
     *n_cands = nc;
@@ -331,6 +335,7 @@ ssj_status resolve(ssj_ctx* ctx, const ssj_batch* b, Collection** R, Collection*
     }
     // sizes derived from n_probes (n_probes + 1 offsets, 32-probe tiles) stay within 32 bits
     if (b->n_probes >= (1u << 31)) return fail(ctx, SSJ_EINVAL, "n_probes must be below 2^31");
+    if (b->n_cands >= kMaxCands) return fail(ctx, SSJ_EINVAL, "n_cands must be below 2^40");
     auto ir = ctx->colls.find(b->R);
     auto is = ctx->colls.find(b->S);
     if (ir == ctx->colls.end() || is == ctx->colls.end()) return fail(ctx, SSJ_ENOTFOUND, "unknown collection");
@@ -909,6 +914,7 @@ extern "C" ssj_status ssj_verify_batches(ssj_ctx* ctx, const ssj_batch* batches,
         sh.n_tiles += (uint32_t)tiles;
         sh.total_probes += b->n_probes;
         sh.total_cands += n_cands[i];
+        if (sh.total_cands >= kMaxCands) return fail(ctx, SSJ_EINVAL, "2^40 or more candidates in one call");
         // device staging of this batch: probe ids, offsets, candidate ids, output
         io_off[i] = off;
         off += align256(4ull * std::max<uint32_t>(b->n_probes, 1)) + align256(8ull * (b->n_probes + 1)) +
@@ -1832,6 +1838,7 @@ extern "C" ssj_status ssj_multi_create(ssj_ctx* ctx, const ssj_batch* batches, u
         sh.n_tiles += (uint32_t)tiles;
         sh.total_probes += b->n_probes;
         sh.total_cands += b->n_cands;
+        if (sh.total_cands >= kMaxCands) return fail(ctx, SSJ_EINVAL, "2^40 or more candidates in one launch");
         table[i] = I;
         m->colls.push_back(b->R);
         m->colls.push_back(b->S);

@@ -226,10 +226,11 @@ def test_misaligned_arrays_never_reach_the_kernels(coll):
         ssj.ssj_destroy(ctx)
 
 
-def test_sizes_beyond_32_bit_arithmetic_are_refused(coll):
-    """A batch of 2^31 or more probes and a collection of 2^31 or more sets are refused before any
-    array is read or any memory is sized from them (the n + 1 offsets and 32-probe tiles derived
-    from those counts stay within 32 bits); the context keeps working."""
+def test_sizes_beyond_the_size_arithmetic_are_refused(coll):
+    """A batch of 2^31 or more probes, a collection of 2^31 or more sets and a batch of 2^40 or
+    more candidates are refused before any memory is sized from them (the n + 1 offsets and
+    32-probe tiles stay within 32 bits, the workspace sizes far from 64-bit wrap); the context
+    keeps working."""
     ctx = ssj.ssj_create(0)
     try:
         h = ssj.ssj_load_collection(ctx, coll.offsets, coll.tokens)
@@ -241,6 +242,15 @@ def test_sizes_beyond_32_bit_arithmetic_are_refused(coll):
         handle = ctypes.c_uint32()
         assert ssj.lib().ssj_load_collection(ctx, one.ctypes.data, one.ctypes.data, 1 << 31, 0,
                                              ctypes.byref(handle)) == ssj.SSJ_EINVAL
+        # 2^40 candidates: as the count of a device batch, and as the last host offset
+        b = ssj.ssj_batch(h, h, 4, 5, 1, one.ctypes.data, one.ctypes.data, one.ctypes.data, 1 << 40,
+                          ssj.SSJ_DEVICE_PTRS | ssj.SSJ_COUNT_ONLY)
+        assert ssj.lib().ssj_verify_batch(ctx, ctypes.byref(b), None, 0, ctypes.byref(n_out)) == ssj.SSJ_EINVAL
+        assert "2^40" in ssj.ssj_last_error(ctx)
+        offs = np.array([0, 1 << 40], dtype=np.uint64)
+        b = ssj.ssj_batch(h, h, 4, 5, 1, one.ctypes.data, offs.ctypes.data, one.ctypes.data, 0, ssj.SSJ_COUNT_ONLY)
+        assert ssj.lib().ssj_verify_batch(ctx, ctypes.byref(b), None, 0, ctypes.byref(n_out)) == ssj.SSJ_EINVAL
+        assert "2^40" in ssj.ssj_last_error(ctx)
         b = synth.all_pairs_batch(coll.n)
         got = ssj.triples_to_array(ssj.ssj_verify_batch(ctx, h, h, 4, 5, b.probe_ids, b.cand_offsets, b.cand_ids))
         assert np.array_equal(got, oracle.sort_triples(oracle.bruteforce_self(coll.offsets, coll.tokens, 4, 5)))
