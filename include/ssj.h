@@ -418,7 +418,9 @@ typedef struct {
 ssj_status ssj_multi_autotune(ssj_ctx* ctx, ssj_multi* m, void* stream, uint32_t reps, ssj_tune_result* out);
 
 /* Size the workspace for batches of up to n_probes probes and n_cands
- * candidates (device allocation happens here, not in later calls). */
+ * candidates (device allocation happens here, not in later calls).
+ * Errors: SSJ_EINVAL (n_probes of 2^31 or more, n_cands of 2^40 or more),
+ * SSJ_ENOMEM. */
 ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands);
 
 /* Read and clear the device-side error word of the last stream-ordered or

@@ -738,6 +738,8 @@ extern "C" ssj_status ssj_collection_info(ssj_ctx* ctx, ssj_coll coll, uint32_t*
 
 extern "C" ssj_status ssj_reserve(ssj_ctx* ctx, uint32_t n_probes, uint64_t n_cands) {
     if (!ctx) return SSJ_EINVAL;
+    if (n_probes >= (1u << 31) || n_cands >= kMaxCands)
+        return fail(ctx, SSJ_EINVAL, "n_probes must be below 2^31 and n_cands below 2^40");
     DeviceGuard g(ctx->device);
     return ensure_device_buffer(ctx, &ctx->ws, &ctx->ws_bytes, workspace_bytes(n_probes, n_cands, ctx->num_sms));
 }

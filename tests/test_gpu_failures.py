@@ -247,6 +247,8 @@ def test_sizes_beyond_the_size_arithmetic_are_refused(coll):
                           ssj.SSJ_DEVICE_PTRS | ssj.SSJ_COUNT_ONLY)
         assert ssj.lib().ssj_verify_batch(ctx, ctypes.byref(b), None, 0, ctypes.byref(n_out)) == ssj.SSJ_EINVAL
         assert "2^40" in ssj.ssj_last_error(ctx)
+        assert ssj.lib().ssj_reserve(ctx, 16, 1 << 40) == ssj.SSJ_EINVAL
+        assert ssj.lib().ssj_reserve(ctx, 1 << 31, 16) == ssj.SSJ_EINVAL
         offs = np.array([0, 1 << 40], dtype=np.uint64)
         b = ssj.ssj_batch(h, h, 4, 5, 1, one.ctypes.data, offs.ctypes.data, one.ctypes.data, 0, ssj.SSJ_COUNT_ONLY)
         assert ssj.lib().ssj_verify_batch(ctx, ctypes.byref(b), None, 0, ctypes.byref(n_out)) == ssj.SSJ_EINVAL
