@@ -377,3 +377,52 @@ def test_renumbering_and_id_permutation_invariance():
     got = {tuple(map(int, t)) for t in oracle.bruteforce_self(c2.offsets, c2.tokens, 3, 5)}
     want = {(min(perm[r], perm[s]), max(perm[r], perm[s]), o) for r, s, o in base}
     assert got == want
+
+
+# ---------------------------------------------------------------- helpers the parity tests lean on
+
+def test_sort_triples_is_the_r_then_s_order_of_python_tuples():
+    """sort_triples against Python's own tuple sort, with ids above 2^31 (a signed key would
+    misplace them) and triples that share r."""
+    rng = np.random.default_rng(11)
+    r = rng.integers(0, 2**32, size=400, dtype=np.uint64)
+    r[::3] = r[0]  # many triples with the same r
+    s = rng.integers(0, 2**32, size=400, dtype=np.uint64)
+    o = rng.integers(0, 2000, size=400, dtype=np.uint64)
+    t = np.stack([r, s, o], axis=1).astype(np.uint32)
+    want = sorted(map(tuple, t.tolist()), key=lambda x: (x[0], x[1]))
+    assert oracle.sort_triples(t).tolist() == [list(x) for x in want]
+    assert oracle.sort_triples(np.zeros((0, 3), dtype=np.uint32)).shape == (0, 3)
+
+
+def test_verify_batch_threads_equals_bruteforce_for_any_split():
+    """The threaded oracle splits the probes into contiguous ranges: for any number of ranges
+    (one, a few, more than there are probes) and a batch with empty candidate lists, its results
+    are brute force's on the listed pairs, in the probe order of the single-range call."""
+    spec = synth.tiny_self_join(n=240)
+    spec.plant_frac, spec.plant_edits = 0.2, 2
+    c = synth.collection(spec)
+    b = synth.all_pairs_batch(c.n)  # probe r is paired with r+1 .. n-1
+    # every fifth probe keeps no candidates (empty lists inside the batch)
+    co = b.cand_offsets.astype(np.int64)
+    counts = np.diff(co)
+    keep = np.ones(len(b.cand_ids), dtype=bool)
+    dropped = set(range(0, b.n_probes, 5))
+    for k in dropped:
+        keep[co[k]:co[k + 1]] = False
+        counts[k] = 0
+    offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint64)
+    cands = b.cand_ids[keep]
+    args = (c.offsets, c.tokens, c.offsets, c.tokens, True, 3, 5, b.probe_ids, offs, cands)
+    whole = np.asarray(oracle.verify_batch(*args)).reshape(-1, 3)
+    # brute force over all pairs, less the pairs whose probe (the smaller id) lost its list
+    want = [t for t in oracle.sort_triples(oracle.bruteforce_self(c.offsets, c.tokens, 3, 5)).tolist()
+            if t[0] not in dropped]
+    assert len(want) > 20
+    assert oracle.sort_triples(whole).tolist() == want
+    assert np.all(np.diff(whole[:, 0].astype(np.int64)) >= 0)  # probe order
+    for n_threads in (1, 2, 3, 7, b.n_probes + 5):
+        got = np.asarray(oracle.verify_batch_threads(*args, n_threads=n_threads)).reshape(-1, 3)
+        assert np.array_equal(got, whole), n_threads
+    empty = oracle.verify_batch_threads(c.offsets, c.tokens, c.offsets, c.tokens, True, 3, 5, [], [0], [])
+    assert empty.shape == (0, 3)
