@@ -805,7 +805,8 @@ def run_reference(args):
         for k, p, q, pr, co, ci in sample:
             cR, cS, selfj = coll_pair(colls, k)
             oracle.verify_batch(cR.offsets, cR.tokens, cS.offsets, cS.tokens, selfj, p, q, pr, co, ci, sim=SIM)
-    one_step()  # warm-up
+    for _ in range(args.warmup):  # untimed warm-up steps, as in the GPU arm
+        one_step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         one_step()
@@ -822,7 +823,7 @@ def run_reference(args):
                                         f"{args.steps} steps of a fixed sample of {sample_pairs} of the "
                                         f"{pairs_step} candidate pairs of a step: every {stride}-th probe of "
                                         f"each of the {len(batches)} batches with all its candidates")
-                                       + ", after one warm-up step, one host thread"},
+                                       + f", after {args.warmup} untimed warm-up steps, one host thread"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -68,3 +68,36 @@ def test_both_arms_report_the_same_config():
     batches = [(0, 3, 5, b.probe_ids, b.cand_offsets, b.cand_ids)]
     c1, c2 = bench.common_config(cfg, batches, args), bench.common_config(dict(cfg), batches, args)
     assert c1 == c2 and c1["pairs_per_step"] == len(b.cand_ids) and c1["instances_per_launch"] == 1
+
+
+def _bench_reference(env_extra):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "tiny", "--steps", "2",
+                        "--warmup", "3"], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_prints_one_line_of_the_contract():
+    """`bench.py --impl reference` runs the oracle on the CPU (no GPU needed) and prints one JSON
+    line with the GPU arm's metric, unit and config, its own cpu_baseline and a copy-free e2e."""
+    (line,) = _bench_reference({"RANK": "0", "WORLD_SIZE": "1"})
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["steps"] == 2 and line["warmup"] == 3 and line["higher_is_better"]
+    assert line["config"]["workload"] == "tiny" and line["config"]["pairs_per_step"] == 499_500
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert "3 untimed warm-up steps" in cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_0_only():
+    """Under torchrun the reference arm's ranks other than 0 exit 0 without work or output."""
+    assert _bench_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
