@@ -408,12 +408,26 @@ def rank_share(batches, rank: int, world: int):
     return out
 
 
-def common_config(cfg, batches, args):
-    """The config both arms report (same keys and values): the workload and its candidates."""
+def input_bytes_of(colls, batches):
+    """Bytes of a step's inputs as they sit on the device: token arrays and set offsets of the
+    collections, probe ids, candidate offsets and candidate ids of the batches."""
+    return (sum(4 * len(c.tokens) + 8 * c.n for c in colls)
+            + sum(4 * len(b[3]) + 8 * len(b[4]) + 4 * len(b[5]) for b in batches))
+
+
+def common_config(cfg, colls, batches, args):
+    """The config both arms report (same keys and values): the workload, its candidates, and how
+    the GPU arm keeps timed steps from reusing L2 (inputs larger than L2, and a flush between
+    steps)."""
+    nbytes = input_bytes_of(colls, batches)
+    l2 = (f"inputs {nbytes / 1e6:.0f} MB, " + ("larger than" if nbytes > 129e6 else "within")
+          + " the 129 MB L2; " + (f"the GPU arm writes {args.l2_flush_mb} MiB before every timed step"
+                                  if args.l2_flush_mb else "no flush between steps (profiling run)"))
     return dict(cfg, pairs_per_step=int(sum(len(b[5]) for b in batches)), instances_per_launch=len(batches),
                 similarity=args.sim,
                 candidates=("AllPairs prefix filter" + (" + PPJoin" if args.ppjoin else ""))
-                if args.workload != "tiny" else "all pairs")
+                if args.workload != "tiny" else "all pairs",
+                l2_between_steps=l2)
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -617,7 +631,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_staged_t = max_over_ranks(e2e_staged_t, world, dev)
     result = {"total_ms": total_ms, "step_ms": step_ms, "verify_ms": verify_ms, "plan_ms": plan_ms,
               "launches": launches, "counts": result_counts, "pairs_step": pairs_step, "pairs_all": pairs_all,
-              "graph_ms": graph_ms, "cfg": common_config(cfg, all_batches, args),
+              "graph_ms": graph_ms, "cfg": common_config(cfg, colls, all_batches, args),
               "e2e_value": pairs_all * e2e_steps / e2e_t if e2e_t > 0 else None, "h2d": h2d, "d2h": d2h,
               "e2e_single_value": pairs_all * e2e_steps / e2e_single_t if e2e_single_t > 0 else None,
               "e2e_staged_value": pairs_all * e2e_steps / e2e_staged_t if e2e_staged_t > 0 else None,
@@ -816,7 +830,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "strong" if args.gpus > 1 else "weak", "vs_baseline": None,
-            "dtype": "u32", "data": "synthetic", "config": common_config(cfg, batches, args),
+            "dtype": "u32", "data": "synthetic", "config": common_config(cfg, colls, batches, args),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": (f"{args.steps} full steps of the workload ({pairs_step} pairs each)"
                                         if whole else
@@ -888,8 +902,7 @@ def main():
         return
     pairs_step = res["pairs_step"]
     total_s = res["total_ms"] / 1e3
-    input_bytes = (sum(4 * len(c.tokens) + 8 * c.n for c in colls)
-                   + sum(4 * len(b[3]) + 8 * len(b[4]) + 4 * len(b[5]) for b in batches))
+    input_bytes = input_bytes_of(colls, batches)
     value = whole_job_value(res["pairs_all"], args.steps, total_s)
     peak, peak_kind = measured_hbm_peak()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -62,12 +62,16 @@ def test_both_arms_report_the_same_config():
     """The GPU arm and the reference arm build their `config` with the same function from the same
     workload and candidates, so the two lines can be compared key by key."""
     import types
-    args = types.SimpleNamespace(sim="jaccard", ppjoin=False, workload="short_sets")
+    args = types.SimpleNamespace(sim="jaccard", ppjoin=False, workload="short_sets", l2_flush_mb=512)
     cfg = {"workload": "short_sets", "n_sets": 10}
+    c = synth.collection(synth.tiny_self_join(seed=1001, n=50))
     b = synth.random_batch(1, 50, 50, 20, 5)
     batches = [(0, 3, 5, b.probe_ids, b.cand_offsets, b.cand_ids)]
-    c1, c2 = bench.common_config(cfg, batches, args), bench.common_config(dict(cfg), batches, args)
+    c1, c2 = bench.common_config(cfg, [c], batches, args), bench.common_config(dict(cfg), [c], batches, args)
     assert c1 == c2 and c1["pairs_per_step"] == len(b.cand_ids) and c1["instances_per_launch"] == 1
+    nbytes = 4 * len(c.tokens) + 8 * c.n + 4 * len(b.probe_ids) + 8 * len(b.cand_offsets) + 4 * len(b.cand_ids)
+    assert bench.input_bytes_of([c], batches) == nbytes
+    assert "within the 129 MB L2" in c1["l2_between_steps"] and "512 MiB" in c1["l2_between_steps"]
 
 
 def _bench_reference(env_extra):
