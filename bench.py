@@ -474,10 +474,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     if args.granularity:
         # a fixed setting (profiling runs: no tuning launches before the timed ones)
-        g = [int(x) for x in args.granularity.split(",")]
-        t, l, w, b = g[:4]
-        d = g[4] if len(g) > 4 else 0
-        ix = g[5] if len(g) > 5 else 0
+        t, l, w, b, d, ix = parse_granularity(args.granularity)
         ssj.ssj_set_granularity(ctx, t, l, w, b)
         ssj.ssj_set_short_pairs(ctx, d)
         ssj.ssj_set_index_items(ctx, ix)
@@ -842,13 +839,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
+WORKLOADS = ("uneven_instances", "tiny", "short_sets", "long_sets", "serving_collection", "rs_short", "serving",
+             "candgen")
+
+
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="uneven_instances")
+    ap.add_argument("--workload", default="uneven_instances", choices=WORKLOADS)
     ap.add_argument("--no-serving", action="store_true", help="skip the served-latency leg of the default workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
@@ -865,7 +866,25 @@ def main():
                     help="load the collections with SSJ_PIN_L2 (persisting-L2 window over the token array)")
     ap.add_argument("--instances", type=int, default=0,
                     help="uneven_instances: verify only the first N instances (profiling runs on a smaller case)")
-    args = ap.parse_args()
+    return ap
+
+
+def parse_granularity(text: str):
+    """--granularity: thread, lane and warp bin keys and block_threads, then optionally
+    drain_min_live and index_min_cands (0 when absent)."""
+    g = [int(x) for x in text.split(",")]
+    if not 4 <= len(g) <= 6 or min(g) < 0:
+        raise ValueError(f"--granularity wants 4 to 6 non-negative integers, got {text!r}")
+    return tuple(g[:4]) + (g[4] if len(g) > 4 else 0, g[5] if len(g) > 5 else 0)
+
+
+def main():
+    args = build_parser().parse_args()
+    if args.granularity:
+        try:
+            parse_granularity(args.granularity)
+        except ValueError as e:
+            raise SystemExit(str(e))
     global SIM, INSTANCES
     SIM = SIM_NAMES[args.sim]
     INSTANCES = args.instances

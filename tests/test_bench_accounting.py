@@ -105,3 +105,40 @@ def test_reference_arm_prints_one_line_of_the_contract():
 def test_reference_arm_runs_on_rank_0_only():
     """Under torchrun the reference arm's ranks other than 0 exit 0 without work or output."""
     assert _bench_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_every_profile_command_runs_committed_files_with_flags_bench_accepts():
+    """Each summary under profiles/ gives the command that made it: an ncu run with
+    --clock-control none of `python bench.py ...`, whose arguments the current bench.py parser
+    still accepts (workload, granularity setting, flags)."""
+    import glob
+    import os
+    import re
+    import shlex
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    files = sorted(glob.glob(os.path.join(root, "profiles", "*.md")))
+    assert files
+    for f in files:
+        text = open(f).read()
+        blocks = re.findall(r"```\n(.*?)```", text, flags=re.S)
+        cmds = [b.replace("\\\n", " ") for b in blocks if "bench.py" in b]
+        assert cmds, f"{f} gives no command"
+        for cmd in cmds:
+            cmd = " ".join(cmd.split())
+            assert cmd.startswith("ncu ") and "--clock-control none" in cmd, f
+            tail = cmd.split("python bench.py", 1)[1]
+            args = bench.build_parser().parse_args(shlex.split(tail))
+            assert args.warmup >= 3, f
+            if args.granularity:
+                bench.parse_granularity(args.granularity)
+
+
+def test_parse_granularity():
+    assert bench.parse_granularity("512,2048,2048,256") == (512, 2048, 2048, 256, 0, 0)
+    assert bench.parse_granularity("4096,1,4096,65664,16,256") == (4096, 1, 4096, 65664, 16, 256)
+    for bad in ("1,2,3", "1,2,3,4,5,6,7", "1,-2,3,4"):
+        try:
+            bench.parse_granularity(bad)
+        except ValueError:
+            continue
+        raise AssertionError(bad)
