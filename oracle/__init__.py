@@ -1,7 +1,7 @@
 """CPU oracle for the verification phase of exact set similarity joins.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
-the CPU-baseline leg of ``bench.py`` may import this package.  The library
+the CPU-baseline leg and reference arm of ``bench.py`` may import this package.  The library
 (``paper_1812_09141_gb300``) never imports, links or calls it; the two share
 no code.
 
@@ -28,6 +28,8 @@ Functions and the passages they follow:
   for full-size parity tests, with no arithmetic of its own.
 * ``renumber`` - token renumbering by ascending frequency (Section 2.2.1).
 * ``allpairs_self`` - algorithm ALL (Sections 2.2.3, 2.2.4, 3.1).
+* ``sort_triples`` - the canonical (r, s) order in which result lists are
+  compared (the paper leaves output order open, Section 3.3.1).
 
 Every function is pinned by a test in ``tests/test_oracle_pins.py`` against
 something other than itself (the paper's worked example, exact rationals,

@@ -5,7 +5,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library's product path links,
  * loads or calls this file; only the test suite, the smoke check and the
- * bench's CPU-baseline leg do.  It shares no code, header or table with the
+ * bench's CPU-baseline leg and reference arm do.  It shares no code, header or table with the
  * CUDA library.
  *
  * Plain, single-threaded, slow on purpose: every function is the textbook
