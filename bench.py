@@ -373,8 +373,8 @@ class ClockSampler:
 
 def max_over_ranks(value: float, world: int, device=None) -> float:
     """The largest value over the ranks of the job (every rank gets it), then a barrier.
-    Each rank verifies the whole workload on its own GPU (replicas: the path has no exchange
-    step), so the job's time is its slowest rank's."""
+    Each rank verifies its own contiguous probe range of every batch against its own copy of the
+    collections (the path has no exchange step), so the job's time is its slowest rank's."""
     if world == 1:
         return value
     import torch
