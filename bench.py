@@ -17,8 +17,9 @@ value   pairs/s with inputs resident in HBM; L2 is flushed (512 MiB write)
         over ranks.  With N ranks every batch is split into N contiguous
         probe ranges, one per rank (strong scaling; no data exchange).
 e2e     the same metric through the public synchronous call with pinned
-        host buffers: host->device copies, kernels and the result readback
-        in the timed region.
+        host buffers: the inputs' transfer (copies, or in calls of 2^25+
+        candidates the kernels' own reads of the pinned inputs over the host
+        link), kernels and the result readback in the timed region.
 served  (default workload, one rank) continuous batching on the resident
         1,000,000-set collection: p50/p99 submit-to-result latency of 1,000
         Poisson-arriving requests at 0.5x and 0.9x of the closed-loop peak,
