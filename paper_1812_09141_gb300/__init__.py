@@ -316,9 +316,9 @@ def ssj_self_join(ctx: int, coll: int, p: int, q: int, flags: int = 0, cap: int 
 
 
 def ssj_verify_batches(ctx: int, batches: list, caps: list | None = None):
-    """Several host batches in one call (one batched launch; a call of more than 2^24 candidates
-    runs two, the second group's inputs moving while the first group's kernels run; pinned inputs
-    of a call of 2^25+ candidates are read by the kernels directly).  batches: list of (R, S, p, q, probe_ids,
+    """Several host batches in one call (one batched launch; a call of 2^25+ candidates over two or
+    more batches runs two, the second group's inputs moving while the first group's kernels run,
+    and its pinned inputs are read by the kernels directly).  batches: list of (R, S, p, q, probe_ids,
     cand_offsets, cand_ids, flags).  Returns a list with, per batch, its structured triples (or
     its count with SSJ_COUNT_ONLY)."""
     n = len(batches)
