@@ -226,7 +226,7 @@ ssj_status ssj_verify_batch(ssj_ctx* ctx, const ssj_batch* batch, ssj_triple* ou
  * one verify kernel cover every batch of a group.  A call with fewer than
  * 2^25 candidates is one group, its inputs copied to the device first.  A
  * larger call is cut into two consecutive groups of batches with about
- * equal candidate counts: its inputs in pinned host memory are read by the
+ * equal candidate counts (one group if it holds a single batch): its inputs in pinned host memory are read by the
  * kernels directly over the host link (SSJ_HOST_DIRECT) unless a batch sets
  * SSJ_HOST_STAGED, and the inputs that are copied are copied for the second
  * group on a second stream while the first group's kernels run.  Then the
